@@ -1,0 +1,160 @@
+"""Pins for the oracle's direct and Krylov solvers (Sec. 3, Alg. 1, Sec. 5).
+
+Fixed by mathematics: hand-solved 2x2 systems, manufactured solutions, finite
+termination of CG and GMRES in exact-enough arithmetic, the flexible Arnoldi
+relation, orthonormality, the CG error bound quoted in Sec. 3 and the
+one-step convergence of FGMRES when the inner solve is exact with delta = 0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1408_1237_gb300 import inputs
+
+
+def test_direct_solve_2x2_by_hand(oracle_mod):
+    # K = [[1+g, a], [a, 1+g]]: x = [(1+g) b1 - a b2, (1+g) b2 - a b1] / ((1+g)^2 - a^2)
+    g, a = 0.1, 0.5
+    K = np.array([[1 + g, a], [a, 1 + g]])
+    b = np.array([1.0, -2.0])
+    det = (1 + g) ** 2 - a * a
+    expect = np.array([(1 + g) * 1.0 - a * -2.0, (1 + g) * -2.0 - a * 1.0]) / det
+    np.testing.assert_allclose(oracle_mod.direct_solve(K, b), expect, rtol=1e-14)
+
+
+def test_direct_solve_manufactured(oracle_mod):
+    X = inputs.uniform_points(300, 2, seed=11).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.1, 1e-2)
+    x_true = np.random.default_rng(12).standard_normal(300)
+    b = K @ x_true
+    x = oracle_mod.direct_solve(K, b)
+    kappa = np.linalg.cond(K)
+    assert np.linalg.norm(x - x_true) / np.linalg.norm(x_true) < 1e3 * kappa * 1e-16
+    L = np.linalg.cholesky(K)
+    assert np.abs(L @ L.T - K).max() < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 5, 16])
+def test_cg_finite_termination(oracle_mod, N):
+    # In exact arithmetic CG terminates in at most N steps.
+    rng = np.random.default_rng(N)
+    A = rng.standard_normal((N, N))
+    A = A @ A.T + N * np.eye(N)
+    b = rng.standard_normal(N)
+    x, it = oracle_mod.cg(lambda v: A @ v, b, tol=1e-12, maxit=N + 2)
+    assert it <= N + 1
+    assert np.linalg.norm(A @ x - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_cg_error_bound(oracle_mod):
+    # Sec. 3: |e_k|_K / |e_0|_K <= 2 ((sqrt(kappa)-1)/(sqrt(kappa)+1))^k
+    X = inputs.uniform_points(200, 2, seed=13).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.05, 0.1)
+    lam = np.linalg.eigvalsh(K)
+    kappa = lam[-1] / lam[0]
+    rho = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    b = np.random.default_rng(14).standard_normal(200)
+    x_star = oracle_mod.direct_solve(K, b)
+    knorm = lambda e: math.sqrt(e @ K @ e)
+    e0 = knorm(x_star)
+    for k in range(1, 30):
+        xk, _ = oracle_mod.cg(lambda v: K @ v, b, tol=0.0, maxit=k)
+        assert knorm(x_star - xk) <= 2 * rho ** k * e0 * (1 + 1e-9) + 1e-12
+
+
+@pytest.mark.parametrize("N", [4, 12])
+def test_gmres_finite_termination(oracle_mod, N):
+    # GMRES (Alg. 1 with M = I) with restart >= N is exact after <= N steps.
+    X = inputs.uniform_points(N, 2, seed=N + 20).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.4, 0.05)
+    b = np.random.default_rng(N).standard_normal(N)
+    res = oracle_mod.fgmres(lambda v: K @ v, b, restart=N, tol=1e-13, max_cycles=1)
+    assert res.outer_iters <= N
+    assert res.relres <= 1e-11
+
+
+def test_fgmres_exact_inner_delta_zero_one_step(oracle_mod):
+    # With M = K solved exactly, K M^-1 = I and FGMRES converges in one step.
+    X = inputs.uniform_points(80, 2, seed=30).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.2, 1e-2)
+    b = np.random.default_rng(31).standard_normal(80)
+    inner = lambda v: (oracle_mod.direct_solve(K, v), 0)
+    res = oracle_mod.fgmres(lambda v: K @ v, b, restart=10, tol=1e-12, max_cycles=2,
+                            inner=inner)
+    assert res.outer_iters == 1
+    assert res.relres < 1e-12
+
+
+def test_flexible_arnoldi_relation_and_orthonormality(oracle_mod):
+    # K Z_k = V_{k+1} Hbar_k with V orthonormal (Eq. Arnoldi for the flexible basis).
+    X = inputs.uniform_points(120, 2, seed=32).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.1, 1e-2)
+    M = K + 0.1 * np.eye(120)
+    b = np.random.default_rng(33).standard_normal(120)
+    inner = lambda v: oracle_mod.cg(lambda u: M @ u, v, 1e-2, 100)
+    res = oracle_mod.fgmres(lambda v: K @ v, b, restart=12, tol=1e-14, max_cycles=1,
+                            inner=inner)
+    V, Z, H, beta = res.last_cycle
+    k = Z.shape[0]
+    assert k == 12
+    np.testing.assert_allclose(K @ Z.T, V.T @ H, atol=1e-11)
+    np.testing.assert_allclose(V @ V.T, np.eye(k + 1), atol=1e-11)
+    # first basis vector is the normalised initial residual (x0 = 0)
+    np.testing.assert_allclose(V[0] * beta, b, atol=1e-12)
+
+
+def test_estimate_equals_true_residual(oracle_mod):
+    # The least-squares residual of Alg. 1 equals |b - K x| in exact arithmetic.
+    X = inputs.uniform_points(150, 2, seed=34).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.1, 1e-2)
+    b = np.random.default_rng(35).standard_normal(150)
+    for steps in (3, 7):
+        res = oracle_mod.fgmres(lambda v: K @ v, b, restart=steps, tol=1e-14, max_cycles=1)
+        true = np.linalg.norm(b - K @ res.x) / np.linalg.norm(b)
+        assert res.history[-1] == pytest.approx(true, rel=1e-8)
+
+
+def test_preconditioned_spectrum_bound(oracle_mod):
+    # Exact inner solve with M = K + delta I: K M^-1 has eigenvalues
+    # lambda / (lambda + delta) in [lmin/(lmin+delta), lmax/(lmax+delta)], so the
+    # outer GMRES residual obeys the SPD Chebyshev bound with that kappa.
+    X = inputs.uniform_points(200, 2, seed=36).astype(np.float64)
+    gamma, delta = 1e-3, 1e-2
+    K = oracle_mod.regularised_matrix(X, 0.15, gamma)
+    lam = np.linalg.eigvalsh(K)
+    mu = lam / (lam + delta)
+    kappa = mu.max() / mu.min()
+    rho = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    M = K + delta * np.eye(200)
+    b = np.random.default_rng(37).standard_normal(200)
+    inner = lambda v: (oracle_mod.direct_solve(M, v), 0)
+    res = oracle_mod.fgmres(lambda v: K @ v, b, restart=60, tol=1e-13, max_cycles=1,
+                            inner=inner)
+    # K M^-1 = Q diag(mu) Q^T is symmetric, so GMRES's residual is bounded by
+    # 2 rho^k (minimal residual <= Chebyshev polynomial on [mu_min, mu_max])
+    for k, est in enumerate(res.history, start=1):
+        assert est <= 2 * rho ** k * (1 + 1e-8) + 1e-13
+
+
+def test_paper_solver_matches_cholesky_small_problem(oracle_mod):
+    p = inputs.small_problem(seed=0, N=600)
+    X, b = p["X"].astype(np.float64), p["b"].astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, p["sigma"], p["gamma"])
+    M = K + p["delta"] * np.eye(600)
+    res = oracle_mod.krr_fgmres(lambda v: K @ v, lambda v: M @ v, b,
+                                restart=30, tol=1e-6, inner_tol=1e-2)
+    x_star = oracle_mod.direct_solve(K, b)
+    assert res.relres <= 1e-6
+    kappa = np.linalg.cond(K)
+    assert np.linalg.norm(res.x - x_star) / np.linalg.norm(x_star) <= kappa * 1e-6
+    # unpreconditioned CG needs many more MVPs than FGMRES has outer steps
+    _, it_cg = oracle_mod.cg(lambda v: K @ v, b, 1e-6, 5000)
+    assert res.outer_iters < it_cg
+
+
+def test_paper_parameter_rules(oracle_mod):
+    # Sec. 6: delta = 10 gamma (1e-3 when gamma = 0); inner tol = 10 x outer tol
+    assert oracle_mod.default_delta(1e-3) == pytest.approx(1e-2)
+    assert oracle_mod.default_delta(0.0) == pytest.approx(1e-3)
+    assert oracle_mod.default_inner_tol(1e-4) == pytest.approx(1e-3)
