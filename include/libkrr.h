@@ -1,0 +1,205 @@
+/*
+ * libkrr -- preconditioned Krylov solvers for Gaussian-kernel regression on
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of "Preconditioned Krylov solvers for kernel regression"
+ * (Srinivasan, Hu, Gumerov, Murtugudde, Duraiswami; arXiv:1408.1237):
+ * solve K x = b with K = K_hat + gamma I (Eq. 3), K_hat the Gaussian kernel
+ * matrix of Eqs. 1-2, by flexible GMRES (Algorithm 1) right-preconditioned by
+ * a truncated conjugate-gradient solve with M = K + delta I (Sec. 5).  The
+ * kernel matrix is never stored: every product K q is summed on the fly.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Arrays:     X is N x d row-major float32 (point i at X[i*d .. i*d+d-1]).
+ *             Multi-column arrays (Q, Y, B, Xsol) are N x m column-major
+ *             float32: column c starts at element c*N.
+ * Pointers:   array pointers may be DEVICE pointers (cudaMalloc / PyTorch
+ *             tensors on the handle's device) or HOST pointers (pageable or
+ *             pinned).  Host arrays are staged through the handle's device
+ *             workspace with copies on `stream`, and such a call synchronises
+ *             `stream` before it returns.  Calls on device arrays are
+ *             stream-ordered and return without waiting unless an `info`
+ *             pointer asks for results (see each function).
+ *             The caller owns every array; the library never frees one.
+ *             No array may alias another unless a function says so.
+ * Streams:    `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *             default stream).  All device work of a call runs on it.
+ * Handle:     a krr_handle binds to the device that is current when it is
+ *             created and owns the device workspace (grown on demand, freed by
+ *             krr_destroy).  A handle is not thread-safe: use one per host
+ *             thread, or serialise calls.
+ * Errors:     every function returns a krr_status and never aborts or exits;
+ *             krr_last_error(h) gives a message for the last failing call on h.
+ *             Invalid arguments are rejected before any device work is queued.
+ *             Scalar outputs (gradients of krr_mll_grad) are HOST pointers.
+ * Limits:     1 <= d <= 64; N >= 1 (N = 0 returns KRR_OK with no work);
+ *             sigma > 0; shifts (gamma, delta) >= 0; all finite.
+ */
+#ifndef LIBKRR_H
+#define LIBKRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct krr_handle_s* krr_handle;
+
+typedef enum {
+    KRR_OK = 0,
+    KRR_ERR_INVALID_ARG = 1,   /* bad size, pointer, sigma, shift or option     */
+    KRR_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has it)   */
+    KRR_ERR_OOM = 3,           /* workspace allocation failed                   */
+    KRR_ERR_NONFINITE = 4,     /* NaN or Inf met in inputs or iterates          */
+    KRR_NOT_CONVERGED = 5,     /* iteration cap reached before the tolerance    */
+    KRR_ERR_BREAKDOWN = 6,     /* Krylov breakdown that is not a lucky one      */
+    KRR_ERR_TIMEOUT = 7,       /* a bounded device wait ran out                 */
+    KRR_ERR_UNIMPLEMENTED = 8  /* option combination not built                  */
+} krr_status;
+
+/* Arithmetic of the kernel product.  KRR_FP32 sums in float32 with a
+ * compensated (Kahan) fold across source tiles; KRR_BF16 / KRR_FP16 evaluate
+ * the kernel values at reduced precision with float32 accumulation (the
+ * low-accuracy inner product that Sec. 5.1 allows for the preconditioner). */
+typedef enum { KRR_FP32 = 0, KRR_BF16 = 1, KRR_FP16 = 2 } krr_precision;
+
+/* Options of krr_fgmres_solve (defaults from Sec. 6 in brackets).
+ * Fill with krr_fgmres_default_opts(). */
+typedef struct {
+    int restart;          /* m of FGMRES(m), 1..64                      [30]   */
+    int max_cycles;       /* restart cycles before KRR_NOT_CONVERGED     [50]   */
+    double tol;           /* outer tol on |b - K x| / |b|                [1e-6] */
+    double delta;         /* preconditioner shift; < 0: 10 gamma, or 1e-3
+                             when gamma = 0 (Sec. 6)                      [-1]   */
+    double inner_tol;     /* inner CG tol on |v - M z| / |v|; < 0: 10 tol [-1]  */
+    int inner_maxit;      /* inner CG iteration cap; 0 = no preconditioner
+                             (plain GMRES)                               [100]  */
+    krr_precision inner_prec; /* arithmetic of the inner product M p    [FP32] */
+    int use_graph;        /* 1: run the whole solve as one CUDA graph with
+                             device-side loop control; 0: host-driven loop
+                             with one status read per step               [1]    */
+} krr_fgmres_opts;
+
+/* Per-right-hand-side solver report. */
+typedef struct {
+    int outer_iters;        /* Arnoldi steps over all cycles (FGMRES) or CG
+                               iterations (krr_cg_solve)                        */
+    int inner_iters;        /* inner CG iterations in total                     */
+    int cycles;             /* restart cycles run                               */
+    int breakdowns;         /* inner p^T M p <= 0 events (inner solve cut short) */
+    double relres_est;      /* last residual estimate |g_{j+1}| / |b|           */
+    double relres_true;     /* |b - K x| / |b| from a fresh product at exit     */
+    double time_ms;         /* device time of the solve                         */
+    krr_status status;
+} krr_solve_info;
+
+/* One problem of a batched solve.  All arrays are DEVICE pointers. */
+typedef struct {
+    const float* X;   /* N x d row-major                                       */
+    const float* B;   /* N x m_rhs column-major right-hand sides               */
+    float* Xsol;      /* N x m_rhs column-major solutions (in: ignored)        */
+    int64_t N;
+    float gamma;
+} krr_problem;
+
+/* ---------------------------------------------------------------- handle */
+krr_status krr_create(krr_handle* out);
+krr_status krr_destroy(krr_handle h);
+const char* krr_last_error(krr_handle h);
+const char* krr_status_string(krr_status s);
+/* Library version as major*10000 + minor*100 + patch. */
+int krr_version(void);
+void krr_fgmres_default_opts(krr_fgmres_opts* opts);
+
+/* ----------------------------------------------------------- kernel MVP
+ * Y = (K_hat + gamma I) Q  (Eqs. 1-3; the weighted kernel sum of Sec. 3.1):
+ *     Y[i,c] = sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) Q[j,c] + gamma Q[i,c]
+ * over all N^2 pairs (no cut-off), summed on the fly in O(N) memory.
+ * X: N x d; Q, Y: N x m column-major, 1 <= m <= 64.  Y must not alias X or Q.
+ * prec: KRR_FP32 (max relative error per element, against the FP64 sum
+ * scaled by sum_j |Q_jc| K_hat_ij + gamma |Q_ic|, below 1e-5) or KRR_BF16 /
+ * KRR_FP16 (reduced-precision kernel values, float32 accumulation).
+ * Asynchronous on device arrays. */
+krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d,
+                          float sigma, float gamma, const float* Q, int m,
+                          float* Y, krr_precision prec, void* stream);
+
+/* Prediction product of Eq. GPR_mean / Eq. Kriging:
+ *     Y[t,c] = sum_j exp(-|xt_t - xs_j|^2 / (2 sigma^2)) Q[j,c]
+ * Xt: Nt x d targets, Xs: Ns x d sources, Q: Ns x m, Y: Nt x m (no diagonal
+ * term).  Asynchronous on device arrays. */
+krr_status krr_kernel_mvp_rect(krr_handle h, const float* Xt, int64_t Nt,
+                               const float* Xs, int64_t Ns, int d, float sigma,
+                               const float* Q, int m, float* Y,
+                               krr_precision prec, void* stream);
+
+/* ----------------------------------------------------------- CG solve
+ * Conjugate gradient (Sec. 3) on (K_hat + shift I) x = b: the unpreconditioned
+ * baseline when shift = gamma, the inner preconditioner solve when shift =
+ * gamma + delta.  x: in = initial guess, out = solution (length N).  Stops when
+ * |b - A x| / |b| <= tol (recursive residual) or after maxit iterations.
+ * Returns KRR_NOT_CONVERGED if the cap is reached.  If info != NULL the call
+ * waits for the solve and fills *info (relres_true from a fresh product). */
+krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d,
+                        float sigma, float shift, const float* b, float* x,
+                        double tol, int maxit, krr_precision prec,
+                        krr_solve_info* info, void* stream);
+
+/* ----------------------------------------------------------- FGMRES solve
+ * Algorithm 1 on K = K_hat + gamma I with the paper's preconditioner:
+ * truncated CG on M = K + delta I (Sec. 5), restart m, x0 = 0.  Arnoldi
+ * (modified Gram-Schmidt) and the Givens least-squares update run in FP64;
+ * the outer products K z_j and the true residual in FP32 with compensated
+ * summation; the inner products M p in opts->inner_prec.
+ * B: N x m_rhs right-hand sides, Xsol: N x m_rhs solutions (column-major),
+ * each column solved to |b - K x| / |b| <= opts->tol (true residual).
+ * opts = NULL takes the defaults.  info: NULL or an array of m_rhs reports.
+ * The call waits for the solve when info != NULL.  Returns the worst status
+ * over the columns. */
+krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d,
+                            float sigma, float gamma, const float* B, int m_rhs,
+                            float* Xsol, const krr_fgmres_opts* opts,
+                            krr_solve_info* info, void* stream);
+
+/* Many independent problems (same d, sigma, opts; own N_k, gamma_k, m_rhs
+ * right-hand sides each) solved together.  probs: HOST array of nprob
+ * krr_problem records whose arrays are DEVICE pointers.  info: NULL or
+ * nprob * m_rhs reports (problem-major).  Waits for the solve when
+ * info != NULL.  Returns the worst status. */
+krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs,
+                                    int nprob, int d, float sigma, int m_rhs,
+                                    const krr_fgmres_opts* opts,
+                                    krr_solve_info* info, void* stream);
+
+/* ----------------------------------------------------- MLL gradient
+ * Gradient of the GP log-marginal likelihood
+ *     L = -1/2 y^T K^-1 y - 1/2 log det K - N/2 log 2 pi   (Sec. 2.1 ML fit)
+ * with respect to log sigma, log gamma and the points X, using alpha = K^-1 y
+ * and u_p = K^-1 z_p (FGMRES solves) for n_probes Rademacher probes z_p drawn
+ * from SplitMix64 seeded with `seed` (element (i, p) is -1 when the top bit of
+ * output number p*N + i + 1 is set), and the Hutchinson estimate
+ * K^-1 ~ (1/P) sum_p u_p z_p^T in the trace term.
+ * dlogsigma, dloggamma: HOST doubles; dX: N x d row-major float32 (device or
+ * host), may be NULL.  Waits for the result before returning. */
+krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int d,
+                        float sigma, float gamma, const float* y, int n_probes,
+                        uint64_t seed, const krr_fgmres_opts* opts,
+                        double* dlogsigma, double* dloggamma, float* dX,
+                        krr_solve_info* info, void* stream);
+
+/* ----------------------------------------------------- diagnostics
+ * Issue-rate microbenchmarks that bound the kernel product (not part of the
+ * paper's method): results per second of MUFU.EX2 (ex2.approx.ftz.f32), of
+ * scalar FP32 FMA, and of FP32 lanes through packed f32x2 FMA, on the
+ * handle's device at its current clocks (about 10 ms of GPU time; waits for
+ * the result).  Outputs are HOST doubles; any may be NULL. */
+krr_status krr_measure_alu_peaks(krr_handle h, double* ex2_per_s, double* ffma_per_s,
+                                 double* ffma2_lanes_per_s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBKRR_H */

@@ -1,0 +1,21 @@
+// Helpers shared by the C-ABI translation units (defined in krr_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace krr {
+
+krr_status set_error(Ctx& c, krr_status s, const char* fmt, ...);
+krr_status cuda_error(Ctx& c, cudaError_t e, const char* what);
+bool is_device_ptr(const Ctx& c, const void* p);
+krr_status read_device_error(Ctx& c, cudaStream_t st, const char* what);
+krr_status check_points(Ctx& c, const char* fn, const float* X, int64_t N, int d, float sigma);
+krr_status device_view(Ctx& c, const char* slot, const float* p, size_t count, bool in,
+                       cudaStream_t st, float** out, bool* staged);
+
+}  // namespace krr
+
+struct krr_handle_s {
+  krr::Ctx ctx;
+};

@@ -1,0 +1,95 @@
+// Internal host-side interfaces of libkrr (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <unordered_map>
+
+#include "../../include/libkrr.h"
+
+namespace krr {
+
+constexpr int PAD = 2048;  // prepared arrays are padded to a multiple of PAD points
+
+inline int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Grow-only device workspace addressed by name.
+struct Workspace {
+  std::unordered_map<std::string, Buf> slots;
+  cudaError_t get(const std::string& name, size_t bytes, void** out);
+  void release_all();
+};
+
+// Targets are handled in warp blocks of WB = 32*T consecutive sorted points
+// (T targets per thread).  prep.cu computes, per warp block, the centre of its
+// bounding box and whether it is compact enough for the expanded exponent
+// form, and orders the blocks so that the expanded ones come first.
+struct PointsDev {
+  int64_t N = 0, Npad = 0;
+  int d = 0;
+  float scale = 0.f;    // s = sqrt(log2(e) / (2 sigma^2))
+  float* xs = nullptr;  // tile-blocked SoA of the raw coordinates, Npad*d floats
+  int* perm = nullptr;  // sorted position -> original index
+  int T = 1;            // targets per thread of the product kernels
+  int64_t nblk = 0;     // warp blocks: ceil(N / (32*T))
+  float* ctr = nullptr; // nblk x d block centres (raw coordinates)
+  int* order = nullptr; // nblk block indices, expanded-form blocks first
+  int* n_exp = nullptr; // device scalar: number of expanded-form blocks
+};
+
+// Targets per thread the product kernels use for N targets in d dimensions.
+int mvp_targets_per_thread(int d, int64_t N);
+// Squared radius (scaled units) up to which a warp block uses the expanded form.
+constexpr float EXPANDED_R2 = 8.0f;
+
+struct Ctx {
+  int device = 0;
+  int num_sms = 0;
+  Workspace ws;
+  int* d_err = nullptr;        // device error word (DevErr)
+  int* h_status = nullptr;     // pinned host mirror for status reads
+  std::string last_error;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// ---- prep.cu
+// Sort X (N x d row-major, device) along a Morton curve and pack the scaled,
+// tile-blocked structure-of-arrays copy.  `tag` names the workspace slots.
+cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma,
+                           const char* tag, PointsDev& P, cudaStream_t st);
+// out[i] = in[perm[i]] (float columns, m of them, column stride N / Npad);
+// padded tail of each column set to zero.
+cudaError_t gather_sorted(const float* in, int64_t N, int m, const int* perm, int64_t Npad,
+                          float* out, cudaStream_t st);
+// out[perm[i]] = in[i]
+cudaError_t scatter_orig(const float* in, int64_t Npad, int64_t N, int m, const int* perm,
+                         float* out, cudaStream_t st);
+
+// ---- mvp.cu
+struct MvpOut {
+  // y = alpha * (K_hat q + shift q) + beta * u, sorted order
+  float alpha = 1.f, beta = 0.f;
+  const float* u = nullptr;
+  float* out_f = nullptr;       // sorted-order float output (may be null)
+  double* out_d = nullptr;      // sorted-order double output (may be null)
+  const int* perm = nullptr;    // if set with out_orig: scatter to original order
+  float* out_orig = nullptr;
+  const float* dotw = nullptr;  // if set: *dot += sum_i y_i * dotw_i
+  double* dot = nullptr;
+};
+
+// Single right-hand side product over prepared targets T and sources S
+// (the same object for the square product).  q: sorted source weights
+// (length S.Npad, zero padded); qdiag: sorted target weights for the shift
+// term (may be null when shift == 0).
+cudaError_t mvp_launch(Ctx& c, const PointsDev& T, const PointsDev& S, const float* q,
+                       const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
+                       cudaStream_t st);
+
+}  // namespace krr

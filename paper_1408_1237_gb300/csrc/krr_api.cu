@@ -1,0 +1,277 @@
+// C-ABI entry points of libkrr: handle, workspace, argument checks, host
+// array staging and the kernel-product calls.  The solvers live in krylov.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "api_util.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace krr {
+
+cudaError_t Workspace::get(const std::string& name, size_t bytes, void** out) {
+  bytes = std::max<size_t>(bytes, 256);
+  auto it = slots.find(name);
+  if (it != slots.end() && it->second.bytes >= bytes) {
+    *out = it->second.p;
+    return cudaSuccess;
+  }
+  if (it != slots.end()) {
+    // cudaFree waits for the device, so work queued on the old buffer is done
+    cudaFree(it->second.p);
+    it->second = Buf{};
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  slots[name] = Buf{p, bytes};
+  *out = p;
+  return cudaSuccess;
+}
+
+void Workspace::release_all() {
+  for (auto& kv : slots) cudaFree(kv.second.p);
+  slots.clear();
+}
+
+krr_status set_error(Ctx& c, krr_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  c.last_error = buf;
+  return s;
+}
+
+krr_status cuda_error(Ctx& c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(c, KRR_ERR_OOM, "%s: out of device memory", what);
+  if (e == cudaErrorNotSupported)
+    return set_error(c, KRR_ERR_UNIMPLEMENTED, "%s: configuration not built", what);
+  return set_error(c, KRR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const Ctx& c, const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) &&
+         a.device == c.device;
+}
+
+// Read and clear the device error word (waits for `st`).
+krr_status read_device_error(Ctx& c, cudaStream_t st, const char* what) {
+  cudaError_t e = cudaMemcpyAsync(c.h_status, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_error(c, e, what);
+  const int v = *c.h_status;
+  if (v == DEV_OK) return KRR_OK;
+  cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
+  cudaStreamSynchronize(st);
+  if (v == DEV_TIMEOUT) return set_error(c, KRR_ERR_TIMEOUT, "%s: a bounded device wait ran out", what);
+  if (v == DEV_NONFINITE) return set_error(c, KRR_ERR_NONFINITE, "%s: non-finite input", what);
+  if (v == DEV_BREAKDOWN) return set_error(c, KRR_ERR_BREAKDOWN, "%s: Krylov breakdown", what);
+  return set_error(c, KRR_ERR_CUDA, "%s: device error %d", what, v);
+}
+
+krr_status check_points(Ctx& c, const char* fn, const float* X, int64_t N, int d, float sigma) {
+  if (N < 0 || N > (int64_t(1) << 30))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: N = %lld out of range [0, 2^30]", fn, (long long)N);
+  if (d < 1 || d > 64) return set_error(c, KRR_ERR_INVALID_ARG, "%s: d = %d out of range [1, 64]", fn, d);
+  if (!(sigma > 0.f) || !std::isfinite(sigma))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: sigma must be finite and > 0", fn);
+  if (N > 0 && X == nullptr) return set_error(c, KRR_ERR_INVALID_ARG, "%s: X is NULL", fn);
+  if (d > 8) return set_error(c, KRR_ERR_UNIMPLEMENTED, "%s: d = %d > 8 not built yet", fn, d);
+  return KRR_OK;
+}
+
+// Device view of a caller array: the array itself when it is on the handle's
+// device, else a staged copy in the workspace (copied in when `in`).
+krr_status device_view(Ctx& c, const char* slot, const float* p, size_t count, bool in,
+                       cudaStream_t st, float** out, bool* staged) {
+  if (p == nullptr || count == 0 || is_device_ptr(c, p)) {
+    *out = const_cast<float*>(p);
+    *staged = false;
+    return KRR_OK;
+  }
+  void* d;
+  cudaError_t e = c.ws.get(slot, count * sizeof(float), &d);
+  if (e) return cuda_error(c, e, slot);
+  if (in && (e = cudaMemcpyAsync(d, p, count * sizeof(float), cudaMemcpyHostToDevice, st)))
+    return cuda_error(c, e, slot);
+  *out = (float*)d;
+  *staged = true;
+  return KRR_OK;
+}
+
+}  // namespace krr
+
+using namespace krr;
+
+extern "C" {
+
+int krr_version(void) { return 100; }
+
+const char* krr_status_string(krr_status s) {
+  switch (s) {
+    case KRR_OK: return "KRR_OK";
+    case KRR_ERR_INVALID_ARG: return "KRR_ERR_INVALID_ARG";
+    case KRR_ERR_CUDA: return "KRR_ERR_CUDA";
+    case KRR_ERR_OOM: return "KRR_ERR_OOM";
+    case KRR_ERR_NONFINITE: return "KRR_ERR_NONFINITE";
+    case KRR_NOT_CONVERGED: return "KRR_NOT_CONVERGED";
+    case KRR_ERR_BREAKDOWN: return "KRR_ERR_BREAKDOWN";
+    case KRR_ERR_TIMEOUT: return "KRR_ERR_TIMEOUT";
+    case KRR_ERR_UNIMPLEMENTED: return "KRR_ERR_UNIMPLEMENTED";
+  }
+  return "KRR_UNKNOWN";
+}
+
+void krr_fgmres_default_opts(krr_fgmres_opts* o) {
+  if (!o) return;
+  o->restart = 30;
+  o->max_cycles = 50;
+  o->tol = 1e-6;
+  o->delta = -1.0;
+  o->inner_tol = -1.0;
+  o->inner_maxit = 100;
+  o->inner_prec = KRR_FP32;
+  o->use_graph = 1;
+}
+
+krr_status krr_create(krr_handle* out) {
+  if (!out) return KRR_ERR_INVALID_ARG;
+  *out = nullptr;
+  krr_handle h = new (std::nothrow) krr_handle_s();
+  if (!h) return KRR_ERR_OOM;
+  Ctx& c = h->ctx;
+  cudaError_t e = cudaGetDevice(&c.device);
+  if (!e) e = cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device);
+  if (!e) e = cudaMalloc(&c.d_err, sizeof(int));
+  if (!e) e = cudaMemset(c.d_err, 0, sizeof(int));
+  if (!e) e = cudaMallocHost(&c.h_status, 64 * sizeof(int));
+  if (!e) e = cudaEventCreate(&c.ev0);
+  if (!e) e = cudaEventCreate(&c.ev1);
+  if (e) {
+    cudaGetLastError();
+    if (c.d_err) cudaFree(c.d_err);
+    if (c.h_status) cudaFreeHost(c.h_status);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? KRR_ERR_OOM : KRR_ERR_CUDA;
+  }
+  *out = h;
+  return KRR_OK;
+}
+
+krr_status krr_destroy(krr_handle h) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  cudaDeviceSynchronize();
+  c.ws.release_all();
+  cudaFree(c.d_err);
+  cudaFreeHost(c.h_status);
+  cudaEventDestroy(c.ev0);
+  cudaEventDestroy(c.ev1);
+  delete h;
+  return KRR_OK;
+}
+
+const char* krr_last_error(krr_handle h) { return h ? h->ctx.last_error.c_str() : "NULL handle"; }
+
+krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float sigma, float gamma,
+                          const float* Q, int m, float* Y, krr_precision prec, void* stream) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  const char* fn = "krr_kernel_mvp";
+  krr_status s = check_points(c, fn, X, N, d, sigma);
+  if (s) return s;
+  if (!(gamma >= 0.f) || !std::isfinite(gamma))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: gamma must be finite and >= 0", fn);
+  if (m < 1 || m > 64) return set_error(c, KRR_ERR_INVALID_ARG, "%s: m = %d out of range [1, 64]", fn, m);
+  if (prec != KRR_FP32 && prec != KRR_BF16 && prec != KRR_FP16)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: unknown precision %d", fn, (int)prec);
+  if (N == 0) return KRR_OK;
+  if (!Q || !Y) return set_error(c, KRR_ERR_INVALID_ARG, "%s: Q or Y is NULL", fn);
+  if (Y == Q || (const void*)Y == (const void*)X)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: Y aliases an input", fn);
+  cudaStream_t st = (cudaStream_t)stream;
+  float *dX, *dQ, *dY;
+  bool sX, sQ, sY;
+  if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
+  if ((s = device_view(c, "stage.Q", Q, (size_t)N * m, true, st, &dQ, &sQ))) return s;
+  if ((s = device_view(c, "stage.Y", Y, (size_t)N * m, false, st, &dY, &sY))) return s;
+  PointsDev P;
+  cudaError_t e = prepare_points(c, dX, N, d, sigma, "pts", P, st);
+  if (e) return cuda_error(c, e, fn);
+  void* qs;
+  if ((e = c.ws.get("mvp.qs", sizeof(float) * P.Npad * m, &qs))) return cuda_error(c, e, fn);
+  if ((e = gather_sorted(dQ, N, m, P.perm, P.Npad, (float*)qs, st))) return cuda_error(c, e, fn);
+  for (int col = 0; col < m; ++col) {
+    const float* qc = (const float*)qs + (size_t)col * P.Npad;
+    MvpOut o;
+    o.perm = P.perm;
+    o.out_orig = dY + (size_t)col * N;
+    if ((e = mvp_launch(c, P, P, qc, qc, gamma, prec, o, st))) return cuda_error(c, e, fn);
+  }
+  if (sY) {
+    if ((e = cudaMemcpyAsync(Y, dY, sizeof(float) * N * m, cudaMemcpyDeviceToHost, st)))
+      return cuda_error(c, e, fn);
+  }
+  if (sX || sQ || sY) return read_device_error(c, st, fn);
+  return KRR_OK;
+}
+
+krr_status krr_kernel_mvp_rect(krr_handle h, const float* Xt, int64_t Nt, const float* Xs,
+                               int64_t Ns, int d, float sigma, const float* Q, int m, float* Y,
+                               krr_precision prec, void* stream) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  const char* fn = "krr_kernel_mvp_rect";
+  krr_status s = check_points(c, fn, Xt, Nt, d, sigma);
+  if (s) return s;
+  if ((s = check_points(c, fn, Xs, Ns, d, sigma))) return s;
+  if (m < 1 || m > 64) return set_error(c, KRR_ERR_INVALID_ARG, "%s: m = %d out of range [1, 64]", fn, m);
+  if (Nt == 0) return KRR_OK;
+  if (!Y) return set_error(c, KRR_ERR_INVALID_ARG, "%s: Y is NULL", fn);
+  cudaStream_t st = (cudaStream_t)stream;
+  float *dXt, *dXs, *dQ, *dY;
+  bool s1, s2, s3, s4;
+  if ((s = device_view(c, "stage.Xt", Xt, (size_t)Nt * d, true, st, &dXt, &s1))) return s;
+  if ((s = device_view(c, "stage.Xs", Xs, (size_t)Ns * d, true, st, &dXs, &s2))) return s;
+  if ((s = device_view(c, "stage.Q", Q, (size_t)Ns * m, true, st, &dQ, &s3))) return s;
+  if ((s = device_view(c, "stage.Y", Y, (size_t)Nt * m, false, st, &dY, &s4))) return s;
+  cudaError_t e;
+  if (Ns == 0) {
+    if ((e = cudaMemsetAsync(dY, 0, sizeof(float) * Nt * m, st))) return cuda_error(c, e, fn);
+  } else {
+    if (!Q) return set_error(c, KRR_ERR_INVALID_ARG, "%s: Q is NULL", fn);
+    PointsDev T, S;
+    if ((e = prepare_points(c, dXt, Nt, d, sigma, "pts_t", T, st))) return cuda_error(c, e, fn);
+    if ((e = prepare_points(c, dXs, Ns, d, sigma, "pts_s", S, st))) return cuda_error(c, e, fn);
+    void* qs;
+    if ((e = c.ws.get("mvp.qs", sizeof(float) * S.Npad * m, &qs))) return cuda_error(c, e, fn);
+    if ((e = gather_sorted(dQ, Ns, m, S.perm, S.Npad, (float*)qs, st))) return cuda_error(c, e, fn);
+    for (int col = 0; col < m; ++col) {
+      MvpOut o;
+      o.perm = T.perm;
+      o.out_orig = dY + (size_t)col * Nt;
+      if ((e = mvp_launch(c, T, S, (const float*)qs + (size_t)col * S.Npad, nullptr, 0.f, prec, o, st)))
+        return cuda_error(c, e, fn);
+    }
+  }
+  if (s4 && (e = cudaMemcpyAsync(Y, dY, sizeof(float) * Nt * m, cudaMemcpyDeviceToHost, st)))
+    return cuda_error(c, e, fn);
+  if (s1 || s2 || s3 || s4) return read_device_error(c, st, fn);
+  return KRR_OK;
+}
+
+}  // extern "C"

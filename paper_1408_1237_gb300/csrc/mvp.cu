@@ -1,0 +1,481 @@
+// On-the-fly Gaussian kernel product (hot-path steps A2/A4/A6):
+//
+//   y_i = sum_j q_j exp(-|x_i - x_j|^2 / (2 sigma^2)) + shift q_i
+//
+// (Eqs. 1-3; the weighted kernel sum of Sec. 3.1, computed on the fly in O(N)
+// memory).  Points arrive prepared by prep.cu: Morton-sorted, unscaled; with
+// s = sqrt(log2(e) / (2 sigma^2)) a kernel value is 2^(-s^2 |x_i - x_j|^2).
+//
+// Kernel design:
+//  * Targets are processed in warp blocks of WB = 32*T consecutive sorted
+//    points (T per thread, held in registers); a CTA has 8 warps, each on its
+//    own warp block, and a grid row y covers one contiguous range of source
+//    tiles (source splitting balances the grid over the 152 SMs).
+//  * Expanded form, for warp blocks within squared radius EXPANDED_R2 of
+//    their centre c in scaled units x^ = s (x - c):
+//      -|x^_i - x^_j|^2 = -|x^_i|^2 + (b_j + sum_k x^_ik (2 x^_jk)),
+//    b_j = -|x^_j|^2, and 2^(-|x^_i|^2) is factored out of the sum, so a pair
+//    costs d FMAs for the exponent, one MUFU.EX2 and one FMA.  The factored
+//    exponent never exceeds |x^_i|^2 <= EXPANDED_R2, so nothing overflows; its
+//    rounding error is a few ulps of EXPANDED_R2.  x - c is formed from the raw
+//    float32 coordinates, so recentring loses no digits.
+//  * Direct form (warp blocks that are not compact): d subtractions of the raw
+//    coordinates (exact for near pairs), d multiply-adds, one multiply by
+//    -s^2, one MUFU.EX2, one FMA.
+//  * prep.cu orders the warp blocks expanded-first, so every CTA but one runs a
+//    single form and its warps stay in step.
+//  * Source tiles (TS points: d coordinates + weights, contiguous in the
+//    tile-blocked layout) arrive by 1-D TMA bulk copies in a RS-stage
+//    shared-memory ring (mbarrier completion, bounded waits); each warp then
+//    transforms the tile for its own centre into a private shared buffer.
+//  * Two sources share each packed f32x2 FMA (FFMA2/FADD2/FMUL2).
+//  * Per-tile float32 partial sums are folded with Kahan compensation; each
+//    source split writes one FP64 partial per target, and a finalize kernel
+//    adds the splits in fixed order (deterministic), applies 2^(-|x^_i|^2), the
+//    shift term and the fused epilogue (axpy, dot, scatter).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace krr {
+
+namespace {
+
+constexpr int NT = 256;   // threads per CTA: 8 warps
+constexpr int NW = NT / 32;
+
+template <int D>
+constexpr int raw_stages() { return D >= 8 ? 3 : 4; }
+
+struct MvpParams {
+  const float* xt;      // targets, tile-blocked SoA (raw coordinates)
+  int64_t Nt, Nt_pad;
+  const float* tctr;    // target warp-block centres [nblk][D]
+  const int* torder;    // warp blocks, expanded-form first
+  const int* tn_exp;    // number of expanded-form warp blocks
+  int64_t nblk;
+  const float* xs;      // sources, tile-blocked SoA (raw coordinates)
+  const float* q;       // source weights, sorted order, zero padded
+  int ntiles;           // source tiles
+  int tiles_per_split;
+  double* part;         // [splits][Nt_pad]
+  float* fac;           // [Nt_pad] factored scale 2^(-|x^_i|^2) (1 for the direct form)
+  int* err;
+  float s;              // sqrt(log2(e) / (2 sigma^2))
+};
+
+// Warp-cooperative transform of one raw source tile for this warp's centre:
+// expanded form -> (2 x^_j, b_j = -|x^_j|^2, q_j); direct form -> (-x_j, q_j).
+template <int D>
+__device__ __forceinline__ void transform_tile(const float* __restrict__ rs, float* __restrict__ wb,
+                                               const float (&ctr)[D], float s, bool expanded) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < TS / 32; ++v) {
+    const int j = lane + 32 * v;
+    if (expanded) {
+      float xh[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) xh[k] = s * (rs[k * TS + j] - ctr[k]);
+      float b = -(xh[0] * xh[0]);
+#pragma unroll
+      for (int k = 1; k < D; ++k) b = fmaf(-xh[k], xh[k], b);
+#pragma unroll
+      for (int k = 0; k < D; ++k) wb[k * TS + j] = 2.f * xh[k];
+      wb[D * TS + j] = b;
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) wb[k * TS + j] = -rs[k * TS + j];
+    }
+    wb[(D + 1) * TS + j] = rs[D * TS + j];
+  }
+}
+
+template <int D, int T>
+__device__ __forceinline__ void compute_expanded(const float* __restrict__ cb,
+                                                 const float2 (&tx)[T][D], float2 (&acc)[T]) {
+  const float* cX = cb;
+  const float* cB = cb + D * TS;
+  const float* cQ = cb + (D + 1) * TS;
+#pragma unroll 2
+  for (int j = 0; j < TS; j += 4) {
+    float4 xk[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xk[k] = *reinterpret_cast<const float4*>(cX + k * TS + j);
+    const float4 bb = *reinterpret_cast<const float4*>(cB + j);
+    const float4 qq = *reinterpret_cast<const float4*>(cQ + j);
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+      float2 e0 = make_float2(bb.x, bb.y), e1 = make_float2(bb.z, bb.w);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        e0 = ffma2(tx[u][k], make_float2(xk[k].x, xk[k].y), e0);
+        e1 = ffma2(tx[u][k], make_float2(xk[k].z, xk[k].w), e1);
+      }
+      e0.x = ex2(e0.x);
+      e0.y = ex2(e0.y);
+      e1.x = ex2(e1.x);
+      e1.y = ex2(e1.y);
+      acc[u] = ffma2(make_float2(qq.x, qq.y), e0, acc[u]);
+      acc[u] = ffma2(make_float2(qq.z, qq.w), e1, acc[u]);
+    }
+  }
+}
+
+template <int D, int T>
+__device__ __forceinline__ void compute_direct(const float* __restrict__ cb,
+                                               const float2 (&tx)[T][D], float2 (&acc)[T],
+                                               float s2) {
+  const float* cX = cb;  // holds -x_j (raw)
+  const float* cQ = cb + (D + 1) * TS;
+  const float2 ns2 = make_float2(-s2, -s2);
+#pragma unroll 2
+  for (int j = 0; j < TS; j += 4) {
+    float4 xk[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xk[k] = *reinterpret_cast<const float4*>(cX + k * TS + j);
+    const float4 qq = *reinterpret_cast<const float4*>(cQ + j);
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+      float2 d0 = fadd2(tx[u][0], make_float2(xk[0].x, xk[0].y));
+      float2 d1 = fadd2(tx[u][0], make_float2(xk[0].z, xk[0].w));
+      float2 r0 = fmul2(d0, d0), r1 = fmul2(d1, d1);
+#pragma unroll
+      for (int k = 1; k < D; ++k) {
+        d0 = fadd2(tx[u][k], make_float2(xk[k].x, xk[k].y));
+        d1 = fadd2(tx[u][k], make_float2(xk[k].z, xk[k].w));
+        r0 = ffma2(d0, d0, r0);
+        r1 = ffma2(d1, d1, r1);
+      }
+      r0 = fmul2(r0, ns2);
+      r1 = fmul2(r1, ns2);
+      float2 e0, e1;
+      e0.x = ex2(r0.x);
+      e0.y = ex2(r0.y);
+      e1.x = ex2(r1.x);
+      e1.y = ex2(r1.y);
+      acc[u] = ffma2(make_float2(qq.x, qq.y), e0, acc[u]);
+      acc[u] = ffma2(make_float2(qq.z, qq.w), e1, acc[u]);
+    }
+  }
+}
+
+template <int D, int T>
+__global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
+  constexpr int RS = raw_stages<D>();
+  constexpr uint32_t kRawFloats = (D + 1) * TS;
+  constexpr uint32_t kWbFloats = (D + 2) * TS;
+  extern __shared__ __align__(128) float smem[];
+  float* raw = smem;                                   // RS * (D+1) * TS
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* wbuf = smem + RS * kRawFloats + warp * kWbFloats;  // this warp's (D+2) * TS
+  __shared__ __align__(8) uint64_t bars[RS];
+  __shared__ volatile int abort_flag;
+
+  // ---- this warp's target block
+  const int64_t slot = (int64_t)blockIdx.x * NW + warp;
+  const bool live = slot < p.nblk;
+  const int64_t blk = live ? p.torder[slot] : 0;
+  const int64_t last = min(((int64_t)blockIdx.x + 1) * NW, p.nblk);  // CTA's block slots end
+  const bool expanded = last <= (int64_t)(*p.tn_exp);  // uniform over the CTA
+  float ctr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
+
+  float2 tx[T][D];
+  float r2[T];
+#pragma unroll
+  for (int u = 0; u < T; ++u) {
+    const int64_t i = blk * 32 * T + lane + 32 * u;
+    const bool inmem = live && i < p.Nt_pad;
+    const int64_t base = (i / TS) * (int64_t)D * TS + (i % TS);
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float x = inmem ? p.xt[base + (int64_t)k * TS] : ctr[k];
+      const float xh = p.s * (x - ctr[k]);
+      a = fmaf(xh, xh, a);
+      const float v = expanded ? xh : x;
+      tx[u][k] = make_float2(v, v);
+    }
+    r2[u] = a;
+  }
+  if (blockIdx.y == 0 && live) {
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+      const int64_t i = blk * 32 * T + lane + 32 * u;
+      if (i < p.Nt_pad) p.fac[i] = expanded ? exp2f(-r2[u]) : 1.f;
+    }
+  }
+  const float s2 = p.s * p.s;
+
+  // ---- source range of this split
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+
+  float sum[T], comp[T];
+  float2 acc[T];
+#pragma unroll
+  for (int u = 0; u < T; ++u) {
+    sum[u] = comp[u] = 0.f;
+    acc[u] = make_float2(0.f, 0.f);
+  }
+
+  auto issue = [&](int r) {
+    const int stage = r % RS;
+    const int64_t tile = t_begin + r;
+    float* dst = raw + stage * kRawFloats;
+    mbar_arrive_expect_tx(&bars[stage], kRawFloats * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS, p.q + tile * (int64_t)TS, TS * 4, &bars[stage]);
+  };
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < RS; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RS, nt); ++issued) issue(issued);
+
+  for (int r = 0; r < nt; ++r) {
+    // stage (r-1) % RS was released by the barrier that ended iteration r-1
+    if (tid == 0 && r >= 1 && r - 1 + RS < nt) {
+      fence_proxy_async_smem();
+      issue(r - 1 + RS);
+      ++issued;
+    }
+    // warp-uniform outcome: a lane that gave up takes its whole warp with it
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[r % RS], (r / RS) & 1));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    } else {
+      transform_tile<D>(raw + (r % RS) * kRawFloats, wbuf, ctr, p.s, expanded);
+      __syncwarp();
+      if (expanded)
+        compute_expanded<D, T>(wbuf, tx, acc);
+      else
+        compute_direct<D, T>(wbuf, tx, acc, s2);
+#pragma unroll
+      for (int u = 0; u < T; ++u) {
+        kahan_add(sum[u], comp[u], acc[u].x + acc[u].y);
+        acc[u] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  if (abort_flag) {
+    // drain copies still in flight before the CTA's shared memory is released
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RS], (r / RS) & 1);
+    __syncthreads();
+    return;
+  }
+
+  if (live) {
+    double* part = p.part + (int64_t)blockIdx.y * p.Nt_pad;
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+      const int64_t i = blk * 32 * T + lane + 32 * u;
+      if (i < p.Nt_pad) part[i] = (double)sum[u] - (double)comp[u];
+    }
+  }
+}
+
+struct FinParams {
+  const double* part;
+  int splits;
+  int64_t N, Npad;
+  const float* fac;
+  const float* qdiag;
+  float shift;
+  MvpOut o;
+  double* dot_part;        // [gridDim.x] per-block dot partials
+  unsigned int* dot_count; // arrival counter (reset by the last block)
+};
+
+__global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
+  __shared__ double red[8];
+  __shared__ bool is_last;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double out = 0.0, dotv = 0.0;
+  if (i < f.N) {
+    double s = 0.0;
+    for (int sp = 0; sp < f.splits; ++sp) s += f.part[(int64_t)sp * f.Npad + i];
+    double y = (double)f.fac[i] * s;
+    if (f.qdiag) y += (double)f.shift * (double)f.qdiag[i];
+    out = (double)f.o.alpha * y;
+    if (f.o.u) out += (double)f.o.beta * (double)f.o.u[i];
+    if (f.o.out_orig) f.o.out_orig[f.o.perm[i]] = (float)out;
+    if (f.o.dotw) dotv = out * (double)f.o.dotw[i];
+  }
+  if (i < f.Npad) {
+    if (f.o.out_f) f.o.out_f[i] = (float)out;
+    if (f.o.out_d) f.o.out_d[i] = out;
+  }
+  if (f.o.dot) {
+    const double bs = block_sum(dotv, red);
+    if (threadIdx.x == 0) {
+      f.dot_part[blockIdx.x] = bs;
+      __threadfence();
+      is_last = atomicAdd(f.dot_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      double t = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += f.dot_part[b];
+      t = block_sum(t, red);
+      if (threadIdx.x == 0) {
+        *f.o.dot += t;
+        *f.dot_count = 0u;
+      }
+    }
+  }
+}
+
+template <int D, int T>
+cudaError_t launch_typed(const MvpParams& p, int splits, cudaStream_t st) {
+  constexpr int RS = raw_stages<D>();
+  const size_t shm = sizeof(float) * (RS * (D + 1) * TS + NW * (D + 2) * TS);
+  cudaError_t e = cudaFuncSetAttribute(mvp_f32_kernel<D, T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e) return e;
+  dim3 grid((unsigned)((p.nblk + NW - 1) / NW), (unsigned)splits);
+  mvp_f32_kernel<D, T><<<grid, NT, shm, st>>>(p);
+  return cudaGetLastError();
+}
+
+// Split count minimising the makespan ceil(blocks*S/slots) * ceil(tiles/S).
+int choose_splits(int64_t blocks, int tiles, int slots) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (int s = 1; s <= std::min(tiles, 64); ++s) {
+    const double waves = std::ceil((double)blocks * s / slots);
+    const double cost = waves * std::ceil((double)tiles / s);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = s;
+    }
+  }
+  return best;
+}
+
+template <int D>
+constexpr int large_T() {
+  // targets per thread of the large variant (register budget of 128)
+  return (D <= 3) ? 8 : (D <= 5 ? 4 : 2);
+}
+
+int large_T_of(int d) {
+  switch (d) {
+    case 1: return large_T<1>();
+    case 2: return large_T<2>();
+    case 3: return large_T<3>();
+    case 4: return large_T<4>();
+    case 5: return large_T<5>();
+    case 6: return large_T<6>();
+    case 7: return large_T<7>();
+    default: return large_T<8>();
+  }
+}
+
+struct Plan {
+  int splits = 1;
+  int tiles_per_split = 1;
+};
+
+Plan make_plan(int64_t nblk, int ntiles, int num_sms) {
+  const int slots = num_sms * 2;
+  const int64_t ctas = (nblk + NW - 1) / NW;
+  Plan pl;
+  const int splits = choose_splits(ctas, ntiles, slots);
+  pl.tiles_per_split = (ntiles + splits - 1) / splits;
+  pl.splits = (ntiles + pl.tiles_per_split - 1) / pl.tiles_per_split;
+  return pl;
+}
+
+template <int D>
+cudaError_t dispatch_T(MvpParams p, int T, const Plan& pl, cudaStream_t st) {
+  constexpr int TL = large_T<D>();
+  p.tiles_per_split = pl.tiles_per_split;
+  if (T == TL) return launch_typed<D, TL>(p, pl.splits, st);
+  if (T == 1) return launch_typed<D, 1>(p, pl.splits, st);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace
+
+int mvp_targets_per_thread(int d, int64_t N) {
+  // the large-T variant amortises shared-memory loads over more pairs; T = 1
+  // gives small problems enough CTAs
+  const int TL = large_T_of(d);
+  return (N / (256LL * TL) >= 32) ? TL : 1;
+}
+
+cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
+                       const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
+                       cudaStream_t st) {
+  (void)prec;
+  if (Tp.N == 0) return cudaSuccess;
+  MvpParams p{};
+  p.xt = Tp.xs;
+  p.Nt = Tp.N;
+  p.Nt_pad = Tp.Npad;
+  p.tctr = Tp.ctr;
+  p.torder = Tp.order;
+  p.tn_exp = Tp.n_exp;
+  p.nblk = Tp.nblk;
+  p.xs = Sp.xs;
+  p.q = q;
+  p.ntiles = (int)(Sp.Npad / TS);
+  p.s = Sp.scale;
+  p.err = c.d_err;
+  if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
+  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms);
+  void *part, *fac, *dpart, *dcnt;
+  cudaError_t e;
+  if ((e = c.ws.get("mvp.part", sizeof(double) * pl.splits * (size_t)Tp.Npad, &part))) return e;
+  if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &fac))) return e;
+  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
+  const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &dcnt))) return e;
+  if (fresh && (e = cudaMemsetAsync(dcnt, 0, sizeof(unsigned), st))) return e;
+  p.part = (double*)part;
+  p.fac = (float*)fac;
+  const int splits = pl.splits;
+  switch (Tp.d) {
+    case 1: e = dispatch_T<1>(p, Tp.T, pl, st); break;
+    case 2: e = dispatch_T<2>(p, Tp.T, pl, st); break;
+    case 3: e = dispatch_T<3>(p, Tp.T, pl, st); break;
+    case 4: e = dispatch_T<4>(p, Tp.T, pl, st); break;
+    case 5: e = dispatch_T<5>(p, Tp.T, pl, st); break;
+    case 6: e = dispatch_T<6>(p, Tp.T, pl, st); break;
+    case 7: e = dispatch_T<7>(p, Tp.T, pl, st); break;
+    case 8: e = dispatch_T<8>(p, Tp.T, pl, st); break;
+    default: return cudaErrorNotSupported;
+  }
+  if (e) return e;
+  FinParams f{};
+  f.part = p.part;
+  f.splits = splits;
+  f.N = Tp.N;
+  f.Npad = Tp.Npad;
+  f.fac = p.fac;
+  f.qdiag = qdiag;
+  f.shift = shift;
+  f.o = o;
+  f.dot_part = (double*)dpart;
+  f.dot_count = (unsigned*)dcnt;
+  mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f);
+  return cudaGetLastError();
+}
+
+}  // namespace krr

@@ -1,0 +1,151 @@
+"""GPU parity of the kernel product against the FP64 oracle (Eqs. 1-3).
+
+Error measure (the FP32 bar is 1e-5): per element, |y_i - y*_i| divided by the
+natural summation scale sum_j |q_j| K_hat_ij + gamma |q_i| (so rows whose
+signed sum nearly cancels are judged against the size of what was summed).
+Small cases compare every element; the full-size 2^20-point cloud compares a
+seeded sample of rows, each summed by the oracle over all 2^20 sources.
+"""
+import numpy as np
+import pytest
+
+from paper_1408_1237_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def K():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1408_1237_gb300 import binding
+    return binding
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def scaled_error(oracle_mod, X, q, y, sigma, gamma, rows=None):
+    X64 = X.astype(np.float64)
+    q64 = q.astype(np.float64)
+    ref = oracle_mod.mvp(X64, q64, sigma, gamma, rows=rows)
+    scale = oracle_mod.mvp(X64, np.abs(q64), sigma, gamma, rows=rows)
+    yy = y if rows is None else y[rows]
+    return float(np.max(np.abs(yy.astype(np.float64) - ref) / scale))
+
+
+@pytest.mark.parametrize("N,d", [(1, 1), (2, 3), (31, 2), (257, 3), (2000, 2), (2049, 3),
+                                 (3001, 4), (1500, 5), (4097, 8), (777, 7), (600, 6), (5000, 1)])
+def test_mvp_fp32_parity_small(K, oracle_mod, N, d):
+    rng = np.random.default_rng(N * 10 + d)
+    X = rng.random((N, d)).astype(np.float32)
+    q = rng.standard_normal(N).astype(np.float32)
+    sigma, gamma = 0.15, 1e-2
+    y = K.krr_kernel_mvp(_dev(X), _dev(q), sigma, gamma).cpu().numpy()
+    assert scaled_error(oracle_mod, X, q, y, sigma, gamma) <= TOL_FP32
+
+
+@pytest.mark.parametrize("sigma", [0.002, 0.03, 0.5, 5.0])
+def test_mvp_fp32_bandwidths(K, oracle_mod, sigma):
+    # tiny sigma: blocks are wide in scaled units -> direct form; large sigma:
+    # expanded form everywhere.  Both must meet the bar.
+    p = inputs.mvp_problem(seed=3, N=6000, d=3)
+    y = K.krr_kernel_mvp(_dev(p["X"]), _dev(p["Q"]), sigma, 1e-3).cpu().numpy()
+    assert scaled_error(oracle_mod, p["X"], p["Q"], y, sigma, 1e-3) <= TOL_FP32
+
+
+def test_mvp_fp32_mixture_cloud(K, oracle_mod):
+    p = inputs.mixture_problem(seed=1, N=20000)
+    q = np.random.default_rng(5).standard_normal(20000).astype(np.float32)
+    y = K.krr_kernel_mvp(_dev(p["X"]), _dev(q), p["sigma"], p["gamma"]).cpu().numpy()
+    rows = inputs.sample_rows(20000, 3000, seed=6)
+    assert scaled_error(oracle_mod, p["X"], q, y, p["sigma"], p["gamma"], rows) <= TOL_FP32
+
+
+def test_mvp_fp32_full_size_sampled(K, oracle_mod):
+    # The 2^20-point unit-cube cloud at sigma 0.05 (the product benchmark).
+    p = inputs.mvp_problem(seed=0)
+    y = K.krr_kernel_mvp(_dev(p["X"]), _dev(p["Q"]), p["sigma"], p["gamma"]).cpu().numpy()
+    rows = inputs.sample_rows(p["X"].shape[0], 256, seed=7)
+    assert scaled_error(oracle_mod, p["X"], p["Q"], y, p["sigma"], p["gamma"], rows) <= TOL_FP32
+
+
+def test_mvp_multi_column(K, oracle_mod):
+    rng = np.random.default_rng(11)
+    N, m = 3000, 5
+    X = rng.random((N, 3)).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    Y = K.krr_kernel_mvp(_dev(X), _dev(Q), 0.1, 0.02).cpu().numpy()
+    for c in range(m):
+        assert scaled_error(oracle_mod, X, Q[c], Y[c], 0.1, 0.02) <= TOL_FP32
+
+
+def test_mvp_host_arrays_match_device_arrays(K):
+    rng = np.random.default_rng(12)
+    X = rng.random((4000, 2)).astype(np.float32)
+    q = rng.standard_normal(4000).astype(np.float32)
+    y_host = K.krr_kernel_mvp(X, q, 0.05, 1e-3)
+    y_dev = K.krr_kernel_mvp(_dev(X), _dev(q), 0.05, 1e-3).cpu().numpy()
+    assert isinstance(y_host, np.ndarray)
+    np.testing.assert_array_equal(y_host, y_dev)
+
+
+def test_mvp_deterministic(K):
+    p = inputs.mvp_problem(seed=2, N=50000, d=3)
+    X, q = _dev(p["X"]), _dev(p["Q"])
+    y1 = K.krr_kernel_mvp(X, q, p["sigma"], p["gamma"]).cpu().numpy()
+    y2 = K.krr_kernel_mvp(X, q, p["sigma"], p["gamma"]).cpu().numpy()
+    np.testing.assert_array_equal(y1, y2)
+
+
+def test_mvp_degenerate_inputs(K, oracle_mod):
+    # all points identical: K_hat = ones, y = (sum q) + gamma q
+    X = np.full((1000, 3), 0.25, dtype=np.float32)
+    q = np.random.default_rng(13).standard_normal(1000).astype(np.float32)
+    y = K.krr_kernel_mvp(_dev(X), _dev(q), 0.1, 0.5).cpu().numpy()
+    assert scaled_error(oracle_mod, X, q, y, 0.1, 0.5) <= TOL_FP32
+    # N = 0 is a no-op
+    import torch
+    e = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    K.krr_kernel_mvp(e, torch.empty(0, device="cuda"), 0.1, 0.5)
+
+
+def test_mvp_rect_prediction(K, oracle_mod):
+    rng = np.random.default_rng(14)
+    Xs = rng.random((5000, 2)).astype(np.float32)
+    Xt = rng.random((1234, 2)).astype(np.float32)
+    q = rng.standard_normal(5000).astype(np.float32)
+    y = K.krr_kernel_mvp_rect(_dev(Xt), _dev(Xs), _dev(q), 0.05).cpu().numpy()
+    ref = oracle_mod.mvp_rect(Xt.astype(np.float64), Xs.astype(np.float64), q.astype(np.float64), 0.05)
+    scale = oracle_mod.mvp_rect(Xt.astype(np.float64), Xs.astype(np.float64),
+                                np.abs(q.astype(np.float64)), 0.05)
+    assert np.max(np.abs(y - ref) / np.maximum(scale, 1e-30)) <= TOL_FP32
+
+
+def test_invalid_arguments_rejected(K):
+    import torch
+    X = torch.rand((10, 3), device="cuda")
+    q = torch.rand(10, device="cuda")
+    for sigma, gamma in [(0.0, 0.1), (-1.0, 0.1), (float("nan"), 0.1), (0.1, -1.0)]:
+        with pytest.raises(K.KrrError) as ei:
+            K.krr_kernel_mvp(X, q, sigma, gamma)
+        assert ei.value.status == K.KRR_ERR_INVALID_ARG
+    with pytest.raises(K.KrrError) as ei:
+        K.krr_kernel_mvp(torch.rand((10, 65), device="cuda"), q, 0.1, 0.1)
+    assert ei.value.status == K.KRR_ERR_INVALID_ARG
+
+
+def test_nonfinite_input_reported(K):
+    X = np.random.default_rng(15).random((100, 2)).astype(np.float32)
+    X[7, 1] = np.nan
+    q = np.ones(100, dtype=np.float32)
+    with pytest.raises(K.KrrError) as ei:
+        K.krr_kernel_mvp(X, q, 0.1, 0.1)  # host arrays: the call waits and reports
+    assert ei.value.status == K.KRR_ERR_NONFINITE
