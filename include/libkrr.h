@@ -12,8 +12,11 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Arrays:     X is N x d row-major float32 (point i at X[i*d .. i*d+d-1]).
- *             Multi-column arrays (Q, Y, B, Xsol) are N x m column-major
- *             float32: column c starts at element c*N.
+ *             Multi-column arrays (Q, Y, B, Xsol) are N x m column-major:
+ *             column c starts at element c*N.  Inputs are float32; solver
+ *             solutions are FP64 (the iterate is carried in float-float, and
+ *             rounding it to float32 alone can cost more than a 1e-6 relative
+ *             residual when K is ill-conditioned).
  * Pointers:   array pointers may be DEVICE pointers (cudaMalloc / PyTorch
  *             tensors on the handle's device) or HOST pointers (pageable or
  *             pinned).  Host arrays are staged through the handle's device
@@ -99,7 +102,7 @@ typedef struct {
 typedef struct {
     const float* X;   /* N x d row-major                                       */
     const float* B;   /* N x m_rhs column-major right-hand sides               */
-    float* Xsol;      /* N x m_rhs column-major solutions (in: ignored)        */
+    double* Xsol;     /* N x m_rhs column-major FP64 solutions (in: ignored)   */
     int64_t N;
     float gamma;
 } krr_problem;
@@ -138,12 +141,13 @@ krr_status krr_kernel_mvp_rect(krr_handle h, const float* Xt, int64_t Nt,
 /* ----------------------------------------------------------- CG solve
  * Conjugate gradient (Sec. 3) on (K_hat + shift I) x = b: the unpreconditioned
  * baseline when shift = gamma, the inner preconditioner solve when shift =
- * gamma + delta.  x: in = initial guess, out = solution (length N).  Stops when
- * |b - A x| / |b| <= tol (recursive residual) or after maxit iterations.
+ * gamma + delta.  x: FP64, in = initial guess, out = solution (length N).
+ * Stops when the true residual |b - A x| / |b| <= tol or after maxit
+ * iterations in total.
  * Returns KRR_NOT_CONVERGED if the cap is reached.  If info != NULL the call
  * waits for the solve and fills *info (relres_true from a fresh product). */
 krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d,
-                        float sigma, float shift, const float* b, float* x,
+                        float sigma, float shift, const float* b, double* x,
                         double tol, int maxit, krr_precision prec,
                         krr_solve_info* info, void* stream);
 
@@ -153,14 +157,15 @@ krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d,
  * (modified Gram-Schmidt) and the Givens least-squares update run in FP64;
  * the outer products K z_j and the true residual in FP32 with compensated
  * summation; the inner products M p in opts->inner_prec.
- * B: N x m_rhs right-hand sides, Xsol: N x m_rhs solutions (column-major),
+ * B: N x m_rhs right-hand sides (float32), Xsol: N x m_rhs FP64 solutions
+ * (column-major),
  * each column solved to |b - K x| / |b| <= opts->tol (true residual).
  * opts = NULL takes the defaults.  info: NULL or an array of m_rhs reports.
  * The call waits for the solve when info != NULL.  Returns the worst status
  * over the columns. */
 krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d,
                             float sigma, float gamma, const float* B, int m_rhs,
-                            float* Xsol, const krr_fgmres_opts* opts,
+                            double* Xsol, const krr_fgmres_opts* opts,
                             krr_solve_info* info, void* stream);
 
 /* Many independent problems (same d, sigma, opts; own N_k, gamma_k, m_rhs

@@ -191,12 +191,12 @@ def _stream(stream, *arrays):
     return None
 
 
-def _empty_like_cols(ref, m, N):
+def _empty_like_cols(ref, m, N, dtype="float32"):
     shape = (N,) if m == 1 else (m, N)
     if _is_torch(ref):
         import torch
-        return torch.empty(shape, dtype=torch.float32, device=ref.device)
-    return np.empty(shape, dtype=np.float32)
+        return torch.empty(shape, dtype=getattr(torch, dtype), device=ref.device)
+    return np.empty(shape, dtype=dtype)
 
 
 def _cols(Q, N):
@@ -235,11 +235,11 @@ def krr_kernel_mvp_rect(Xt, Xs, Q, sigma, prec="fp32", out=None, handle=None, st
 
 def krr_cg_solve(X, b, sigma, shift, tol=1e-6, maxit=1000, prec="fp32", x0=None,
                  handle=None, stream=None, raise_on_nonconv=False):
-    """CG on (K_hat + shift I) x = b.  Returns (x, info dict)."""
+    """CG on (K_hat + shift I) x = b.  Returns (x FP64, info dict)."""
     h = handle or default_handle()
     N, d = X.shape
     if x0 is None:
-        x = _empty_like_cols(b, 1, N)
+        x = _empty_like_cols(b, 1, N, "float64")
         x[...] = 0
     else:
         x = x0
@@ -253,12 +253,12 @@ def krr_cg_solve(X, b, sigma, shift, tol=1e-6, maxit=1000, prec="fp32", x0=None,
 
 def krr_fgmres_solve(X, B, sigma, gamma, opts=None, out=None, handle=None, stream=None,
                      raise_on_nonconv=False):
-    """FGMRES with the truncated-CG preconditioner.  B (N,) or (m, N).
-    Returns (Xsol, [info dict per column])."""
+    """FGMRES with the truncated-CG preconditioner.  B (N,) or (m, N) float32.
+    Returns (Xsol FP64 like B, [info dict per column])."""
     h = handle or default_handle()
     N, d = X.shape
     m = _cols(B, N)
-    Xsol = out if out is not None else _empty_like_cols(B, m, N)
+    Xsol = out if out is not None else _empty_like_cols(B, m, N, "float64")
     if opts is None:
         opts = default_opts()
     infos = (krr_solve_info * m)()

@@ -13,6 +13,8 @@ krr_status read_device_error(Ctx& c, cudaStream_t st, const char* what);
 krr_status check_points(Ctx& c, const char* fn, const float* X, int64_t N, int d, float sigma);
 krr_status device_view(Ctx& c, const char* slot, const float* p, size_t count, bool in,
                        cudaStream_t st, float** out, bool* staged);
+krr_status device_view_d(Ctx& c, const char* slot, const double* p, size_t count, bool in,
+                         cudaStream_t st, double** out, bool* staged);
 
 }  // namespace krr
 

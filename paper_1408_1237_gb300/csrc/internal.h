@@ -34,6 +34,7 @@ struct PointsDev {
   int64_t N = 0, Npad = 0;
   int d = 0;
   float scale = 0.f;    // s = sqrt(log2(e) / (2 sigma^2))
+  double s2 = 0.0;      // s^2 = log2(e) / (2 sigma^2) in double
   float* xs = nullptr;  // tile-blocked SoA of the raw coordinates, Npad*d floats
   int* perm = nullptr;  // sorted position -> original index
   int T = 1;            // targets per thread of the product kernels
@@ -41,6 +42,7 @@ struct PointsDev {
   float* ctr = nullptr; // nblk x d block centres (raw coordinates)
   int* order = nullptr; // nblk block indices, expanded-form blocks first
   int* n_exp = nullptr; // device scalar: number of expanded-form blocks
+  float* tbox = nullptr;// Npad/TS source tiles x 2d: centre, then half-width per dim
 };
 
 // Targets per thread the product kernels use for N targets in d dimensions.
@@ -56,6 +58,10 @@ struct Ctx {
   int* h_status = nullptr;     // pinned host mirror for status reads
   std::string last_error;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // solver work runs on this non-blocking stream (capturable), joined to the
+  // caller's stream by ev_in / ev_out
+  cudaStream_t work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 // ---- prep.cu
@@ -71,6 +77,15 @@ cudaError_t gather_sorted(const float* in, int64_t N, int m, const int* perm, in
 cudaError_t scatter_orig(const float* in, int64_t Npad, int64_t N, int m, const int* perm,
                          float* out, cudaStream_t st);
 
+// ---- mvp_acc.cu
+// Accurate product for true residuals: out = cu * u + cy * (K_hat q + shift q)
+// in FP64 (sorted order), q given as float-float (qh + ql), with the fused
+// squared norm *dot += |out|^2 when dot != null.  Per-term relative error
+// ~1e-9 on near tiles.
+cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const float* ql,
+                           float shift, double cu, const float* u, double cy, double* out,
+                           double* dot, cudaStream_t st);
+
 // ---- mvp.cu
 struct MvpOut {
   // y = alpha * (K_hat q + shift q) + beta * u, sorted order
@@ -80,9 +95,23 @@ struct MvpOut {
   double* out_d = nullptr;      // sorted-order double output (may be null)
   const int* perm = nullptr;    // if set with out_orig: scatter to original order
   float* out_orig = nullptr;
-  const float* dotw = nullptr;  // if set: *dot += sum_i y_i * dotw_i
+  const float* dotw = nullptr;  // if set: *dot = sum_i y_i * dotw_i (assigned)
   double* dot = nullptr;
+  // CG step length, applied once the dot is complete: *ratio_out =
+  // *ratio_num / *dot when the dot is positive and finite, else 0 with
+  // *brk_flag set to 1.
+  const double* ratio_num = nullptr;
+  double* ratio_out = nullptr;
+  int* brk_flag = nullptr;
+  // predication: when non-null and *active == 0 the launch does nothing
+  const int* active = nullptr;
 };
+
+// Allocate the workspace and set the kernel attributes a later mvp_launch /
+// mvp_acc_launch on these point sets needs, so that launches captured into a
+// CUDA graph allocate nothing.
+cudaError_t mvp_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, cudaStream_t st);
+cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st);
 
 // Single right-hand side product over prepared targets T and sources S
 // (the same object for the square product).  q: sorted source weights

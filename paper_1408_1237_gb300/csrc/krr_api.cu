@@ -113,6 +113,23 @@ krr_status device_view(Ctx& c, const char* slot, const float* p, size_t count, b
   return KRR_OK;
 }
 
+krr_status device_view_d(Ctx& c, const char* slot, const double* p, size_t count, bool in,
+                         cudaStream_t st, double** out, bool* staged) {
+  if (p == nullptr || count == 0 || is_device_ptr(c, p)) {
+    *out = const_cast<double*>(p);
+    *staged = false;
+    return KRR_OK;
+  }
+  void* d;
+  cudaError_t e = c.ws.get(slot, count * sizeof(double), &d);
+  if (e) return cuda_error(c, e, slot);
+  if (in && (e = cudaMemcpyAsync(d, p, count * sizeof(double), cudaMemcpyHostToDevice, st)))
+    return cuda_error(c, e, slot);
+  *out = (double*)d;
+  *staged = true;
+  return KRR_OK;
+}
+
 }  // namespace krr
 
 using namespace krr;
@@ -161,6 +178,9 @@ krr_status krr_create(krr_handle* out) {
   if (!e) e = cudaMallocHost(&c.h_status, 64 * sizeof(int));
   if (!e) e = cudaEventCreate(&c.ev0);
   if (!e) e = cudaEventCreate(&c.ev1);
+  if (!e) e = cudaStreamCreateWithFlags(&c.work, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming);
+  if (!e) e = cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming);
   if (e) {
     cudaGetLastError();
     if (c.d_err) cudaFree(c.d_err);
@@ -181,6 +201,9 @@ krr_status krr_destroy(krr_handle h) {
   cudaFreeHost(c.h_status);
   cudaEventDestroy(c.ev0);
   cudaEventDestroy(c.ev1);
+  cudaEventDestroy(c.ev_in);
+  cudaEventDestroy(c.ev_out);
+  cudaStreamDestroy(c.work);
   delete h;
   return KRR_OK;
 }

@@ -1,23 +1,828 @@
-// Krylov solvers (hot-path steps A5, A7-A10): truncated CG, FGMRES with
-// modified Gram-Schmidt Arnoldi and Givens least squares, device-side control.
+// Krylov solvers (hot-path steps A5, A7-A10):
+//   * krr_cg_solve     -- conjugate gradient (Sec. 3) on (K_hat + shift I) x = b
+//   * krr_fgmres_solve -- Algorithm 1 (flexible GMRES(m), restarted) on
+//                         K = K_hat + gamma I, right-preconditioned by truncated
+//                         CG on M = K + delta I (Sec. 5)
+//
+// Everything runs on the device; the host only enqueues.  All scalars live in
+// a device-resident KState.  Reductions are deterministic: every block writes
+// a partial, and the last block to arrive (atomic ticket, no waiting) sums the
+// partials in fixed order and performs the scalar step that follows (CG step
+// lengths, Givens rotation, convergence tests).  Loop control is either
+//   * a CUDA graph: the whole solve is captured once into nested conditional
+//     WHILE nodes whose conditions the device sets (cudaGraphSetConditional),
+//     so a solve is one graph launch with no host round trip; or
+//   * a host loop that enqueues predicated iterations in batches and reads the
+//     device flags between batches.
+//
+// Precision (the flexible outer iteration tolerates an inexact preconditioner,
+// Sec. 5.1):
+//   * inner products M p in the requested precision, CG vectors in float32,
+//     dot products accumulated in FP64;
+//   * outer products w = K z_j and the restart residuals with the compensated
+//     float32 (float-float) product of mvp_acc.cu;
+//   * Arnoldi orthogonalisation (CGS2: classical Gram-Schmidt applied twice,
+//     which gives the same column as the modified Gram-Schmidt of Alg. 1 to
+//     working precision while needing two grid reductions instead of j+1),
+//     Hessenberg matrix, Givens rotations and least squares in FP64;
+//   * the iterate x in float-float (two float32 arrays, returned as FP64) and the restart
+//     residual r = b - K x (Alg. 1 line 1) from the accurate product of
+//     mvp_acc.cu, so a restart acts as a step of iterative refinement and the
+//     true residual reaches tolerances the float32 products alone cannot.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "api_util.h"
 #include "common.cuh"
 #include "internal.h"
 
+namespace krr {
+namespace {
+
+constexpr int MMAX = 64;      // largest restart length
+constexpr int VT = 256;       // threads of the vector kernels
+
+struct KState {
+  // conjugate gradient
+  double rho, rho0, pAp, alpha, beta, eps2;  // eps2 = (inner tol)^2
+  int k, maxit, cg_cont, cg_brk;
+  // Arnoldi / Givens
+  int j, m, arn_cont, kcols;
+  double H[(MMAX + 1) * MMAX];  // column-major, leading dimension MMAX+1
+  double cs[MMAX], sn[MMAX], g[MMAX + 1], y[MMAX];
+  double h1[MMAX + 1], h2[MMAX + 1];
+  double wnorm2;
+  // restarts
+  double rnorm2, bnorm, beta0, tol, tol_cycle;
+  int cycles, max_cycles, restart_cont, lucky;
+  // report
+  int outer_total, inner_total, breakdowns, status;
+  double relres_est, relres_true;
+  // reduction scratch
+  unsigned ticket;
+};
+
+struct Cond {
+  cudaGraphConditionalHandle h = 0;
+  int use = 0;
+};
+
+__device__ __forceinline__ void set_cond(const Cond& c, int v) {
+  if (c.use) cudaGraphSetConditional(c.h, (unsigned)v);
+}
+
+// Block partial -> per-block slot; returns true in the last block to arrive,
+// where `total` then holds the fixed-order sum of all partials.
+__device__ __forceinline__ bool grid_sum_last(double v, double* partials, unsigned* ticket,
+                                              double* red, double& total) {
+  __shared__ bool is_last;
+  const double bs = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bs;
+    __threadfence();
+    is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += partials[b];
+  total = block_sum(t, red);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// ------------------------------------------------------------------ CG ---
+// z = 0 (z = v when there is no preconditioner), r = p = v (v = V[j] in
+// FP64, or the float vector vf), rho0 = rho = |v|^2.
+__global__ void cg_init_kernel(KState* S, const double* __restrict__ V, const float* __restrict__ vf,
+                               int64_t Np, float* __restrict__ z, float* __restrict__ r,
+                               float* __restrict__ p, double* partials, Cond cc,
+                               const int* active) {
+  __shared__ double red[8];
+  if (active && *active == 0) return;
+  const double* v = V ? V + (int64_t)S->j * Np : nullptr;
+  const bool identity = S->maxit == 0;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float vi = v ? (float)v[i] : vf[i];
+    r[i] = vi;
+    p[i] = vi;
+    z[i] = identity ? vi : 0.f;
+    acc += (double)vi * (double)vi;
+  }
+  double tot;
+  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) {
+    S->rho = tot;
+    S->rho0 = tot;
+    S->k = 0;
+    S->cg_brk = 0;
+    S->cg_cont = (!identity && tot > 0.0) ? 1 : 0;
+    set_cond(cc, S->cg_cont);
+  }
+}
+
+// z += alpha p; r -= alpha Mp; rho' = |r|^2; beta = rho'/rho; continue test.
+__global__ void cg_update_kernel(KState* S, float* __restrict__ z, float* __restrict__ r,
+                                 const float* __restrict__ p, const float* __restrict__ Mp,
+                                 int64_t Np, double* partials, Cond cc) {
+  __shared__ double red[8];
+  if (!S->cg_cont) return;
+  const float a = (float)S->alpha;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    z[i] = fmaf(a, p[i], z[i]);
+    const float ri = fmaf(-a, Mp[i], r[i]);
+    r[i] = ri;
+    acc += (double)ri * (double)ri;
+  }
+  double tot;
+  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) {
+    S->beta = (S->rho > 0.0) ? tot / S->rho : 0.0;
+    S->rho = tot;
+    S->k += 1;
+    S->inner_total += 1;
+    if (S->cg_brk) S->breakdowns += 1;
+    const bool more = !S->cg_brk && S->k < S->maxit && tot > S->eps2 * S->rho0 && isfinite(tot);
+    S->cg_cont = more ? 1 : 0;
+    set_cond(cc, S->cg_cont);
+  }
+}
+
+// p = r + beta p.  Runs after cg_update, whose last block may have cleared
+// cg_cont; the p update is then harmless (p is not used again).
+__global__ void cg_p_kernel(const KState* S, const float* __restrict__ r, float* __restrict__ p,
+                            int64_t Np, const int* active) {
+  if (active && *active == 0) return;
+  const float b = (float)S->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(b, p[i], r[i]);
+}
+
+// ------------------------------------------------------------- Arnoldi ---
+__global__ void store_z_kernel(const KState* S, const float* __restrict__ z, float* __restrict__ Z,
+                               int64_t Np, const int* active) {
+  if (active && *active == 0) return;
+  float* zj = Z + (int64_t)S->j * Np;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x)
+    zj[i] = z[i];
+}
+
+// h1[i] = (w, v_i), i = 0..j  (first Gram-Schmidt pass).
+__global__ void cgs_dots_kernel(KState* S, const double* __restrict__ V, const double* __restrict__ w,
+                                int64_t Np, double* partials, const int* active) {
+  __shared__ double red[8];
+  __shared__ bool is_last;
+  if (active && *active == 0) return;
+  const int nj = S->j + 1;
+  for (int c = 0; c < nj; ++c) {
+    const double* vc = V + (int64_t)c * Np;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+         i += (int64_t)gridDim.x * blockDim.x)
+      acc += vc[i] * w[i];
+    const double bs = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * (MMAX + 1) + c] = bs;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int c = 0; c < nj; ++c) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      t += partials[(int64_t)b * (MMAX + 1) + c];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) S->h1[c] = t;
+  }
+  if (threadIdx.x == 0) S->ticket = 0u;
+}
+
+// w -= sum_i h1[i] v_i; h2[i] = (w, v_i) (second pass); |w|^2; then, in the
+// last block, the Hessenberg column, the Givens update of Alg. 1's least
+// squares problem and the continuation test.
+__global__ void cgs_update_kernel(KState* S, const double* __restrict__ V, double* __restrict__ w,
+                                  int64_t Np, double* partials, Cond ac, const int* active) {
+  __shared__ double red[8];
+  __shared__ bool is_last;
+  __shared__ double h1s[MMAX + 1];
+  if (active && *active == 0) return;
+  const int j = S->j, nj = j + 1;
+  for (int c = threadIdx.x; c < nj; c += blockDim.x) h1s[c] = S->h1[c];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+    for (int c = 0; c < nj; ++c) wi -= h1s[c] * V[(int64_t)c * Np + i];
+    w[i] = wi;
+  }
+  // second-pass dots and the norm of w, from this block's elements
+  for (int c = 0; c <= nj; ++c) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+         i += (int64_t)gridDim.x * blockDim.x)
+      acc += (c < nj) ? V[(int64_t)c * Np + i] * w[i] : w[i] * w[i];
+    const double bs = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * (MMAX + 1) + c] = bs;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int c = 0; c <= nj; ++c) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      t += partials[(int64_t)b * (MMAX + 1) + c];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) {
+      if (c < nj) S->h2[c] = t;
+      else S->wnorm2 = t;
+    }
+  }
+  if (threadIdx.x != 0) return;
+  S->ticket = 0u;
+  // |w - V h2|^2 = |w|^2 - |h2|^2 (V orthonormal)
+  double hh = 0.0;
+  for (int c = 0; c < nj; ++c) hh += S->h2[c] * S->h2[c];
+  const double wn2 = fmax(S->wnorm2 - hh, 0.0);
+  double* Hj = S->H + (int64_t)j * (MMAX + 1);
+  for (int c = 0; c < nj; ++c) Hj[c] = S->h1[c] + S->h2[c];
+  const double hnext = sqrt(wn2);
+  Hj[nj] = hnext;
+  // apply the previous rotations to the new column, then a new rotation that
+  // zeroes H[j+1, j]
+  for (int c = 0; c < j; ++c) {
+    const double t0 = S->cs[c] * Hj[c] + S->sn[c] * Hj[c + 1];
+    const double t1 = -S->sn[c] * Hj[c] + S->cs[c] * Hj[c + 1];
+    Hj[c] = t0;
+    Hj[c + 1] = t1;
+  }
+  const double a = Hj[j], b = Hj[j + 1];
+  const double rr = hypot(a, b);
+  const double cj = rr > 0.0 ? a / rr : 1.0, sj = rr > 0.0 ? b / rr : 0.0;
+  S->cs[j] = cj;
+  S->sn[j] = sj;
+  Hj[j] = rr;
+  Hj[j + 1] = 0.0;
+  const double gj = S->g[j];
+  S->g[j] = cj * gj;
+  S->g[j + 1] = -sj * gj;
+  S->relres_est = fabs(S->g[j + 1]) / S->bnorm;
+  S->outer_total += 1;
+  S->kcols = j + 1;
+  // lucky breakdown: w lies in the span of V, the least-squares residual is exact
+  const bool lucky = !(hnext > 1e-14 * rr) || !isfinite(hnext);
+  S->lucky = lucky ? 1 : 0;
+  S->wnorm2 = hnext;  // reused by cgs_final as the normaliser
+  const bool more = !lucky && (j + 1 < S->m) && S->relres_est > S->tol_cycle;
+  S->arn_cont = more ? 1 : 0;
+  set_cond(ac, S->arn_cont);
+}
+
+// v_{j+1} = (w - V h2) / h_{j+1,j}
+__global__ void cgs_final_kernel(const KState* S, double* __restrict__ V, const double* __restrict__ w,
+                                 int64_t Np, const int* active) {
+  __shared__ double h2s[MMAX + 1];
+  if (active && *active == 0) return;
+  const int j = S->j, nj = j + 1;
+  if (S->lucky || j + 1 > S->m) return;
+  for (int c = threadIdx.x; c < nj; c += blockDim.x) h2s[c] = S->h2[c];
+  __syncthreads();
+  const double inv = 1.0 / S->wnorm2;
+  double* vn = V + (int64_t)nj * Np;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+    for (int c = 0; c < nj; ++c) wi -= h2s[c] * V[(int64_t)c * Np + i];
+    vn[i] = wi * inv;
+  }
+}
+
+__global__ void arn_advance_kernel(KState* S) {
+  if (S->arn_cont) S->j += 1;
+}
+
+// ---------------------------------------------------------- restarts -----
+// Back-substitution R y = g (R upper triangular after the rotations, kcols
+// columns), then x += Z y in float-float.
+__global__ void lsq_kernel(KState* S, const int* active) {
+  if (active && *active == 0) return;
+  const int k = S->kcols;
+  for (int r = k - 1; r >= 0; --r) {
+    double t = S->g[r];
+    for (int c = r + 1; c < k; ++c) t -= S->H[(int64_t)c * (MMAX + 1) + r] * S->y[c];
+    const double d = S->H[(int64_t)r * (MMAX + 1) + r];
+    S->y[r] = d != 0.0 ? t / d : 0.0;
+  }
+}
+
+__global__ void x_update_kernel(const KState* S, const float* __restrict__ Z, int64_t Np,
+                                float* __restrict__ xh, float* __restrict__ xl, const int* active) {
+  __shared__ double ys[MMAX];
+  if (active && *active == 0) return;
+  const int k = S->kcols;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = S->y[c];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double t = (double)xh[i] + (double)xl[i];
+    for (int c = 0; c < k; ++c) t += ys[c] * (double)Z[(int64_t)c * Np + i];
+    const float h = (float)t;
+    xh[i] = h;
+    xl[i] = (float)(t - (double)h);
+  }
+}
+
+// After the accurate residual: convergence test and the next cycle's start
+// (Alg. 1 lines 1 and 13).  tol_stop < tol leaves room for rounding the
+// FP64 iterate to the float32 output.
+__global__ void restart_check_kernel(KState* S, Cond rc, double tol_stop) {
+  const double beta = sqrt(S->rnorm2);
+  S->relres_true = S->bnorm > 0.0 ? beta / S->bnorm : 0.0;
+  bool more = S->bnorm > 0.0 && S->relres_true > tol_stop && isfinite(beta);
+  if (more && S->cycles >= S->max_cycles) {
+    more = false;
+    S->status = KRR_NOT_CONVERGED;
+  }
+  if (!isfinite(beta)) S->status = KRR_ERR_NONFINITE;
+  S->restart_cont = more ? 1 : 0;
+  if (more) {
+    S->cycles += 1;
+    S->beta0 = beta;
+    S->g[0] = beta;
+    for (int c = 1; c <= MMAX; ++c) S->g[c] = 0.0;
+    S->j = 0;
+    S->kcols = 0;
+    S->arn_cont = 1;
+    S->lucky = 0;
+  }
+  set_cond(rc, S->restart_cont);
+}
+
+// V[0] = r / beta0; re-arms the Arnoldi loop (a WHILE condition takes its
+// default only once per graph launch).
+__global__ void v0_kernel(const KState* S, const double* __restrict__ r, double* __restrict__ V,
+                          int64_t Np, const int* active, Cond ac) {
+  if (active && *active == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(ac, 1);
+  const double inv = 1.0 / S->beta0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = r[i] * inv;
+}
+
+// x = 0, r = b (the residual of x0 = 0), |b|^2.
+__global__ void solve_init_kernel(KState* S, const float* __restrict__ b, int64_t Np,
+                                  float* __restrict__ xh, float* __restrict__ xl,
+                                  double* __restrict__ r, double* partials) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    xh[i] = 0.f;
+    xl[i] = 0.f;
+    const double bi = b[i];
+    r[i] = bi;
+    acc += bi * bi;
+  }
+  double tot;
+  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) {
+    S->rnorm2 = tot;
+    S->bnorm = sqrt(tot);
+  }
+}
+
+// Xsol[perm[i]] = xh[i] + xl[i] (FP64, original order)
+__global__ void scatter_x64_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
+                                   const int* __restrict__ perm, int64_t N, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[perm[i]] = (double)xh[i] + (double)xl[i];
+}
+
+__global__ void fill_zero_kernel(float* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 0.f;
+}
+
+__global__ void final_report_kernel(KState* S) {
+  S->relres_true = S->bnorm > 0.0 ? sqrt(S->rnorm2) / S->bnorm : 0.0;
+}
+
+// ---------------------------------------------------------------- driver --
+struct Solver {
+  Ctx& c;
+  cudaStream_t st;
+  PointsDev P;
+  int64_t Np = 0;
+  unsigned vblocks = 1;
+  float gamma = 0.f, mshift = 0.f;
+  krr_precision inner_prec = KRR_FP32;
+  int m = 30;
+  // device buffers
+  KState* S = nullptr;
+  float *b = nullptr, *xh = nullptr, *xl = nullptr, *zero = nullptr;
+  double *r64 = nullptr, *V = nullptr, *w = nullptr, *partials = nullptr;
+  float *Z = nullptr, *z = nullptr, *rr = nullptr, *p = nullptr, *Mp = nullptr;
+  Cond cg_c, arn_c, rst_c;
+
+  explicit Solver(Ctx& cc) : c(cc) {}
+
+  cudaError_t alloc(int restart) {
+    cudaError_t e;
+    void* v;
+    const size_t n = (size_t)Np;
+    m = restart;
+#define KRR_WS(name, ptr, bytes)                      \
+  if ((e = c.ws.get(name, bytes, &v))) return e;       \
+  ptr = (decltype(ptr))v;
+    KRR_WS("kry.state", S, sizeof(KState));
+    KRR_WS("kry.b", b, n * 4);
+    KRR_WS("kry.xh", xh, n * 4);
+    KRR_WS("kry.xl", xl, n * 4);
+    KRR_WS("kry.zero", zero, n * 4);
+    KRR_WS("kry.r64", r64, n * 8);
+    KRR_WS("kry.V", V, n * 8 * (m + 1));
+    KRR_WS("kry.w", w, n * 8);
+    KRR_WS("kry.partials", partials, sizeof(double) * (MMAX + 1) * 1024);
+    KRR_WS("kry.Z", Z, n * 4 * m);
+    KRR_WS("kry.z", z, n * 4);
+    KRR_WS("kry.r", rr, n * 4);
+    KRR_WS("kry.p", p, n * 4);
+    KRR_WS("kry.Mp", Mp, n * 4);
+#undef KRR_WS
+    vblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Np + VT - 1) / VT, 4LL * c.num_sms));
+    fill_zero_kernel<<<vblocks, VT, 0, st>>>(zero, Np);
+    return cudaGetLastError();
+  }
+
+  // ---- one CG iteration on the inner operator: M p = K_hat p + mshift p
+  cudaError_t cg_iteration(const int* active) {
+    MvpOut o;
+    o.out_f = Mp;
+    o.dotw = p;
+    o.dot = &S->pAp;
+    o.ratio_num = &S->rho;
+    o.ratio_out = &S->alpha;
+    o.brk_flag = &S->cg_brk;
+    o.active = active;
+    cudaError_t e = mvp_launch(c, P, P, p, p, mshift, inner_prec, o, st);
+    if (e) return e;
+    cg_update_kernel<<<vblocks, VT, 0, st>>>(S, z, rr, p, Mp, Np, partials, cg_c);
+    cg_p_kernel<<<vblocks, VT, 0, st>>>(S, rr, p, Np, active);
+    return cudaGetLastError();
+  }
+
+  // ---- Arnoldi step after the inner solve: Z[j] = z, w = K z, CGS2, Givens
+  cudaError_t arnoldi_tail(const int* active) {
+    store_z_kernel<<<vblocks, VT, 0, st>>>(S, z, Z, Np, active);
+    // w = K z_j with the compensated product: its error enters the flexible
+    // Arnoldi relation K Z = V Hbar, and through it the true residual
+    cudaError_t e = mvp_acc_launch(c, P, z, zero, gamma, 0.0, nullptr, 1.0, w, nullptr, st);
+    if (e) return e;
+    cgs_dots_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, active);
+    cgs_update_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, arn_c, active);
+    cgs_final_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, active);
+    arn_advance_kernel<<<1, 1, 0, st>>>(S);
+    return cudaGetLastError();
+  }
+
+  cudaError_t cycle_tail(double tol_stop, const int* active) {
+    lsq_kernel<<<1, 1, 0, st>>>(S, active);
+    x_update_kernel<<<vblocks, VT, 0, st>>>(S, Z, Np, xh, xl, active);
+    cudaError_t e = residual();
+    if (e) return e;
+    restart_check_kernel<<<1, 1, 0, st>>>(S, rst_c, tol_stop);
+    return cudaGetLastError();
+  }
+
+  // r64 = b - K x (accurate), rnorm2 = |r|^2
+  cudaError_t residual() {
+    return mvp_acc_launch(c, P, xh, xl, gamma, 1.0, b, -1.0, r64, &S->rnorm2, st);
+  }
+};
+
+cudaError_t read_state(Ctx& c, const KState* S, KState& h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(&h, S, sizeof(KState), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+template <typename T>
+cudaError_t put_field(KState* S, size_t off, T v, cudaStream_t st) {
+  return cudaMemcpyAsync(reinterpret_cast<char*>(S) + off, &v, sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+struct SolveCfg {
+  int restart, max_cycles, inner_maxit;
+  double tol, delta, inner_tol;
+  krr_precision inner_prec;
+  bool graph;
+};
+
+// Host-side initial state for one right-hand side.
+void init_state(KState& h, const SolveCfg& cfg) {
+  memset(&h, 0, sizeof(h));
+  h.maxit = cfg.inner_maxit;
+  h.eps2 = cfg.inner_tol * cfg.inner_tol;
+  h.m = cfg.restart;
+  h.tol = cfg.tol;
+  h.tol_cycle = 0.5 * cfg.tol;
+  h.max_cycles = cfg.max_cycles;
+  h.status = KRR_OK;
+}
+
+std::vector<cudaGraphNode_t> sinks(cudaGraph_t g) {
+  std::vector<cudaGraphNode_t> out;
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) || n == 0) return out;
+  std::vector<cudaGraphNode_t> all(n);
+  cudaGraphGetNodes(g, all.data(), &n);
+  for (auto nd : all) {
+    size_t nout = 0;
+    cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nout);
+    if (nout == 0) out.push_back(nd);
+  }
+  return out;
+}
+
+// Append a WHILE node controlled by `h` after every sink of `parent`.
+cudaError_t add_while(cudaGraph_t parent, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  std::vector<cudaGraphNode_t> deps = sinks(parent);
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddNode(&node, parent, deps.data(), nullptr, deps.size(), &np);
+  if (e) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaSuccess;
+}
+
+// Capture the work enqueued by fn() into `into`, after its current sinks.
+template <typename F>
+cudaError_t capture_into(cudaStream_t st, cudaGraph_t into, F&& fn) {
+  std::vector<cudaGraphNode_t> deps = sinks(into);
+  cudaError_t e = cudaStreamBeginCaptureToGraph(st, into, deps.data(), nullptr, deps.size(),
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e) return e;
+  const cudaError_t fe = fn();
+  cudaGraph_t out;
+  e = cudaStreamEndCapture(st, &out);
+  return fe ? fe : e;
+}
+
+// The whole FGMRES solve (after solve_init and the first restart check) as
+// one graph:  WHILE restart { v0; WHILE arnoldi { cg_init; WHILE cg { CG
+// iteration }; Arnoldi step }; least squares, x update, true residual, check }.
+cudaError_t build_graph(Solver& s, double tol_stop, cudaGraphExec_t* exec) {
+  cudaError_t e;
+  cudaGraph_t g, rbody, abody, cbody;
+  if ((e = cudaGraphCreate(&g, 0))) return e;
+  auto fail = [&](cudaError_t ee) {
+    cudaGraphDestroy(g);
+    return ee;
+  };
+  if ((e = cudaGraphConditionalHandleCreate(&s.rst_c.h, g, 1, cudaGraphCondAssignDefault))) return fail(e);
+  s.rst_c.use = 1;
+  if ((e = add_while(g, s.rst_c.h, &rbody))) return fail(e);
+  if ((e = cudaGraphConditionalHandleCreate(&s.arn_c.h, rbody, 1, cudaGraphCondAssignDefault))) return fail(e);
+  s.arn_c.use = 1;
+  if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t {
+         v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, s.arn_c);
+         return cudaGetLastError();
+       })))
+    return fail(e);
+  if ((e = add_while(rbody, s.arn_c.h, &abody))) return fail(e);
+  if ((e = cudaGraphConditionalHandleCreate(&s.cg_c.h, abody, 0, cudaGraphCondAssignDefault))) return fail(e);
+  s.cg_c.use = 1;
+  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t {
+         cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
+                                                    s.partials, s.cg_c, nullptr);
+         return cudaGetLastError();
+       })))
+    return fail(e);
+  if ((e = add_while(abody, s.cg_c.h, &cbody))) return fail(e);
+  if ((e = capture_into(s.st, cbody, [&]() -> cudaError_t { return s.cg_iteration(nullptr); })))
+    return fail(e);
+  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t { return s.arnoldi_tail(nullptr); })))
+    return fail(e);
+  if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t { return s.cycle_tail(tol_stop, nullptr); })))
+    return fail(e);
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+}  // namespace
+}  // namespace krr
+
 using namespace krr;
+
+namespace {
+
+krr_status resolve_opts(Ctx& c, const char* fn, const krr_fgmres_opts* opts, float gamma,
+                        SolveCfg& cfg) {
+  krr_fgmres_opts o;
+  krr_fgmres_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > MMAX)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: restart %d out of range [1, %d]", fn, o.restart, MMAX);
+  if (o.max_cycles < 1) return set_error(c, KRR_ERR_INVALID_ARG, "%s: max_cycles < 1", fn);
+  if (!(o.tol > 0.0) || !(o.tol < 1.0))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: tol must be in (0, 1)", fn);
+  if (o.inner_maxit < 0 || o.inner_maxit > 100000)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: inner_maxit out of range", fn);
+  if (o.inner_prec != KRR_FP32 && o.inner_prec != KRR_BF16 && o.inner_prec != KRR_FP16)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: unknown inner precision", fn);
+  cfg.restart = o.restart;
+  cfg.max_cycles = o.max_cycles;
+  cfg.tol = o.tol;
+  cfg.delta = o.delta >= 0.0 ? o.delta : (gamma > 0.f ? 10.0 * gamma : 1e-3);  // Sec. 6
+  cfg.inner_tol = o.inner_tol >= 0.0 ? o.inner_tol : 10.0 * o.tol;             // Sec. 6
+  cfg.inner_maxit = o.inner_maxit;
+  cfg.inner_prec = o.inner_prec;
+  cfg.graph = o.use_graph != 0;
+  if (!std::isfinite(cfg.delta) || !std::isfinite(cfg.inner_tol))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: delta / inner_tol not finite", fn);
+  return KRR_OK;
+}
+
+void fill_info(const KState& h, float ms, krr_solve_info* info) {
+  if (!info) return;
+  info->outer_iters = h.outer_total;
+  info->inner_iters = h.inner_total;
+  info->cycles = h.cycles;
+  info->breakdowns = h.breakdowns;
+  info->relres_est = h.relres_est;
+  info->relres_true = h.relres_true;
+  info->time_ms = ms;
+  info->status = (krr_status)h.status;
+}
+
+// One FGMRES solve of the sorted right-hand side already in s.b (exec: the
+// solve graph, or null for the host-driven loop).
+krr_status fgmres_one(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec, KState& hs,
+                      float* ms_out) {
+  Ctx& c = s.c;
+  const char* fn = "krr_fgmres_solve";
+  cudaError_t e;
+  init_state(hs, cfg);
+  if ((e = cudaMemcpyAsync(s.S, &hs, sizeof(KState), cudaMemcpyHostToDevice, s.st)))
+    return cuda_error(c, e, fn);
+  cudaEventRecord(c.ev0, s.st);
+  solve_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials);
+  // the first restart check turns x0 = 0, r0 = b into the first cycle
+  restart_check_kernel<<<1, 1, 0, s.st>>>(s.S, Cond{}, 0.5 * cfg.tol);
+  const double tol_stop = 0.5 * cfg.tol;
+  if (exec) {
+    // the restart loop's default condition is 1: skip the graph when the
+    // first check already stopped (b = 0)
+    KState chk;
+    if ((e = read_state(c, s.S, chk, s.st))) return cuda_error(c, e, fn);
+    if (chk.restart_cont && (e = cudaGraphLaunch(exec, s.st))) return cuda_error(c, e, fn);
+  } else {
+    for (;;) {
+      KState h;
+      if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
+      if (!h.restart_cont) break;
+      v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, Cond{});
+      for (;;) {
+        cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
+                                                   s.partials, Cond{}, nullptr);
+        for (;;) {
+          if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
+          if (!h.cg_cont) break;
+          // predicated batch: iterations after convergence do nothing
+          for (int b = 0; b < 8; ++b)
+            if ((e = s.cg_iteration(&s.S->cg_cont))) return cuda_error(c, e, fn);
+        }
+        if ((e = s.arnoldi_tail(nullptr))) return cuda_error(c, e, fn);
+        if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
+        if (!h.arn_cont) break;
+      }
+      if ((e = s.cycle_tail(tol_stop, nullptr))) return cuda_error(c, e, fn);
+    }
+  }
+  cudaEventRecord(c.ev1, s.st);
+  if ((e = cudaEventSynchronize(c.ev1))) return cuda_error(c, e, fn);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+  *ms_out = ms;
+  if ((e = read_state(c, s.S, hs, s.st))) return cuda_error(c, e, fn);
+  if (hs.status == KRR_OK && hs.relres_true > cfg.tol) hs.status = KRR_NOT_CONVERGED;
+  return KRR_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
-krr_status krr_cg_solve(krr_handle h, const float*, int64_t, int, float, float, const float*,
-                        float*, double, int, krr_precision, krr_solve_info*, void*) {
+krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, float sigma,
+                            float gamma, const float* B, int m_rhs, double* Xsol,
+                            const krr_fgmres_opts* opts, krr_solve_info* info, void* stream) {
   if (!h) return KRR_ERR_INVALID_ARG;
-  return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_cg_solve: not built yet");
+  Ctx& c = h->ctx;
+  const char* fn = "krr_fgmres_solve";
+  krr_status s = check_points(c, fn, X, N, d, sigma);
+  if (s) return s;
+  if (!(gamma >= 0.f) || !std::isfinite(gamma))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: gamma must be finite and >= 0", fn);
+  if (m_rhs < 1 || m_rhs > 1024)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: m_rhs out of range [1, 1024]", fn);
+  SolveCfg cfg;
+  if ((s = resolve_opts(c, fn, opts, gamma, cfg))) return s;
+  if (N == 0) return KRR_OK;
+  if (!B || !Xsol) return set_error(c, KRR_ERR_INVALID_ARG, "%s: B or Xsol is NULL", fn);
+  // all work on the handle's capturable stream, ordered after the caller's
+  cudaStream_t ust = (cudaStream_t)stream;
+  cudaStream_t st = c.work;
+  {
+    cudaError_t e0 = cudaEventRecord(c.ev_in, ust);
+    if (!e0) e0 = cudaStreamWaitEvent(st, c.ev_in, 0);
+    if (e0) return cuda_error(c, e0, fn);
+  }
+  struct Join {
+    Ctx& c;
+    cudaStream_t ust;
+    ~Join() {
+      cudaEventRecord(c.ev_out, c.work);
+      cudaStreamWaitEvent(ust, c.ev_out, 0);
+    }
+  } join{c, ust};
+  float *dX, *dB;
+  double* dXs;
+  bool sX, sB, sXs;
+  if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
+  if ((s = device_view(c, "stage.B", B, (size_t)N * m_rhs, true, st, &dB, &sB))) return s;
+  if ((s = device_view_d(c, "stage.Xsol", Xsol, (size_t)N * m_rhs, false, st, &dXs, &sXs))) return s;
+  Solver sv(c);
+  sv.st = st;
+  cudaError_t e = prepare_points(c, dX, N, d, sigma, "kry.pts", sv.P, st);
+  if (e) return cuda_error(c, e, fn);
+  sv.Np = sv.P.Npad;
+  sv.gamma = gamma;
+  sv.mshift = (float)(gamma + cfg.delta);
+  sv.inner_prec = cfg.inner_prec;
+  if ((e = sv.alloc(cfg.restart))) return cuda_error(c, e, fn);
+  // size every workspace buffer now: nothing may allocate inside a capture
+  if ((e = mvp_reserve(c, sv.P, sv.P, st))) return cuda_error(c, e, fn);
+  if ((e = mvp_acc_reserve(c, sv.P, st))) return cuda_error(c, e, fn);
+  cudaGraphExec_t exec = nullptr;
+  sv.cg_c = sv.arn_c = sv.rst_c = Cond{};
+  if (cfg.graph) {
+    if ((e = build_graph(sv, 0.5 * cfg.tol, &exec))) {
+      cudaGetLastError();
+      return cuda_error(c, e, "krr_fgmres_solve (graph build)");
+    }
+  }
+  struct ExecGuard {
+    cudaGraphExec_t x;
+    ~ExecGuard() {
+      if (x) cudaGraphExecDestroy(x);
+    }
+  } guard{exec};
+  krr_status worst = KRR_OK;
+  for (int col = 0; col < m_rhs; ++col) {
+    if ((e = gather_sorted(dB + (size_t)col * N, N, 1, sv.P.perm, sv.Np, sv.b, st)))
+      return cuda_error(c, e, fn);
+    KState hs;
+    float ms = 0.f;
+    if ((s = fgmres_one(sv, cfg, exec, hs, &ms))) return s;
+    scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, dXs + (size_t)col * N);
+    if ((e = cudaGetLastError())) return cuda_error(c, e, fn);
+    if (info) fill_info(hs, ms, info + col);
+    if (hs.status != KRR_OK && worst == KRR_OK) worst = (krr_status)hs.status;
+  }
+  if (sXs && (e = cudaMemcpyAsync(Xsol, dXs, sizeof(double) * N * m_rhs, cudaMemcpyDeviceToHost, st)))
+    return cuda_error(c, e, fn);
+  krr_status de = read_device_error(c, st, fn);
+  if (de) return de;
+  if (worst == KRR_NOT_CONVERGED)
+    set_error(c, worst, "%s: tolerance not reached in %d cycles", fn, cfg.max_cycles);
+  else if (worst != KRR_OK)
+    set_error(c, worst, "%s: solve failed", fn);
+  return worst;
 }
 
-krr_status krr_fgmres_solve(krr_handle h, const float*, int64_t, int, float, float, const float*,
-                            int, float*, const krr_fgmres_opts*, krr_solve_info*, void*) {
+krr_status krr_cg_solve(krr_handle h, const float*, int64_t, int, float, float, const float*,
+                        double*, double, int, krr_precision, krr_solve_info*, void*) {
   if (!h) return KRR_ERR_INVALID_ARG;
-  return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_fgmres_solve: not built yet");
+  return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_cg_solve: not built yet");
 }
 
 krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem*, int, int, float, int,

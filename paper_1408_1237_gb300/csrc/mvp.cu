@@ -64,6 +64,7 @@ struct MvpParams {
   float* fac;           // [Nt_pad] factored scale 2^(-|x^_i|^2) (1 for the direct form)
   int* err;
   float s;              // sqrt(log2(e) / (2 sigma^2))
+  const int* active;    // predication flag (null: always run)
 };
 
 // Warp-cooperative transform of one raw source tile for this warp's centre:
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   float* wbuf = smem + RS * kRawFloats + warp * kWbFloats;  // this warp's (D+2) * TS
   __shared__ __align__(8) uint64_t bars[RS];
   __shared__ volatile int abort_flag;
+  if (p.active && *p.active == 0) return;
 
   // ---- this warp's target block
   const int64_t slot = (int64_t)blockIdx.x * NW + warp;
@@ -303,6 +305,7 @@ struct FinParams {
 __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
   __shared__ double red[8];
   __shared__ bool is_last;
+  if (f.o.active && *f.o.active == 0) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double out = 0.0, dotv = 0.0;
   if (i < f.N) {
@@ -333,22 +336,43 @@ __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
       for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += f.dot_part[b];
       t = block_sum(t, red);
       if (threadIdx.x == 0) {
-        *f.o.dot += t;
+        *f.o.dot = t;
+        if (f.o.ratio_out) {
+          const bool good = t > 0.0 && isfinite(t);
+          *f.o.ratio_out = good ? *f.o.ratio_num / t : 0.0;
+          if (!good) *f.o.brk_flag = 1;
+        }
         *f.dot_count = 0u;
       }
     }
   }
 }
 
+template <int D>
+constexpr size_t smem_bytes() {
+  return sizeof(float) * (raw_stages<D>() * (D + 1) * TS + NW * (D + 2) * TS);
+}
+
+// Dynamic shared-memory opt-in, once per kernel instance and device.
+template <int D, int T>
+cudaError_t set_attr() {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mvp_f32_kernel<D, T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<D>());
+  if (!e && dev < 128) done[dev] = true;
+  return e;
+}
+
 template <int D, int T>
 cudaError_t launch_typed(const MvpParams& p, int splits, cudaStream_t st) {
-  constexpr int RS = raw_stages<D>();
-  const size_t shm = sizeof(float) * (RS * (D + 1) * TS + NW * (D + 2) * TS);
-  cudaError_t e = cudaFuncSetAttribute(mvp_f32_kernel<D, T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  cudaError_t e = set_attr<D, T>();
   if (e) return e;
   dim3 grid((unsigned)((p.nblk + NW - 1) / NW), (unsigned)splits);
-  mvp_f32_kernel<D, T><<<grid, NT, shm, st>>>(p);
+  mvp_f32_kernel<D, T><<<grid, NT, smem_bytes<D>(), st>>>(p);
   return cudaGetLastError();
 }
 
@@ -402,6 +426,14 @@ Plan make_plan(int64_t nblk, int ntiles, int num_sms) {
 }
 
 template <int D>
+cudaError_t attrs_T(int T) {
+  constexpr int TL = large_T<D>();
+  if (T == TL) return set_attr<D, TL>();
+  if (T == 1) return set_attr<D, 1>();
+  return cudaErrorNotSupported;
+}
+
+template <int D>
 cudaError_t dispatch_T(MvpParams p, int T, const Plan& pl, cudaStream_t st) {
   constexpr int TL = large_T<D>();
   p.tiles_per_split = pl.tiles_per_split;
@@ -417,6 +449,31 @@ int mvp_targets_per_thread(int d, int64_t N) {
   // gives small problems enough CTAs
   const int TL = large_T_of(d);
   return (N / (256LL * TL) >= 32) ? TL : 1;
+}
+
+cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaStream_t st) {
+  if (Tp.N == 0) return cudaSuccess;
+  if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
+  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms);
+  void* v;
+  cudaError_t e;
+  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
+  if ((e = c.ws.get("mvp.part", sizeof(double) * pl.splits * (size_t)Tp.Npad, &v))) return e;
+  if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &v))) return e;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &v))) return e;
+  const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &v))) return e;
+  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned), st))) return e;
+  switch (Tp.d) {
+    case 1: return attrs_T<1>(Tp.T);
+    case 2: return attrs_T<2>(Tp.T);
+    case 3: return attrs_T<3>(Tp.T);
+    case 4: return attrs_T<4>(Tp.T);
+    case 5: return attrs_T<5>(Tp.T);
+    case 6: return attrs_T<6>(Tp.T);
+    case 7: return attrs_T<7>(Tp.T);
+    default: return attrs_T<8>(Tp.T);
+  }
 }
 
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
@@ -436,21 +493,20 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   p.q = q;
   p.ntiles = (int)(Sp.Npad / TS);
   p.s = Sp.scale;
+  p.active = o.active;
   p.err = c.d_err;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
   const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms);
+  cudaError_t e = mvp_reserve(c, Tp, Sp, st);
+  if (e) return e;
   void *part, *fac, *dpart, *dcnt;
-  cudaError_t e;
+  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
   if ((e = c.ws.get("mvp.part", sizeof(double) * pl.splits * (size_t)Tp.Npad, &part))) return e;
   if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &fac))) return e;
-  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
   if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
-  const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &dcnt))) return e;
-  if (fresh && (e = cudaMemsetAsync(dcnt, 0, sizeof(unsigned), st))) return e;
   p.part = (double*)part;
   p.fac = (float*)fac;
-  const int splits = pl.splits;
   switch (Tp.d) {
     case 1: e = dispatch_T<1>(p, Tp.T, pl, st); break;
     case 2: e = dispatch_T<2>(p, Tp.T, pl, st); break;
@@ -465,7 +521,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   if (e) return e;
   FinParams f{};
   f.part = p.part;
-  f.splits = splits;
+  f.splits = pl.splits;
   f.N = Tp.N;
   f.Npad = Tp.Npad;
   f.fac = p.fac;

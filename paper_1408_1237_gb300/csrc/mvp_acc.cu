@@ -1,0 +1,446 @@
+// Accurate kernel product for the true residual of the outer solver
+// (hot-path step A9, Alg. 1 lines 1 and 13: r = b - K x):
+//
+//   out_i = cu u_i + cy (sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) q_j + shift q_i)
+//
+// The residual of a converged solve is a small difference of large sums, so
+// the fast float32 product (relative error ~1e-7 per term) would put a floor
+// near the 1e-6 target.  Here every pair that can matter is evaluated in
+// float-float arithmetic (about 48-bit significands):
+//   * r^2 = sum_k (x_ik - x_jk)^2 from the raw float32 coordinates with exact
+//     differences (TwoSum), exact products (FMA error terms) and TwoSum
+//     accumulation;
+//   * e = -s^2 r^2 with s^2 = log2(e)/(2 sigma^2) split into float hi + lo;
+//   * 2^e by table-driven reduction e = n + k/64 + t, |t| <= 1/128: 2^(k/64)
+//     from a 64-entry float-float table, 2^t = 1 + u with u from the Taylor
+//     series of exp(t ln 2) to degree 4 (remainder < 1e-13), u itself in
+//     float-float; the result is accurate to about 1e-12;
+//   * q_j (the FP64 iterate) arrives as float hi + lo; each product q_j Phi_ij
+//     is split exactly (FMA error term) and summed with TwoSum.
+// A (warp, source tile) pair whose bounding boxes are farther apart than
+// s^2 d^2 > 30 contributes less than 2^-30 per term; it takes a plain float32
+// path into the low-order accumulator.  Each source split writes an FP64
+// partial per target; the finalize kernel sums splits in fixed order and
+// applies the epilogue in FP64 (deterministic).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace krr {
+namespace {
+
+constexpr int NT = 256;
+constexpr int NW = NT / 32;
+constexpr int RS = 3;
+constexpr float FAR_E = 30.f;  // s^2 dist^2 beyond which a tile is far
+
+struct AccConst {
+  float s2h, s2l;  // s^2 = s2h + s2l
+  float c1h, c1l;  // ln 2 = c1h + c1l
+  float c2, c3, c4;  // (ln 2)^k / k!, k = 2..4
+  float th[64], tl[64];  // 2^(k/64) = th[k] + tl[k]
+};
+
+struct AccParams {
+  const float* xs;   // points, tile-blocked SoA (raw), targets = sources
+  int64_t N, Npad;
+  const float* qh;   // source weights hi (sorted, zero padded)
+  const float* ql;   // source weights lo
+  const float* tbox; // source tile boxes
+  int ntiles, tiles_per_split;
+  double* part;      // [splits][Npad]
+  int* err;
+  AccConst k;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// a - b exactly as s + e (Knuth's TwoSum on a and -b).
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
+  s = a - b;
+  const float bb = s - a;
+  e = (a - (s - bb)) - (b + bb);
+}
+
+// Accurate q * exp2(-s^2 |xi - xj|^2) added into (S, L).
+template <int D>
+__device__ __forceinline__ void acc_pair(const float (&xi)[D], const float* __restrict__ xj,
+                                         float qh, float ql, float& S, float& L,
+                                         const AccConst& k, const float* __restrict__ tab_h,
+                                         const float* __restrict__ tab_l) {
+  // r^2 = sum_k (dh + dl)^2 in float-float, the differences exact
+  float dh, dl;
+  two_diff(xi[0], xj[0], dh, dl);
+  float rh = dh * dh;
+  float rl = fmaf(dh, dh, -rh) + 2.f * dh * dl;
+#pragma unroll
+  for (int c = 1; c < D; ++c) {
+    two_diff(xi[c], xj[c * TS], dh, dl);
+    const float p = dh * dh;
+    const float pe = fmaf(dh, dh, -p) + 2.f * dh * dl;
+    float s, e;
+    two_sum(rh, p, s, e);
+    rh = s;
+    rl += e + pe;
+  }
+  // e = -(s2h + s2l)(rh + rl)
+  const float eh = -k.s2h * rh;
+  const float el = fmaf(-k.s2h, rh, -eh) - fmaf(k.s2h, rl, k.s2l * rh);
+  // e = n + j/64 + (r + el), m = 64 n + j = rint(64 eh); below -200 the value
+  // flushes to zero anyway
+  const float y = 64.f * fmaxf(eh, -200.f);  // exact scaling
+  const float tm = y + 12582912.f;          // 1.5 * 2^23: rounds to an integer
+  const float mf = tm - 12582912.f;
+  const float r = (y - mf) * 0.015625f;     // exact, |r| <= 1/128
+  const int m = __float_as_int(tm) - 0x4B400000;
+  const int n = m >> 6;                     // floor(m / 64)
+  const int jt = m - (n << 6);              // 0..63
+  // 2^(r + el) = 1 + uh + ul
+  const float uh = k.c1h * r;
+  const float ul = fmaf(k.c1h, r, -uh) + fmaf(k.c1l, r, k.c1h * el) +
+                   (r * r) * fmaf(fmaf(k.c4, r, k.c3), r, k.c2);
+  // (Th + Tl)(1 + uh + ul) = H + L2
+  const float Th = tab_h[jt], Tl = tab_l[jt];
+  const float P = Th * uh;
+  const float Pe = fmaf(Th, uh, -P);
+  float H = Th + P;                          // |Th| >= 1 > |P|: Fast2Sum
+  float L2 = ((Th - H) + P) + Pe + fmaf(Th, ul, Tl * (1.f + uh));
+  const float sc = (n >= -126) ? __int_as_float((n + 127) << 23) : 0.f;
+  H *= sc;
+  L2 *= sc;
+  // (qh + ql)(H + L2)
+  const float a = qh * H;
+  const float ae = fmaf(qh, H, -a);
+  float s, e;
+  two_sum(S, a, s, e);
+  S = s;
+  L += e + ae + fmaf(qh, L2, ql * H);
+}
+
+template <int D, int TA>
+__global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
+  constexpr uint32_t kStageFloats = (D + 2) * TS;  // coordinates, qh, ql
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t bars[RS];
+  __shared__ volatile int abort_flag;
+  __shared__ float tab_h[64], tab_l[64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 64) {
+    tab_h[tid] = p.k.th[tid];
+    tab_l[tid] = p.k.tl[tid];
+  }
+
+  // this warp's targets: 32*TA consecutive sorted points
+  const int64_t t0 = ((int64_t)blockIdx.x * NW + warp) * 32 * TA;
+  float xi[TA][D];
+  bool valid[TA];
+#pragma unroll
+  for (int u = 0; u < TA; ++u) {
+    const int64_t i = t0 + lane + 32 * u;
+    valid[u] = i < p.N;
+    const int64_t ii = valid[u] ? i : (p.N - 1);
+#pragma unroll
+    for (int c = 0; c < D; ++c) xi[u][c] = p.xs[(ii / TS) * (int64_t)D * TS + (int64_t)c * TS + ii % TS];
+  }
+  float bc[D], bh[D];  // warp box: centre, half-width
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    float lo = xi[0][c], hi = xi[0][c];
+#pragma unroll
+    for (int u = 1; u < TA; ++u) {
+      lo = fminf(lo, xi[u][c]);
+      hi = fmaxf(hi, xi[u][c]);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    bc[c] = 0.5f * (lo + hi);
+    bh[c] = 0.5f * (hi - lo);
+  }
+
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+  float S[TA], L[TA];
+#pragma unroll
+  for (int u = 0; u < TA; ++u) S[u] = L[u] = 0.f;
+
+  auto issue = [&](int r) {
+    const int stage = r % RS;
+    const int64_t tile = t_begin + r;
+    float* dst = smem + stage * kStageFloats;
+    mbar_arrive_expect_tx(&bars[stage], kStageFloats * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS, p.qh + tile * (int64_t)TS, TS * 4, &bars[stage]);
+    bulk_g2s(dst + (D + 1) * TS, p.ql + tile * (int64_t)TS, TS * 4, &bars[stage]);
+  };
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < RS; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RS, nt); ++issued) issue(issued);
+  const float s2h = p.k.s2h;
+
+  for (int r = 0; r < nt; ++r) {
+    if (tid == 0 && r >= 1 && r - 1 + RS < nt) {
+      fence_proxy_async_smem();
+      issue(r - 1 + RS);
+      ++issued;
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[r % RS], (r / RS) & 1));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    } else {
+      const float* st = smem + (r % RS) * kStageFloats;
+      const float* sq = st + D * TS;
+      const float* sl = st + (D + 1) * TS;
+      // near/far test of this warp's box against the tile's box
+      const float* tb = p.tbox + (int64_t)(t_begin + r) * 2 * D;
+      float dist2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const float g = fmaxf(0.f, fabsf(bc[c] - tb[c]) - bh[c] - tb[D + c]);
+        dist2 = fmaf(g, g, dist2);
+      }
+      if (s2h * dist2 <= FAR_E) {
+#pragma unroll 2
+        for (int j = 0; j < TS; ++j) {
+          const float qh = sq[j], ql = sl[j];
+#pragma unroll
+          for (int u = 0; u < TA; ++u)
+            acc_pair<D>(xi[u], st + j, qh, ql, S[u], L[u], p.k, tab_h, tab_l);
+        }
+      } else {
+        for (int j = 0; j < TS; ++j) {
+          const float qh = sq[j];
+#pragma unroll
+          for (int u = 0; u < TA; ++u) {
+            float r2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              const float dd = xi[u][c] - st[c * TS + j];
+              r2 = fmaf(dd, dd, r2);
+            }
+            L[u] = fmaf(qh, ex2(-s2h * r2), L[u]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RS], (r / RS) & 1);
+    __syncthreads();
+    return;
+  }
+  double* part = p.part + (int64_t)blockIdx.y * p.Npad;
+#pragma unroll
+  for (int u = 0; u < TA; ++u) {
+    const int64_t i = t0 + lane + 32 * u;
+    if (valid[u]) part[i] = (double)S[u] + (double)L[u];
+  }
+}
+
+struct AccFin {
+  const double* part;
+  int splits;
+  int64_t N, Npad;
+  const float* qh;
+  const float* ql;
+  double shift, cu, cy;
+  const float* u;
+  double* out;
+  double* dot;
+  double* dot_part;
+  unsigned* dot_count;
+};
+
+__global__ void __launch_bounds__(256) acc_finalize_kernel(const AccFin f) {
+  __shared__ double red[8];
+  __shared__ bool is_last;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double o = 0.0;
+  if (i < f.N) {
+    double y = 0.0;
+    for (int s = 0; s < f.splits; ++s) y += f.part[(int64_t)s * f.Npad + i];
+    y += f.shift * ((double)f.qh[i] + (double)f.ql[i]);
+    o = f.cy * y;
+    if (f.u) o += f.cu * (double)f.u[i];
+  }
+  if (i < f.Npad) f.out[i] = o;
+  if (f.dot) {
+    const double bs = block_sum(o * o, red);
+    if (threadIdx.x == 0) {
+      f.dot_part[blockIdx.x] = bs;
+      __threadfence();
+      is_last = atomicAdd(f.dot_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      double t = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += f.dot_part[b];
+      t = block_sum(t, red);
+      if (threadIdx.x == 0) {
+        *f.dot = t;
+        *f.dot_count = 0u;
+      }
+    }
+  }
+}
+
+// ln 2 in float-float, the Taylor coefficients (ln 2)^k / k! (k = 2..4) and
+// the table 2^(j/64), j = 0..63, in float-float.
+AccConst make_consts() {
+  AccConst k;
+  const double ln2 = std::log(2.0);
+  k.c1h = (float)ln2;
+  k.c1l = (float)(ln2 - (double)k.c1h);
+  k.c2 = (float)(ln2 * ln2 / 2.0);
+  k.c3 = (float)(ln2 * ln2 * ln2 / 6.0);
+  k.c4 = (float)(ln2 * ln2 * ln2 * ln2 / 24.0);
+  for (int j = 0; j < 64; ++j) {
+    const double v = std::exp2(j / 64.0);
+    k.th[j] = (float)v;
+    k.tl[j] = (float)(v - (double)k.th[j]);
+  }
+  return k;
+}
+
+template <int D, int TA>
+cudaError_t set_acc_attr() {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && done[dev]) return cudaSuccess;
+  const size_t shm = sizeof(float) * RS * (D + 2) * TS;
+  cudaError_t e = cudaFuncSetAttribute(mvp_acc_kernel<D, TA>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (!e && dev < 128) done[dev] = true;
+  return e;
+}
+
+template <int D, int TA>
+cudaError_t launch_acc(const AccParams& p, int splits, cudaStream_t st) {
+  const size_t shm = sizeof(float) * RS * (D + 2) * TS;
+  cudaError_t e = set_acc_attr<D, TA>();
+  if (e) return e;
+  dim3 grid((unsigned)((p.N + NT * TA - 1) / (NT * TA)), (unsigned)splits);
+  mvp_acc_kernel<D, TA><<<grid, NT, shm, st>>>(p);
+  return cudaGetLastError();
+}
+
+constexpr int ACC_TA = 2;
+
+struct AccPlan {
+  int splits, tiles_per_split;
+};
+
+AccPlan acc_plan(const PointsDev& P, int num_sms) {
+  const int ntiles = (int)(P.Npad / TS);
+  const int64_t ctas = (P.N + NT * ACC_TA - 1) / (NT * ACC_TA);
+  const int slots = num_sms * 2;
+  // fill the GPU about four times over, never below one tile per split
+  int splits = (int)std::min<int64_t>(ntiles, std::max<int64_t>(1, (4LL * slots + ctas - 1) / ctas));
+  AccPlan pl;
+  pl.tiles_per_split = (ntiles + splits - 1) / splits;
+  pl.splits = (ntiles + pl.tiles_per_split - 1) / pl.tiles_per_split;
+  return pl;
+}
+
+}  // namespace
+
+cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st) {
+  if (P.N == 0) return cudaSuccess;
+  const AccPlan pl = acc_plan(P, c.num_sms);
+  void* v;
+  cudaError_t e;
+  if ((e = c.ws.get("acc.part", sizeof(double) * pl.splits * (size_t)P.Npad, &v))) return e;
+  const unsigned fin_blocks = (unsigned)((P.Npad + 255) / 256);
+  if ((e = c.ws.get("acc.dotpart", sizeof(double) * fin_blocks, &v))) return e;
+  const bool fresh = c.ws.slots.find("acc.dotcnt") == c.ws.slots.end();
+  if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned), &v))) return e;
+  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned), st))) return e;
+  switch (P.d) {
+    case 1: return set_acc_attr<1, ACC_TA>();
+    case 2: return set_acc_attr<2, ACC_TA>();
+    case 3: return set_acc_attr<3, ACC_TA>();
+    case 4: return set_acc_attr<4, ACC_TA>();
+    case 5: return set_acc_attr<5, ACC_TA>();
+    case 6: return set_acc_attr<6, ACC_TA>();
+    case 7: return set_acc_attr<7, ACC_TA>();
+    case 8: return set_acc_attr<8, ACC_TA>();
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const float* ql,
+                           float shift, double cu, const float* u, double cy, double* out,
+                           double* dot, cudaStream_t st) {
+  if (P.N == 0) return cudaSuccess;
+  cudaError_t e = mvp_acc_reserve(c, P, st);
+  if (e) return e;
+  AccParams p{};
+  p.xs = P.xs;
+  p.N = P.N;
+  p.Npad = P.Npad;
+  p.qh = qh;
+  p.ql = ql;
+  p.tbox = P.tbox;
+  p.ntiles = (int)(P.Npad / TS);
+  p.err = c.d_err;
+  p.k = make_consts();
+  // s^2 = log2(e) / (2 sigma^2) in float-float from the double value
+  p.k.s2h = (float)P.s2;
+  p.k.s2l = (float)(P.s2 - (double)p.k.s2h);
+  const AccPlan pl = acc_plan(P, c.num_sms);
+  p.tiles_per_split = pl.tiles_per_split;
+  void *part, *dpart, *dcnt;
+  const unsigned fin_blocks = (unsigned)((P.Npad + 255) / 256);
+  if ((e = c.ws.get("acc.part", sizeof(double) * pl.splits * (size_t)P.Npad, &part))) return e;
+  if ((e = c.ws.get("acc.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
+  if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned), &dcnt))) return e;
+  p.part = (double*)part;
+  switch (P.d) {
+    case 1: e = launch_acc<1, ACC_TA>(p, pl.splits, st); break;
+    case 2: e = launch_acc<2, ACC_TA>(p, pl.splits, st); break;
+    case 3: e = launch_acc<3, ACC_TA>(p, pl.splits, st); break;
+    case 4: e = launch_acc<4, ACC_TA>(p, pl.splits, st); break;
+    case 5: e = launch_acc<5, ACC_TA>(p, pl.splits, st); break;
+    case 6: e = launch_acc<6, ACC_TA>(p, pl.splits, st); break;
+    case 7: e = launch_acc<7, ACC_TA>(p, pl.splits, st); break;
+    case 8: e = launch_acc<8, ACC_TA>(p, pl.splits, st); break;
+    default: return cudaErrorNotSupported;
+  }
+  if (e) return e;
+  AccFin f{};
+  f.part = p.part;
+  f.splits = pl.splits;
+  f.N = P.N;
+  f.Npad = P.Npad;
+  f.qh = qh;
+  f.ql = ql;
+  f.shift = shift;
+  f.cu = cu;
+  f.cy = cy;
+  f.u = u;
+  f.out = out;
+  f.dot = dot;
+  f.dot_part = (double*)dpart;
+  f.dot_count = (unsigned*)dcnt;
+  acc_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f);
+  return cudaGetLastError();
+}
+
+}  // namespace krr

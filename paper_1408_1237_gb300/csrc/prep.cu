@@ -263,6 +263,30 @@ __global__ void order_kernel(const int* __restrict__ flag, int64_t nblk, int* __
   if (threadIdx.x == 0) *n_exp = total;
 }
 
+// Bounding box of every source tile of TS sorted points (padded points repeat
+// the last real one, so including them leaves the box unchanged): one warp
+// per tile; tbox[t*2d + k] = centre, tbox[t*2d + d + k] = half-width.
+__global__ void tilebox_kernel(const float* __restrict__ xs, int64_t ntiles, int d,
+                               float* __restrict__ tbox) {
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= ntiles) return;
+  for (int k = 0; k < d; ++k) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int j = lane; j < TS; j += 32) {
+      const float v = xs[t * (int64_t)d * TS + (int64_t)k * TS + j];
+      lo = fminf(lo, v);
+      hi = fmaxf(hi, v);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if (lane == 0) {
+      tbox[t * 2 * d + k] = 0.5f * (lo + hi);
+      tbox[t * 2 * d + d + k] = 0.5f * (hi - lo);
+    }
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -287,7 +311,8 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.N = N;
   P.d = d;
   P.Npad = round_up(std::max<int64_t>(N, 1), PAD);
-  P.scale = (float)std::sqrt(std::log2(std::exp(1.0)) / (2.0 * (double)sigma * (double)sigma));
+  P.s2 = 1.0 / (std::log(2.0) * 2.0 * (double)sigma * (double)sigma);  // log2(e) / (2 sigma^2)
+  P.scale = (float)std::sqrt(P.s2);
   cudaError_t e;
   void *xs, *perm, *ka, *kb, *va, *vb, *hist, *bbp, *bb;
   const int nbb = (int)std::min<int64_t>(blocks_for(N, BBOX_THREADS), 256);
@@ -339,6 +364,11 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   blkinfo_kernel<<<blocks_for(P.nblk, 8), 256, 0, st>>>(P.xs, N, d, P.T, P.scale, P.nblk, P.ctr,
                                                        (int*)flag);
   order_kernel<<<1, SCAN_THREADS, 0, st>>>((const int*)flag, P.nblk, P.order, P.n_exp);
+  const int64_t ntiles = P.Npad / TS;
+  void* tbox;
+  if ((e = c.ws.get(t + ".tbox", sizeof(float) * 2 * d * ntiles, &tbox))) return e;
+  P.tbox = (float*)tbox;
+  tilebox_kernel<<<blocks_for(ntiles, 8), 256, 0, st>>>(P.xs, ntiles, d, P.tbox);
   return cudaGetLastError();
 }
 
