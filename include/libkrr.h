@@ -203,6 +203,22 @@ krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int d,
 krr_status krr_measure_alu_peaks(krr_handle h, double* ex2_per_s, double* ffma_per_s,
                                  double* ffma2_lanes_per_s, void* stream);
 
+/* Launch and timing counters for measurement (not part of the method). */
+typedef struct {
+    long long launches;     /* kernels the library launched since it was loaded
+                               (a launch captured into a CUDA graph counts once) */
+    int product_launches;   /* fast-product kernel launches timed since the
+                               last read                                        */
+    double product_ms;      /* their summed device time (CUDA events recorded
+                               on the stream each launch ran on)                */
+    double product_pairs;   /* target x source pairs they evaluated, per column */
+} krr_profile;
+/* Start (enable != 0) or stop timing the fast-product kernel on h; resets the
+ * timed list.  Timing adds two event records per product launch. */
+krr_status krr_profile_enable(krr_handle h, int enable);
+/* Fill *out, waiting for the recorded events, and reset the timed list. */
+krr_status krr_profile_read(krr_handle h, krr_profile* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,11 @@ class krr_solve_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class krr_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("product_launches", ctypes.c_int),
+                ("product_ms", ctypes.c_double), ("product_pairs", ctypes.c_double)]
+
+
 class krr_problem(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Xsol", ctypes.c_void_p),
                 ("N", ctypes.c_int64), ("gamma", ctypes.c_float)]
@@ -76,6 +81,8 @@ _SIGNATURES = {
                       _vp, ctypes.POINTER(krr_solve_info), _vp], _int),
     "krr_measure_alu_peaks": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
                                _vp], _int),
+    "krr_profile_enable": ([_vp, _int], _int),
+    "krr_profile_read": ([_vp, ctypes.POINTER(krr_profile)], _int),
 }
 
 
@@ -318,3 +325,16 @@ def krr_measure_alu_peaks(handle=None, stream=None):
     h.check(lib().krr_measure_alu_peaks(h.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                         stream))
     return a.value, b.value, c.value
+
+
+def krr_profile_enable(enable=True, handle=None):
+    h = handle or default_handle()
+    h.check(lib().krr_profile_enable(h.h, 1 if enable else 0))
+
+
+def krr_profile_read(handle=None):
+    """dict(launches, product_launches, product_ms, product_pairs); resets the timed list."""
+    h = handle or default_handle()
+    p = krr_profile()
+    h.check(lib().krr_profile_read(h.h, ctypes.byref(p)))
+    return {f: getattr(p, f) for f, _ in p._fields_}

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/libkrr.h"
 
 #ifndef __CUDACC__
@@ -10,6 +12,11 @@
 #endif
 
 namespace krr {
+
+// Kernels launched by the library since load (host-side count; a launch
+// captured into a CUDA graph counts once, at capture).
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Source tile length: sources move through shared memory in tiles of TS
 // points; every prepared point array is padded to a multiple of TS.

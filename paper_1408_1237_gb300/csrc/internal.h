@@ -5,6 +5,7 @@
 
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "../../include/libkrr.h"
 
@@ -62,6 +63,11 @@ struct Ctx {
   // caller's stream by ev_in / ev_out
   cudaStream_t work = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // profiling of the fast product kernel (krr_profile_enable / _read)
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
+  size_t prof_used = 0;              // events in use (even)
+  double prof_pairs = 0.0;
 };
 
 // ---- prep.cu

@@ -12,6 +12,8 @@
 
 namespace krr {
 
+std::atomic<long long> g_launches{0};
+
 cudaError_t Workspace::get(const std::string& name, size_t bytes, void** out) {
   bytes = std::max<size_t>(bytes, 256);
   auto it = slots.find(name);
@@ -203,12 +205,40 @@ krr_status krr_destroy(krr_handle h) {
   cudaEventDestroy(c.ev1);
   cudaEventDestroy(c.ev_in);
   cudaEventDestroy(c.ev_out);
+  for (auto ev : c.prof_ev) cudaEventDestroy(ev);
   cudaStreamDestroy(c.work);
   delete h;
   return KRR_OK;
 }
 
 const char* krr_last_error(krr_handle h) { return h ? h->ctx.last_error.c_str() : "NULL handle"; }
+
+krr_status krr_profile_enable(krr_handle h, int enable) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  h->ctx.profiling = enable != 0;
+  h->ctx.prof_used = 0;
+  h->ctx.prof_pairs = 0.0;
+  return KRR_OK;
+}
+
+krr_status krr_profile_read(krr_handle h, krr_profile* out) {
+  if (!h || !out) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  out->launches = g_launches.load();
+  out->product_launches = (int)(c.prof_used / 2);
+  out->product_ms = 0.0;
+  out->product_pairs = c.prof_pairs;
+  for (size_t k = 0; k + 1 < c.prof_used; k += 2) {
+    cudaError_t e = cudaEventSynchronize(c.prof_ev[k + 1]);
+    if (e) return cuda_error(c, e, "krr_profile_read");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.prof_ev[k], c.prof_ev[k + 1]);
+    out->product_ms += ms;
+  }
+  c.prof_used = 0;
+  c.prof_pairs = 0.0;
+  return KRR_OK;
+}
 
 krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float sigma, float gamma,
                           const float* Q, int m, float* Y, krr_precision prec, void* stream) {

@@ -464,7 +464,7 @@ struct Solver {
     KRR_WS("kry.Mp", Mp, n * 4);
 #undef KRR_WS
     vblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Np + VT - 1) / VT, 4LL * c.num_sms));
-    fill_zero_kernel<<<vblocks, VT, 0, st>>>(zero, Np);
+    fill_zero_kernel<<<vblocks, VT, 0, st>>>(zero, Np); count_launch();
     return cudaGetLastError();
   }
 
@@ -480,31 +480,31 @@ struct Solver {
     o.active = active;
     cudaError_t e = mvp_launch(c, P, P, p, p, mshift, inner_prec, o, st);
     if (e) return e;
-    cg_update_kernel<<<vblocks, VT, 0, st>>>(S, z, rr, p, Mp, Np, partials, cg_c);
-    cg_p_kernel<<<vblocks, VT, 0, st>>>(S, rr, p, Np, active);
+    cg_update_kernel<<<vblocks, VT, 0, st>>>(S, z, rr, p, Mp, Np, partials, cg_c); count_launch();
+    cg_p_kernel<<<vblocks, VT, 0, st>>>(S, rr, p, Np, active); count_launch();
     return cudaGetLastError();
   }
 
   // ---- Arnoldi step after the inner solve: Z[j] = z, w = K z, CGS2, Givens
   cudaError_t arnoldi_tail(const int* active) {
-    store_z_kernel<<<vblocks, VT, 0, st>>>(S, z, Z, Np, active);
+    store_z_kernel<<<vblocks, VT, 0, st>>>(S, z, Z, Np, active); count_launch();
     // w = K z_j with the compensated product: its error enters the flexible
     // Arnoldi relation K Z = V Hbar, and through it the true residual
     cudaError_t e = mvp_acc_launch(c, P, z, zero, gamma, 0.0, nullptr, 1.0, w, nullptr, st);
     if (e) return e;
-    cgs_dots_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, active);
-    cgs_update_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, arn_c, active);
-    cgs_final_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, active);
-    arn_advance_kernel<<<1, 1, 0, st>>>(S);
+    cgs_dots_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, active); count_launch();
+    cgs_update_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, arn_c, active); count_launch();
+    cgs_final_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, active); count_launch();
+    arn_advance_kernel<<<1, 1, 0, st>>>(S); count_launch();
     return cudaGetLastError();
   }
 
   cudaError_t cycle_tail(double tol_stop, const int* active) {
-    lsq_kernel<<<1, 1, 0, st>>>(S, active);
-    x_update_kernel<<<vblocks, VT, 0, st>>>(S, Z, Np, xh, xl, active);
+    lsq_kernel<<<1, 1, 0, st>>>(S, active); count_launch();
+    x_update_kernel<<<vblocks, VT, 0, st>>>(S, Z, Np, xh, xl, active); count_launch();
     cudaError_t e = residual();
     if (e) return e;
-    restart_check_kernel<<<1, 1, 0, st>>>(S, rst_c, tol_stop);
+    restart_check_kernel<<<1, 1, 0, st>>>(S, rst_c, tol_stop); count_launch();
     return cudaGetLastError();
   }
 
@@ -603,7 +603,7 @@ cudaError_t build_graph(Solver& s, double tol_stop, cudaGraphExec_t* exec) {
   if ((e = cudaGraphConditionalHandleCreate(&s.arn_c.h, rbody, 1, cudaGraphCondAssignDefault))) return fail(e);
   s.arn_c.use = 1;
   if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t {
-         v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, s.arn_c);
+         v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, s.arn_c); count_launch();
          return cudaGetLastError();
        })))
     return fail(e);
@@ -612,7 +612,7 @@ cudaError_t build_graph(Solver& s, double tol_stop, cudaGraphExec_t* exec) {
   s.cg_c.use = 1;
   if ((e = capture_into(s.st, abody, [&]() -> cudaError_t {
          cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
-                                                    s.partials, s.cg_c, nullptr);
+                                                    s.partials, s.cg_c, nullptr); count_launch();
          return cudaGetLastError();
        })))
     return fail(e);
@@ -685,9 +685,9 @@ krr_status fgmres_one(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec, KSta
   if ((e = cudaMemcpyAsync(s.S, &hs, sizeof(KState), cudaMemcpyHostToDevice, s.st)))
     return cuda_error(c, e, fn);
   cudaEventRecord(c.ev0, s.st);
-  solve_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials);
+  solve_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
   // the first restart check turns x0 = 0, r0 = b into the first cycle
-  restart_check_kernel<<<1, 1, 0, s.st>>>(s.S, Cond{}, 0.5 * cfg.tol);
+  restart_check_kernel<<<1, 1, 0, s.st>>>(s.S, Cond{}, 0.5 * cfg.tol); count_launch();
   const double tol_stop = 0.5 * cfg.tol;
   if (exec) {
     // the restart loop's default condition is 1: skip the graph when the
@@ -700,10 +700,10 @@ krr_status fgmres_one(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec, KSta
       KState h;
       if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
       if (!h.restart_cont) break;
-      v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, Cond{});
+      v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, Cond{}); count_launch();
       for (;;) {
         cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
-                                                   s.partials, Cond{}, nullptr);
+                                                   s.partials, Cond{}, nullptr); count_launch();
         for (;;) {
           if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
           if (!h.cg_cont) break;
@@ -803,7 +803,7 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
     KState hs;
     float ms = 0.f;
     if ((s = fgmres_one(sv, cfg, exec, hs, &ms))) return s;
-    scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, dXs + (size_t)col * N);
+    scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, dXs + (size_t)col * N); count_launch();
     if ((e = cudaGetLastError())) return cuda_error(c, e, fn);
     if (info) fill_info(hs, ms, info + col);
     if (hs.status != KRR_OK && worst == KRR_OK) worst = (krr_status)hs.status;

@@ -372,7 +372,7 @@ cudaError_t launch_typed(const MvpParams& p, int splits, cudaStream_t st) {
   cudaError_t e = set_attr<D, T>();
   if (e) return e;
   dim3 grid((unsigned)((p.nblk + NW - 1) / NW), (unsigned)splits);
-  mvp_f32_kernel<D, T><<<grid, NT, smem_bytes<D>(), st>>>(p);
+  mvp_f32_kernel<D, T><<<grid, NT, smem_bytes<D>(), st>>>(p); count_launch();
   return cudaGetLastError();
 }
 
@@ -479,7 +479,7 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
                        const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                        cudaStream_t st) {
-  (void)prec;
+  if (prec != KRR_FP32) return cudaErrorNotSupported;  // reduced precision: not built yet
   if (Tp.N == 0) return cudaSuccess;
   MvpParams p{};
   p.xt = Tp.xs;
@@ -507,6 +507,22 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &dcnt))) return e;
   p.part = (double*)part;
   p.fac = (float*)fac;
+  cudaEvent_t pev1 = nullptr;
+  if (c.profiling) {
+    if (c.prof_used + 2 > c.prof_ev.size() && c.prof_ev.size() < 8192) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev))) return e;
+        c.prof_ev.push_back(ev);
+      }
+    }
+    if (c.prof_used + 2 <= c.prof_ev.size()) {
+      cudaEventRecord(c.prof_ev[c.prof_used], st);
+      pev1 = c.prof_ev[c.prof_used + 1];
+      c.prof_used += 2;
+      c.prof_pairs += (double)Tp.N * (double)Sp.N;
+    }
+  }
   switch (Tp.d) {
     case 1: e = dispatch_T<1>(p, Tp.T, pl, st); break;
     case 2: e = dispatch_T<2>(p, Tp.T, pl, st); break;
@@ -519,6 +535,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
     default: return cudaErrorNotSupported;
   }
   if (e) return e;
+  if (pev1) cudaEventRecord(pev1, st);
   FinParams f{};
   f.part = p.part;
   f.splits = pl.splits;
@@ -530,7 +547,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   f.o = o;
   f.dot_part = (double*)dpart;
   f.dot_count = (unsigned*)dcnt;
-  mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f);
+  mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
 }
 

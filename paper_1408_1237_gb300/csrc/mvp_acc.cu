@@ -337,7 +337,7 @@ cudaError_t launch_acc(const AccParams& p, int splits, cudaStream_t st) {
   cudaError_t e = set_acc_attr<D, TA>();
   if (e) return e;
   dim3 grid((unsigned)((p.N + NT * TA - 1) / (NT * TA)), (unsigned)splits);
-  mvp_acc_kernel<D, TA><<<grid, NT, shm, st>>>(p);
+  mvp_acc_kernel<D, TA><<<grid, NT, shm, st>>>(p); count_launch();
   return cudaGetLastError();
 }
 
@@ -439,7 +439,7 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   f.dot = dot;
   f.dot_part = (double*)dpart;
   f.dot_count = (unsigned*)dcnt;
-  acc_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f);
+  acc_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
 }
 

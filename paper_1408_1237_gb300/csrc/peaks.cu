@@ -75,9 +75,9 @@ extern "C" krr_status krr_measure_alu_peaks(krr_handle h, double* ex2_per_s, dou
     float best = 1e30f;
     for (int rep = 0; rep < 4; ++rep) {
       cudaEventRecord(c.ev0, st);
-      if (k == 0) ex2_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f);
-      if (k == 1) ffma_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f);
-      if (k == 2) ffma2_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f);
+      if (k == 0) ex2_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f); count_launch();
+      if (k == 1) ffma_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f); count_launch();
+      if (k == 2) ffma2_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f); count_launch();
       cudaEventRecord(c.ev1, st);
       if ((e = cudaEventSynchronize(c.ev1))) return cuda_error(c, e, "krr_measure_alu_peaks");
       float ms;

@@ -294,14 +294,14 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 cudaError_t gather_sorted(const float* in, int64_t N, int m, const int* perm, int64_t Npad,
                           float* out, cudaStream_t st) {
   if (Npad == 0) return cudaSuccess;
-  gather_kernel<<<blocks_for(Npad, 256), 256, 0, st>>>(in, N, m, perm, Npad, out);
+  gather_kernel<<<blocks_for(Npad, 256), 256, 0, st>>>(in, N, m, perm, Npad, out); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t scatter_orig(const float* in, int64_t Npad, int64_t N, int m, const int* perm,
                          float* out, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  scatter_kernel<<<blocks_for(N, 256), 256, 0, st>>>(in, Npad, N, m, perm, out);
+  scatter_kernel<<<blocks_for(N, 256), 256, 0, st>>>(in, Npad, N, m, perm, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -330,26 +330,26 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.perm = (int*)perm;
 
   bbox_partial_kernel<<<nbb, BBOX_THREADS, sizeof(float) * 2 * d * (BBOX_THREADS / 32), st>>>(
-      X, N, d, (float*)bbp, c.d_err);
-  bbox_final_kernel<<<1, 128, 0, st>>>((const float*)bbp, nbb, d, (float*)bb);
+      X, N, d, (float*)bbp, c.d_err); count_launch();
+  bbox_final_kernel<<<1, 128, 0, st>>>((const float*)bbp, nbb, d, (float*)bb); count_launch();
   const int dk = std::min(d, 30);
   const int bits = std::max(1, std::min(16, 30 / dk));
   morton_kernel<<<blocks_for(N, 256), 256, 0, st>>>(X, N, d, dk, bits, (const float*)bb,
-                                                    (uint32_t*)ka, (int*)va);
+                                                    (uint32_t*)ka, (int*)va); count_launch();
   const int key_bits = bits * dk;
   uint32_t *kin = (uint32_t*)ka, *kout = (uint32_t*)kb;
   int *vin = (int*)va, *vout = (int*)vb;
   for (int shift = 0; shift < key_bits; shift += 8) {
-    radix_hist_kernel<<<nchunks, SORT_THREADS, 0, st>>>(kin, N, shift, (uint32_t*)hist, nchunks);
-    radix_scan_kernel<<<1, SCAN_THREADS, 0, st>>>((uint32_t*)hist, 256LL * nchunks);
+    radix_hist_kernel<<<nchunks, SORT_THREADS, 0, st>>>(kin, N, shift, (uint32_t*)hist, nchunks); count_launch();
+    radix_scan_kernel<<<1, SCAN_THREADS, 0, st>>>((uint32_t*)hist, 256LL * nchunks); count_launch();
     radix_scatter_kernel<<<nchunks, SORT_THREADS, 0, st>>>(kin, vin, N, shift,
                                                            (const uint32_t*)hist, nchunks, kout,
-                                                           vout);
+                                                           vout); count_launch();
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
   if ((e = cudaMemcpyAsync(P.perm, vin, sizeof(int) * N, cudaMemcpyDeviceToDevice, st))) return e;
-  pack_kernel<<<blocks_for(P.Npad, 256), 256, 0, st>>>(X, N, P.Npad, d, P.perm, P.xs);
+  pack_kernel<<<blocks_for(P.Npad, 256), 256, 0, st>>>(X, N, P.Npad, d, P.perm, P.xs); count_launch();
 
   P.T = mvp_targets_per_thread(d, N);
   P.nblk = (N + 32 * P.T - 1) / (32 * P.T);
@@ -362,13 +362,13 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.order = (int*)order;
   P.n_exp = (int*)nexp;
   blkinfo_kernel<<<blocks_for(P.nblk, 8), 256, 0, st>>>(P.xs, N, d, P.T, P.scale, P.nblk, P.ctr,
-                                                       (int*)flag);
-  order_kernel<<<1, SCAN_THREADS, 0, st>>>((const int*)flag, P.nblk, P.order, P.n_exp);
+                                                       (int*)flag); count_launch();
+  order_kernel<<<1, SCAN_THREADS, 0, st>>>((const int*)flag, P.nblk, P.order, P.n_exp); count_launch();
   const int64_t ntiles = P.Npad / TS;
   void* tbox;
   if ((e = c.ws.get(t + ".tbox", sizeof(float) * 2 * d * ntiles, &tbox))) return e;
   P.tbox = (float*)tbox;
-  tilebox_kernel<<<blocks_for(ntiles, 8), 256, 0, st>>>(P.xs, ntiles, d, P.tbox);
+  tilebox_kernel<<<blocks_for(ntiles, 8), 256, 0, st>>>(P.xs, ntiles, d, P.tbox); count_launch();
   return cudaGetLastError();
 }
 
