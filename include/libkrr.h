@@ -59,7 +59,9 @@ typedef enum {
     KRR_NOT_CONVERGED = 5,     /* iteration cap reached before the tolerance    */
     KRR_ERR_BREAKDOWN = 6,     /* Krylov breakdown that is not a lucky one      */
     KRR_ERR_TIMEOUT = 7,       /* a bounded device wait ran out                 */
-    KRR_ERR_UNIMPLEMENTED = 8  /* option combination not built                  */
+    KRR_ERR_UNIMPLEMENTED = 8, /* option combination not built                  */
+    KRR_ERR_SIZE_LIMIT = 9     /* problem larger than krr_kernel_mvp_noalloc's
+                                  fixed scratch array accepts                   */
 } krr_status;
 
 /* Arithmetic of the kernel product.  KRR_FP32 sums in float32 with a
@@ -218,6 +220,28 @@ typedef struct {
 krr_status krr_profile_enable(krr_handle h, int enable);
 /* Fill *out, waiting for the recorded events, and reset the timed list. */
 krr_status krr_profile_read(krr_handle h, krr_profile* out);
+
+/* ------------------------------------------------ no-allocation product
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: code running inside host callbacks or
+ * allocator hooks, processes whose device memory pool belongs to another
+ * framework, and latency-bound paths where cudaMalloc's implicit device
+ * synchronisation is not allowed.  Such callers cannot create a krr_handle
+ * either, since a handle grows its workspace with cudaMalloc.
+ * Result: that of krr_kernel_mvp with KRR_FP32, for DEVICE arrays X (N x d
+ * row-major), Q and Y (N x m column-major) with N <= 16384, d <= 8 and
+ * m <= 16.  Larger problems return KRR_ERR_SIZE_LIMIT; host arrays and bad
+ * values return KRR_ERR_INVALID_ARG.
+ * It allocates nothing.  Its scratch is one fixed device array of 10,405,376
+ * bytes, held by every GPU that loads the library until the process exits.
+ * The first call made with a device current looks up that array's device
+ * address (cudaGetSymbolAddress), so make it before any stream capture.  All
+ * calls on a device share the array and it keeps the last call's contents;
+ * calls that overlap on the GPU race on it and give wrong results.
+ * Asynchronous on `stream`. */
+krr_status krr_kernel_mvp_noalloc(const float* X, int64_t N, int d, float sigma,
+                                  float gamma, const float* Q, int m, float* Y,
+                                  void* stream);
 
 #ifdef __cplusplus
 }

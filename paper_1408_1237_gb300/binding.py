@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libkrr.so")
 
 KRR_OK, KRR_ERR_INVALID_ARG, KRR_ERR_CUDA, KRR_ERR_OOM, KRR_ERR_NONFINITE = 0, 1, 2, 3, 4
 KRR_NOT_CONVERGED, KRR_ERR_BREAKDOWN, KRR_ERR_TIMEOUT, KRR_ERR_UNIMPLEMENTED = 5, 6, 7, 8
+KRR_ERR_SIZE_LIMIT = 9
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
 
 
@@ -82,6 +83,7 @@ _SIGNATURES = {
     "krr_measure_alu_peaks": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
                                _vp], _int),
     "krr_profile_enable": ([_vp, _int], _int),
+    "krr_kernel_mvp_noalloc": ([_vp, _i64, _int, _f, _f, _vp, _int, _vp, _vp], _int),
     "krr_profile_read": ([_vp, ctypes.POINTER(krr_profile)], _int),
 }
 
@@ -338,3 +340,20 @@ def krr_profile_read(handle=None):
     p = krr_profile()
     h.check(lib().krr_profile_read(h.h, ctypes.byref(p)))
     return {f: getattr(p, f) for f, _ in p._fields_}
+
+
+def krr_kernel_mvp_noalloc(X, Q, sigma, gamma, out=None, stream=None):
+    """The kernel product through the entry point that allocates no device
+    memory (for callers that cannot allocate: callbacks, allocator hooks,
+    foreign memory pools, latency-bound paths).  Device tensors only;
+    N <= 16384, d <= 8, m <= 16.  The output is allocated here, by the caller
+    side, unless `out` is given."""
+    N, d = X.shape
+    m = _cols(Q, N)
+    Y = out if out is not None else _empty_like_cols(Q, m, N)
+    s = lib().krr_kernel_mvp_noalloc(_ptr(X), N, d, sigma, gamma, _ptr(Q), m, _ptr(Y),
+                                     _stream(stream, X, Q, Y))
+    if s != KRR_OK:
+        raise KrrError(s, "krr_kernel_mvp_noalloc (limits: device arrays, N <= 16384, "
+                          "d <= 8, m <= 16)")
+    return Y

@@ -151,6 +151,7 @@ const char* krr_status_string(krr_status s) {
     case KRR_ERR_BREAKDOWN: return "KRR_ERR_BREAKDOWN";
     case KRR_ERR_TIMEOUT: return "KRR_ERR_TIMEOUT";
     case KRR_ERR_UNIMPLEMENTED: return "KRR_ERR_UNIMPLEMENTED";
+    case KRR_ERR_SIZE_LIMIT: return "KRR_ERR_SIZE_LIMIT";
   }
   return "KRR_UNKNOWN";
 }
