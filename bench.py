@@ -31,6 +31,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP32 form"
+# DRAM bytes (read + write) of one product-kernel launch on the 2^20-point
+# workload, from one ncu capture (profiles/mvp_f32_kernel_cube1M_d3.md); valid
+# only for the kernel source it was taken on.
+TRAFFIC = {"source": "paper_1408_1237_gb300/csrc/mvp.cu", "sha1": "c6b59369cc94b9a6bbcad94ae2afbf5950649c4c",
+           "bytes": 23.76e6 + 84.93e6}
 MVP_N, MVP_D = 1 << 20, 3
 
 
@@ -305,7 +310,7 @@ def run_libkrr(args):
             },
             "roofline": {
                 "bound": "alu", "achieved": achieved, "peak": peak_pairs / 1e9,
-                "unit": "Gpairs/s", "frac": achieved * 1e9 / peak_pairs, "traffic": None,
+                "unit": "Gpairs/s", "frac": achieved * 1e9 / peak_pairs, "traffic": traffic_bytes(),
                 "kernel": "mvp_f32_kernel", "launch_ms": kern_ms,
                 "peak_source": "measured on this GPU: min(MUFU.EX2 rate, FP32 lane rate/(d+1)) = "
                                f"min({ex2_rate / 1e12:.2f}e12, {fp32_lanes / 1e12:.2f}e12/{MVP_D + 1})",
@@ -323,6 +328,17 @@ def run_libkrr(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def traffic_bytes():
+    """ncu DRAM bytes per product launch, or None once the kernel changed."""
+    import hashlib
+    path = os.path.join(ROOT, TRAFFIC["source"])
+    try:
+        h = hashlib.sha1(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return TRAFFIC["bytes"] if h == TRAFFIC["sha1"] else None
 
 
 def solve_once(K, torch, p, dev, stream, inner_prec):
