@@ -119,6 +119,25 @@ struct MvpOut {
 cudaError_t mvp_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, cudaStream_t st);
 cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st);
 
+// Several right-hand sides at once: Y[:, c] = (K_hat + shift I) Q[:, c] for
+// c < m (m <= 16), Q sorted with column stride S.Npad, qdiag with column
+// stride T.Npad.  Output per column c: out_f + c*T.Npad (sorted) and/or
+// out_orig + c*T.N (original order); the dot / step-length epilogue of o
+// applies to column 0 only.  prec KRR_FP32 evaluates on the tensor cores
+// with hi/lo-split operands (float32-grade); KRR_FP16 / KRR_BF16 with single
+// half-precision operands.
+cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
+                             const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
+                             cudaStream_t st);
+// ---- mvp_tc.cu: tensor-core partial sums of the expanded-form warp blocks
+// dry = true only sets the kernel attributes (before any graph capture).
+cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
+                            bool split, bool bf, int splits, int tiles_per_split, double* part,
+                            float* fac, const int* active, cudaStream_t st, bool dry = false);
+// Workspace and attributes of mvp_multi_launch with m columns and prec.
+cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, int m,
+                              krr_precision prec, cudaStream_t st);
+
 // Single right-hand side product over prepared targets T and sources S
 // (the same object for the square product).  q: sorted source weights
 // (length S.Npad, zero padded); qdiag: sorted target weights for the shift

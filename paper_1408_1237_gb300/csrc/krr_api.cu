@@ -269,12 +269,21 @@ krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float 
   void* qs;
   if ((e = c.ws.get("mvp.qs", sizeof(float) * P.Npad * m, &qs))) return cuda_error(c, e, fn);
   if ((e = gather_sorted(dQ, N, m, P.perm, P.Npad, (float*)qs, st))) return cuda_error(c, e, fn);
-  for (int col = 0; col < m; ++col) {
-    const float* qc = (const float*)qs + (size_t)col * P.Npad;
+  if (m == 1 || m > 16) {
+    for (int col = 0; col < m; ++col) {
+      const float* qc = (const float*)qs + (size_t)col * P.Npad;
+      MvpOut o;
+      o.perm = P.perm;
+      o.out_orig = dY + (size_t)col * N;
+      if ((e = mvp_launch(c, P, P, qc, qc, gamma, prec, o, st))) return cuda_error(c, e, fn);
+    }
+  } else {
+    // all columns in one pass: each kernel value serves m columns on the tensor cores
     MvpOut o;
     o.perm = P.perm;
-    o.out_orig = dY + (size_t)col * N;
-    if ((e = mvp_launch(c, P, P, qc, qc, gamma, prec, o, st))) return cuda_error(c, e, fn);
+    o.out_orig = dY;
+    if ((e = mvp_multi_launch(c, P, P, (const float*)qs, m, (const float*)qs, gamma, prec, o, st)))
+      return cuda_error(c, e, fn);
   }
   if (sY) {
     if ((e = cudaMemcpyAsync(Y, dY, sizeof(float) * N * m, cudaMemcpyDeviceToHost, st)))

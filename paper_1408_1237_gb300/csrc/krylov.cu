@@ -781,6 +781,8 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
   if ((e = sv.alloc(cfg.restart))) return cuda_error(c, e, fn);
   // size every workspace buffer now: nothing may allocate inside a capture
   if ((e = mvp_reserve(c, sv.P, sv.P, st))) return cuda_error(c, e, fn);
+  if (cfg.inner_prec != KRR_FP32 && (e = mvp_multi_reserve(c, sv.P, sv.P, 1, cfg.inner_prec, st)))
+    return cuda_error(c, e, fn);
   if ((e = mvp_acc_reserve(c, sv.P, st))) return cuda_error(c, e, fn);
   cudaGraphExec_t exec = nullptr;
   sv.cg_c = sv.arn_c = sv.rst_c = Cond{};

@@ -65,6 +65,8 @@ struct MvpParams {
   int* err;
   float s;              // sqrt(log2(e) / (2 sigma^2))
   const int* active;    // predication flag (null: always run)
+  int64_t part_stride;  // distance between splits in part (Nt_pad for one column)
+  int direct_only;      // skip expanded-form warp blocks (the tensor-core kernel does them)
 };
 
 // Warp-cooperative transform of one raw source tile for this warp's centre:
@@ -178,10 +180,12 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
 
   // ---- this warp's target block
   const int64_t slot = (int64_t)blockIdx.x * NW + warp;
-  const bool live = slot < p.nblk;
+  const int64_t nexp = *p.tn_exp;
+  if (p.direct_only && ((int64_t)blockIdx.x + 1) * NW <= nexp) return;  // CTA fully expanded
+  const bool live = slot < p.nblk && !(p.direct_only && slot < nexp);
   const int64_t blk = live ? p.torder[slot] : 0;
   const int64_t last = min(((int64_t)blockIdx.x + 1) * NW, p.nblk);  // CTA's block slots end
-  const bool expanded = last <= (int64_t)(*p.tn_exp);  // uniform over the CTA
+  const bool expanded = last <= nexp;  // uniform over the CTA
   float ctr[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   }
 
   if (live) {
-    double* part = p.part + (int64_t)blockIdx.y * p.Nt_pad;
+    double* part = p.part + (int64_t)blockIdx.y * p.part_stride;
 #pragma unroll
     for (int u = 0; u < T; ++u) {
       const int64_t i = blk * 32 * T + lane + 32 * u;
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
 struct FinParams {
   const double* part;
   int splits;
+  int64_t part_stride;
   int64_t N, Npad;
   const float* fac;
   const float* qdiag;
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
   double out = 0.0, dotv = 0.0;
   if (i < f.N) {
     double s = 0.0;
-    for (int sp = 0; sp < f.splits; ++sp) s += f.part[(int64_t)sp * f.Npad + i];
+    for (int sp = 0; sp < f.splits; ++sp) s += f.part[(int64_t)sp * f.part_stride + i];
     double y = (double)f.fac[i] * s;
     if (f.qdiag) y += (double)f.shift * (double)f.qdiag[i];
     out = (double)f.o.alpha * y;
@@ -479,7 +484,7 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
                        const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                        cudaStream_t st) {
-  if (prec != KRR_FP32) return cudaErrorNotSupported;  // reduced precision: not built yet
+  if (prec != KRR_FP32) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
   if (Tp.N == 0) return cudaSuccess;
   MvpParams p{};
   p.xt = Tp.xs;
@@ -494,6 +499,8 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   p.ntiles = (int)(Sp.Npad / TS);
   p.s = Sp.scale;
   p.active = o.active;
+  p.part_stride = Tp.Npad;
+  p.direct_only = 0;
   p.err = c.d_err;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
   const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms);
@@ -539,6 +546,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   FinParams f{};
   f.part = p.part;
   f.splits = pl.splits;
+  f.part_stride = Tp.Npad;
   f.N = Tp.N;
   f.Npad = Tp.Npad;
   f.fac = p.fac;
@@ -549,6 +557,98 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   f.dot_count = (unsigned*)dcnt;
   mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m,
+                              krr_precision prec, cudaStream_t st) {
+  if (Tp.N == 0) return cudaSuccess;
+  cudaError_t e = mvp_reserve(c, Tp, Sp, st);
+  if (e) return e;
+  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms);
+  void* v;
+  if ((e = c.ws.get("mvp.partm", sizeof(double) * pl.splits * (size_t)m * Tp.Npad, &v))) return e;
+  return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pl.splits,
+                         pl.tiles_per_split, nullptr, nullptr, nullptr, st, true);
+}
+
+cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* Q, int m,
+                             const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
+                             cudaStream_t st) {
+  if (Tp.N == 0) return cudaSuccess;
+  if (Tp.d < 1 || Tp.d > 8 || m < 1 || m > 16) return cudaErrorNotSupported;
+  MvpParams p{};
+  p.xt = Tp.xs;
+  p.Nt = Tp.N;
+  p.Nt_pad = Tp.Npad;
+  p.tctr = Tp.ctr;
+  p.torder = Tp.order;
+  p.tn_exp = Tp.n_exp;
+  p.nblk = Tp.nblk;
+  p.xs = Sp.xs;
+  p.ntiles = (int)(Sp.Npad / TS);
+  p.err = c.d_err;
+  p.s = Sp.scale;
+  p.active = o.active;
+  p.part_stride = (int64_t)m * Tp.Npad;
+  p.direct_only = 1;
+  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms);
+  cudaError_t e = mvp_reserve(c, Tp, Sp, st);
+  if (e) return e;
+  void *part, *fac, *dpart, *dcnt;
+  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
+  if ((e = c.ws.get("mvp.partm", sizeof(double) * pl.splits * (size_t)m * Tp.Npad, &part))) return e;
+  if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &fac))) return e;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &dcnt))) return e;
+  p.part = (double*)part;
+  p.fac = (float*)fac;
+  // expanded-form blocks: all columns on the tensor cores
+  if ((e = mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pl.splits,
+                           pl.tiles_per_split, p.part, p.fac, o.active, st)))
+    return e;
+  // direct-form blocks: float32 CUDA-core kernel, one column at a time
+  for (int col = 0; col < m; ++col) {
+    MvpParams pc = p;
+    pc.q = Q + (size_t)col * Sp.Npad;
+    pc.part = p.part + (size_t)col * Tp.Npad;
+    switch (Tp.d) {
+      case 1: e = dispatch_T<1>(pc, Tp.T, pl, st); break;
+      case 2: e = dispatch_T<2>(pc, Tp.T, pl, st); break;
+      case 3: e = dispatch_T<3>(pc, Tp.T, pl, st); break;
+      case 4: e = dispatch_T<4>(pc, Tp.T, pl, st); break;
+      case 5: e = dispatch_T<5>(pc, Tp.T, pl, st); break;
+      case 6: e = dispatch_T<6>(pc, Tp.T, pl, st); break;
+      case 7: e = dispatch_T<7>(pc, Tp.T, pl, st); break;
+      default: e = dispatch_T<8>(pc, Tp.T, pl, st); break;
+    }
+    if (e) return e;
+  }
+  for (int col = 0; col < m; ++col) {
+    FinParams f{};
+    f.part = p.part + (size_t)col * Tp.Npad;
+    f.splits = pl.splits;
+    f.part_stride = (int64_t)m * Tp.Npad;
+    f.N = Tp.N;
+    f.Npad = Tp.Npad;
+    f.fac = p.fac;
+    f.qdiag = qdiag ? qdiag + (size_t)col * Tp.Npad : nullptr;
+    f.shift = shift;
+    f.o = o;
+    if (col > 0) {
+      f.o.dot = nullptr;
+      f.o.dotw = nullptr;
+      f.o.ratio_out = nullptr;
+    }
+    if (o.out_f) f.o.out_f = o.out_f + (size_t)col * Tp.Npad;
+    if (o.out_d) f.o.out_d = o.out_d + (size_t)col * Tp.Npad;
+    if (o.out_orig) f.o.out_orig = o.out_orig + (size_t)col * Tp.N;
+    if (o.u) f.o.u = o.u + (size_t)col * Tp.Npad;
+    f.dot_part = (double*)dpart;
+    f.dot_count = (unsigned*)dcnt;
+    mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
+    if ((e = cudaGetLastError())) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace krr

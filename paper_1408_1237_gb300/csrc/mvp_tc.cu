@@ -1,0 +1,505 @@
+// Tensor-core kernel product for several right-hand sides and for the
+// reduced-precision inner product (hot-path steps A3/A4):
+//
+//   Y[i, c] = sum_j 2^(-s^2 |x_i - x_j|^2) Q[j, c]        (Eqs. 1-2)
+//
+// over the expanded-form warp blocks of prep.cu (compact target blocks with
+// centre c, x^ = s (x - c), |x^_i|^2 <= EXPANDED_R2), written as two dense
+// contractions on the tensor cores (mma.sync m16n8k16, f16 or bf16 inputs,
+// f32 accumulation) around one special-function step:
+//
+//  1. E = A B^T with A_i = [x^_i, 1] and B_j = [2 x^_j, b_j], b_j = -|x^_j|^2,
+//     so that E_ij = -|x^_i - x^_j|^2 + |x^_i|^2.  A and B are split into
+//     f16 hi + lo parts stacked along the contraction (K) dimension,
+//     A' = [Ah, Ah, Al, Al], B' = [Bh, Bl, Bh, Bl] (three terms when four do
+//     not fit), so one MMA yields E to about 2^-33 relative: FP32-grade
+//     exponents at d <= 3, about 2^-22 otherwise.
+//  2. P = 2^E by MUFU.EX2 straight from the accumulator registers; the
+//     accumulator fragment of the first MMA is the operand fragment of the
+//     second (no shared-memory round trip); 2^(-|x^_i|^2) is applied by the
+//     finalize kernel.
+//  3. Y += P Q: in f16 for the reduced-precision product, or with P and Q
+//     split hi + lo (three MMAs: Ph Qh + Pl Qh + Ph Ql) for float32-grade
+//     results, folded into float32 Kahan sums every few source tiles.
+//
+// The tensor work per pair (2m flops for P Q plus 2 x 16 for E) is far below
+// even the mma.sync peak; the kernel is bound by MUFU.EX2 and the f32->f16
+// packing, and the accumulation into many right-hand sides is nearly free.
+// Operands stay in registers, which is why mma.sync (register fragments) is
+// used rather than tcgen05 (operands in shared or tensor memory).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace krr {
+namespace {
+
+constexpr int RS = 2;  // raw stages
+
+struct TcParams {
+  const float* xt;    // targets (tile-blocked SoA, raw)
+  int64_t Nt, Nt_pad;
+  const float* tctr;  // warp-block centres
+  const int* torder;
+  const int* tn_exp;
+  int64_t nblk;
+  int WB;             // warp-block size (targets)
+  const float* xs;    // sources (tile-blocked SoA, raw)
+  const float* Q;     // sorted source weights, m columns of stride Ns_pad
+  int64_t Ns_pad;
+  int m;
+  int ntiles, tiles_per_split;
+  double* part;       // [split][col][Nt_pad]
+  float* fac;         // [Nt_pad]
+  int* err;
+  float s;
+  const int* active;
+};
+
+// Terms of the split exponent: 4 (Ah Bh + Ah Bl + Al Bh + Al Bl) when 4(D+1)
+// fits the contraction, else 3; contraction steps of 16.
+template <int D>
+struct ExpLayout {
+  static constexpr int W = D + 1;
+  static constexpr int TERMS = (4 * W <= 16 || (4 * W > 16 && 4 * W <= 32 && D > 4)) ? 4 : 3;
+  static constexpr int KSTEPS = (TERMS * W + 15) / 16;
+  static constexpr int KV = 16 * KSTEPS;              // halves per K-vector
+  static constexpr int KV_STRIDE_W = KSTEPS == 1 ? 12 : 20;  // 32-bit words, bank-conflict free
+};
+
+template <bool BF>
+struct Half;
+template <>
+struct Half<false> {
+  using T = __half;
+  using T2 = __half2;
+  static __device__ __forceinline__ T from(float v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ float to(T v) { return __half2float(v); }
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
+    T2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float2 unpack(uint32_t u) {
+    T2 h = *reinterpret_cast<T2*>(&u);
+    return __half22float2(h);
+  }
+};
+template <>
+struct Half<true> {
+  using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ T from(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float to(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
+    T2 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float2 unpack(uint32_t u) {
+    T2 h = *reinterpret_cast<T2*>(&u);
+    return __bfloat1622float2(h);
+  }
+};
+
+template <bool BF>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  if constexpr (BF) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  } else {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  }
+}
+
+// Value of K-vector slot k for the split vector v (hi/lo per component):
+// A' = [h, h, l, l] (operand A) or B' = [h, l, h, l] (operand B); 3-term
+// layouts drop the last block.
+template <int D>
+__device__ __forceinline__ float kv_value(const float (&h)[D + 1], const float (&l)[D + 1], int k,
+                                          bool is_a) {
+  constexpr int W = D + 1;
+  constexpr int TERMS = ExpLayout<D>::TERMS;
+  const int term = k / W, comp = k % W;
+  if (term >= TERMS) return 0.f;
+  const bool lo = is_a ? (term >= 2) : (term & 1);
+  float v = 0.f;
+#pragma unroll
+  for (int c = 0; c < W; ++c)
+    if (c == comp) v = lo ? l[c] : h[c];
+  return v;
+}
+
+template <int D, int MT, int NRT, bool SPLIT, bool BF>
+__global__ void __launch_bounds__(256) mvp_tc_kernel(const TcParams p) {
+  using L = ExpLayout<D>;
+  using H = Half<BF>;
+  constexpr int W = D + 1;
+  constexpr int MC = 8 * NRT;  // padded right-hand sides
+  constexpr int QSTRIDE_W = 132;  // words per column of a source tile (256 halves + pad)
+  extern __shared__ __align__(128) float smem[];
+  const int nthreads = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  __shared__ __align__(8) uint64_t bars[RS];
+  __shared__ volatile int abort_flag;
+  if (p.active && *p.active == 0) return;
+  const int64_t nexp = *p.tn_exp;
+  if ((int64_t)blockIdx.x >= nexp) return;  // direct-form blocks: CUDA-core kernel
+
+  const int raw_floats = (D + p.m) * TS;
+  float* raw = smem;                                                  // RS stages
+  uint32_t* kvb = reinterpret_cast<uint32_t*>(smem + RS * raw_floats);  // 2 x TS x KV_STRIDE_W
+  uint32_t* qb = kvb + 2 * TS * L::KV_STRIDE_W;                         // 2 x (SPLIT?2:1) x MC x QSTRIDE_W
+  constexpr int QBUF_W = (SPLIT ? 2 : 1) * MC * QSTRIDE_W;
+
+  const int64_t blk = p.torder[blockIdx.x];
+  float ctr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
+
+  // ---- operand A' of the exponent MMA for this warp's m-tiles (constant)
+  uint32_t afr[MT][L::KSTEPS][4];
+  const int64_t row0 = blk * p.WB + (int64_t)warp * 16 * MT;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {  // rows g and g + 8
+      const int64_t i = row0 + mt * 16 + g + 8 * half;
+      const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+      float ah[W], al[W];
+      float r2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float x = p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
+        const float xh = p.s * (x - ctr[k]);
+        r2 = fmaf(xh, xh, r2);
+        ah[k] = H::to(H::from(xh));
+        al[k] = xh - ah[k];
+      }
+      ah[D] = 1.f;
+      al[D] = 0.f;
+      if (blockIdx.y == 0 && t == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
+#pragma unroll
+      for (int ks = 0; ks < L::KSTEPS; ++ks) {
+        const int k0 = 16 * ks + 2 * t;
+        afr[mt][ks][half] = H::pack(kv_value<D>(ah, al, k0, true), kv_value<D>(ah, al, k0 + 1, true));
+        afr[mt][ks][half + 2] =
+            H::pack(kv_value<D>(ah, al, k0 + 8, true), kv_value<D>(ah, al, k0 + 9, true));
+      }
+    }
+  }
+
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+
+  float acc[MT][NRT][4];
+  float S[MT][NRT][4], C[MT][NRT][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int rt = 0; rt < NRT; ++rt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][rt][e] = S[mt][rt][e] = C[mt][rt][e] = 0.f;
+
+  auto issue = [&](int r) {
+    const int stage = r % RS;
+    const int64_t tile = t_begin + r;
+    float* dst = raw + stage * raw_floats;
+    mbar_arrive_expect_tx(&bars[stage], (uint32_t)raw_floats * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    for (int c = 0; c < p.m; ++c)
+      bulk_g2s(dst + (D + c) * TS, p.Q + (int64_t)c * p.Ns_pad + tile * (int64_t)TS, TS * 4,
+               &bars[stage]);
+  };
+
+  // CTA-wide transform of raw tile r into buffer b: source K-vectors and the
+  // weights in half precision (hi, and lo when split)
+  auto transform = [&](int r, int b) {
+    const float* rs = raw + (r % RS) * raw_floats;
+    uint32_t* kv = kvb + b * TS * L::KV_STRIDE_W;
+    uint32_t* qq = qb + b * QBUF_W;
+    for (int j = tid; j < TS; j += nthreads) {
+      float bh[W], bl[W];
+      float bb = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float xh = p.s * (rs[k * TS + j] - ctr[k]);
+        bb = fmaf(-xh, xh, bb);
+        const float v = 2.f * xh;
+        bh[k] = H::to(H::from(v));
+        bl[k] = v - bh[k];
+      }
+      if (bb < -30000.f) {  // farther than any target can see: contributes 0
+#pragma unroll
+        for (int k = 0; k < D; ++k) bh[k] = bl[k] = 0.f;
+        bb = -30000.f;
+      }
+      bh[D] = H::to(H::from(bb));
+      bl[D] = bb - bh[D];
+      uint16_t hv[L::KV];
+#pragma unroll
+      for (int k = 0; k < L::KV; ++k) {
+        const typename H::T hk = H::from(kv_value<D>(bh, bl, k, false));
+        hv[k] = *reinterpret_cast<const uint16_t*>(&hk);
+      }
+#pragma unroll
+      for (int w = 0; w < L::KV / 2; ++w)
+        kv[j * L::KV_STRIDE_W + w] = (uint32_t)hv[2 * w] | ((uint32_t)hv[2 * w + 1] << 16);
+    }
+    // weights: column c of the tile as halves at qq[c*QSTRIDE_W*2 + j]
+    uint16_t* qh = reinterpret_cast<uint16_t*>(qq);
+    uint16_t* ql = qh + MC * QSTRIDE_W * 2;
+    for (int e = tid; e < MC * TS; e += nthreads) {
+      const int c = e / TS, j = e % TS;
+      const float v = c < p.m ? rs[(D + c) * TS + j] : 0.f;
+      const typename H::T h = H::from(v);
+      qh[c * QSTRIDE_W * 2 + j] = *reinterpret_cast<const uint16_t*>(&h);
+      if (SPLIT) {
+        const typename H::T l = H::from(v - H::to(h));
+        ql[c * QSTRIDE_W * 2 + j] = *reinterpret_cast<const uint16_t*>(&l);
+      }
+    }
+  };
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < RS; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RS, nt); ++issued) issue(issued);
+  if (nt > 0) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[0], 0));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    }
+    __syncthreads();
+    if (!abort_flag) transform(0, 0);
+    __syncthreads();
+  }
+
+  for (int r = 0; r < nt && !abort_flag; ++r) {
+    // raw stage r % RS was consumed by transform(r); refill it with tile r + RS
+    if (tid == 0 && r + RS < nt) {
+      fence_proxy_async_smem();
+      issue(r + RS);
+      ++issued;
+    }
+    if (r + 1 < nt) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[(r + 1) % RS], ((r + 1) / RS) & 1));
+      if (!ok) {
+        abort_flag = 1;
+        if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+      } else {
+        transform(r + 1, (r + 1) & 1);
+      }
+    }
+    const uint32_t* kv = kvb + (r & 1) * TS * L::KV_STRIDE_W;
+    const uint32_t* qh = qb + (r & 1) * QBUF_W;
+    const uint32_t* ql = qh + MC * QSTRIDE_W;
+#pragma unroll 1
+    for (int kk = 0; kk < TS / 16; ++kk) {
+      // exponent operand B' for the two 8-source halves of this 16-source step
+      uint32_t bfr[2][L::KSTEPS][2];
+#pragma unroll
+      for (int nt2 = 0; nt2 < 2; ++nt2) {
+        const int j = kk * 16 + nt2 * 8 + g;
+#pragma unroll
+        for (int ks = 0; ks < L::KSTEPS; ++ks) {
+          bfr[nt2][ks][0] = kv[j * L::KV_STRIDE_W + 8 * ks + t];
+          bfr[nt2][ks][1] = kv[j * L::KV_STRIDE_W + 8 * ks + t + 4];
+        }
+      }
+      // weights operand for each group of 8 right-hand sides
+      uint32_t qfh[NRT][2], qfl[NRT][2];
+#pragma unroll
+      for (int rt = 0; rt < NRT; ++rt) {
+        const int c = rt * 8 + g;
+        qfh[rt][0] = qh[c * QSTRIDE_W + kk * 8 + t];
+        qfh[rt][1] = qh[c * QSTRIDE_W + kk * 8 + t + 4];
+        if (SPLIT) {
+          qfl[rt][0] = ql[c * QSTRIDE_W + kk * 8 + t];
+          qfl[rt][1] = ql[c * QSTRIDE_W + kk * 8 + t + 4];
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < L::KSTEPS; ++ks) {
+          mma16816<BF>(e0, afr[mt][ks], bfr[0][ks][0], bfr[0][ks][1]);
+          mma16816<BF>(e1, afr[mt][ks], bfr[1][ks][0], bfr[1][ks][1]);
+        }
+        // P = 2^E; accumulator layout (rows g, g+8; cols 2t, 2t+1) of the two
+        // 8-source halves is the A-operand layout of the 16-source step
+        float pv[8];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          pv[e] = ex2(e0[e]);
+          pv[4 + e] = ex2(e1[e]);
+        }
+        uint32_t ph[4];
+        ph[0] = H::pack(pv[0], pv[1]);
+        ph[1] = H::pack(pv[2], pv[3]);
+        ph[2] = H::pack(pv[4], pv[5]);
+        ph[3] = H::pack(pv[6], pv[7]);
+        uint32_t pl[4];
+        if (SPLIT) {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const float2 hv = H::unpack(ph[w]);
+            pl[w] = H::pack(pv[2 * w] - hv.x, pv[2 * w + 1] - hv.y);
+          }
+        }
+#pragma unroll
+        for (int rt = 0; rt < NRT; ++rt) {
+          mma16816<BF>(acc[mt][rt], ph, qfh[rt][0], qfh[rt][1]);
+          if (SPLIT) {
+            mma16816<BF>(acc[mt][rt], pl, qfh[rt][0], qfh[rt][1]);
+            mma16816<BF>(acc[mt][rt], ph, qfl[rt][0], qfl[rt][1]);
+          }
+        }
+      }
+    }
+    // fold the tile's sums into compensated float32 accumulators
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int rt = 0; rt < NRT; ++rt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          kahan_add(S[mt][rt][e], C[mt][rt][e], acc[mt][rt][e]);
+          acc[mt][rt][e] = 0.f;
+        }
+    __syncthreads();
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RS], (r / RS) & 1);
+    __syncthreads();
+    return;
+  }
+
+  // ---- partials: rows g, g+8 of each m-tile, columns 2t, 2t+1 of each group
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int64_t i = row0 + mt * 16 + g + 8 * half;
+      if (i >= p.Nt_pad) continue;
+#pragma unroll
+      for (int rt = 0; rt < NRT; ++rt)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = rt * 8 + 2 * t + cc;
+          if (c >= p.m) continue;
+          const int e = 2 * half + cc;
+          p.part[((int64_t)blockIdx.y * p.m + c) * p.Nt_pad + i] =
+              (double)S[mt][rt][e] - (double)C[mt][rt][e];
+        }
+    }
+}
+
+template <int D, int MT, int NRT, bool SPLIT, bool BF>
+cudaError_t launch(const TcParams& p, int splits, int warps, cudaStream_t st, bool dry) {
+  using L = ExpLayout<D>;
+  constexpr int MC = 8 * NRT;
+  const size_t shm = sizeof(float) * RS * (D + p.m) * TS + sizeof(uint32_t) * 2 * TS * L::KV_STRIDE_W +
+                     sizeof(uint32_t) * 2 * (SPLIT ? 2 : 1) * MC * 132;
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    // sized for the largest m of this instance
+    const size_t shm_max = sizeof(float) * RS * (D + MC) * TS + sizeof(uint32_t) * 2 * TS * L::KV_STRIDE_W +
+                           sizeof(uint32_t) * 2 * (SPLIT ? 2 : 1) * MC * 132;
+    cudaError_t e = cudaFuncSetAttribute(mvp_tc_kernel<D, MT, NRT, SPLIT, BF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max);
+    if (e) return e;
+    done[dev] = true;
+  }
+  if (dry) return cudaSuccess;
+  dim3 grid((unsigned)p.nblk, (unsigned)splits);
+  mvp_tc_kernel<D, MT, NRT, SPLIT, BF><<<grid, 32 * warps, shm, st>>>(p); count_launch();
+  return cudaGetLastError();
+}
+
+template <int D, bool SPLIT, bool BF>
+cudaError_t dispatch_m(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+  // m-tiles per warp: 4 (2 for two groups of right-hand sides with split
+  // accumulators, keeping registers under 128); never beyond the block
+  const int mt_max = p.WB / 16;
+  if (p.m <= 8) {
+    const int MT = std::min(4, mt_max);
+    const int warps = p.WB / (16 * MT);
+    if (MT == 4) return launch<D, 4, 1, SPLIT, BF>(p, splits, warps, st, dry);
+    return launch<D, 2, 1, SPLIT, BF>(p, splits, warps, st, dry);
+  }
+  const int MT = std::min(2, mt_max);
+  return launch<D, 2, 2, SPLIT, BF>(p, splits, p.WB / (16 * MT), st, dry);
+}
+
+template <int D>
+cudaError_t dispatch_prec(const TcParams& p, int splits, bool split, bool bf, cudaStream_t st,
+                          bool dry) {
+  if (split)
+    return bf ? dispatch_m<D, true, true>(p, splits, st, dry) : dispatch_m<D, true, false>(p, splits, st, dry);
+  return bf ? dispatch_m<D, false, true>(p, splits, st, dry) : dispatch_m<D, false, false>(p, splits, st, dry);
+}
+
+}  // namespace
+
+cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
+                            bool split, bool bf, int splits, int tiles_per_split, double* part,
+                            float* fac, const int* active, cudaStream_t st, bool dry) {
+  if (m < 1 || m > 16) return cudaErrorNotSupported;
+  if ((32 * T.T) % 32 != 0 || 32 * T.T < 32) return cudaErrorNotSupported;
+  TcParams p{};
+  p.xt = T.xs;
+  p.Nt = T.N;
+  p.Nt_pad = T.Npad;
+  p.tctr = T.ctr;
+  p.torder = T.order;
+  p.tn_exp = T.n_exp;
+  p.nblk = T.nblk;
+  p.WB = 32 * T.T;
+  p.xs = S.xs;
+  p.Q = Q;
+  p.Ns_pad = S.Npad;
+  p.m = m;
+  p.ntiles = (int)(S.Npad / TS);
+  p.tiles_per_split = tiles_per_split;
+  p.part = part;
+  p.fac = fac;
+  p.err = c.d_err;
+  p.s = S.scale;
+  p.active = active;
+  switch (T.d) {
+    case 1: return dispatch_prec<1>(p, splits, split, bf, st, dry);
+    case 2: return dispatch_prec<2>(p, splits, split, bf, st, dry);
+    case 3: return dispatch_prec<3>(p, splits, split, bf, st, dry);
+    case 4: return dispatch_prec<4>(p, splits, split, bf, st, dry);
+    case 5: return dispatch_prec<5>(p, splits, split, bf, st, dry);
+    case 6: return dispatch_prec<6>(p, splits, split, bf, st, dry);
+    case 7: return dispatch_prec<7>(p, splits, split, bf, st, dry);
+    case 8: return dispatch_prec<8>(p, splits, split, bf, st, dry);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace krr

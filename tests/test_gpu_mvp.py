@@ -149,3 +149,41 @@ def test_nonfinite_input_reported(K):
     with pytest.raises(K.KrrError) as ei:
         K.krr_kernel_mvp(X, q, 0.1, 0.1)  # host arrays: the call waits and reports
     assert ei.value.status == K.KRR_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("m,d", [(2, 3), (5, 2), (16, 3), (16, 4), (8, 8), (3, 1)])
+def test_mvp_multi_rhs_tensor_cores_fp32(K, oracle_mod, m, d):
+    # m >= 2 runs the tensor-core kernel with hi/lo-split operands
+    rng = np.random.default_rng(100 + m * 10 + d)
+    N = 6000
+    X = rng.random((N, d)).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    sigma = 0.08 if d <= 3 else 0.3
+    Y = K.krr_kernel_mvp(_dev(X), _dev(Q), sigma, 1e-3).cpu().numpy()
+    for c in range(m):
+        assert scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-3) <= TOL_FP32, c
+
+
+def test_mvp_multi_rhs_full_size_sampled(K, oracle_mod):
+    # the 2^20-point cube with 16 right-hand sides (the multi-column benchmark)
+    p = inputs.mvp_problem(seed=4, N=1 << 20, d=3, m=16)
+    Q = np.ascontiguousarray(p["Q"].T)
+    Y = K.krr_kernel_mvp(_dev(p["X"]), _dev(Q), p["sigma"], p["gamma"]).cpu().numpy()
+    rows = inputs.sample_rows(1 << 20, 64, seed=9)
+    for c in (0, 7, 15):
+        assert scaled_error(oracle_mod, p["X"], Q[c], Y[c], p["sigma"], p["gamma"], rows) <= TOL_FP32
+
+
+@pytest.mark.parametrize("prec,bound", [("fp16", 2e-3), ("bf16", 2e-2)])
+def test_mvp_reduced_precision_error(K, oracle_mod, prec, bound):
+    # the inner preconditioner product: half-precision kernel values and
+    # weights, float32 accumulation; its error is reported, not hidden
+    rng = np.random.default_rng(77)
+    N = 8000
+    X = rng.random((N, 2)).astype(np.float32)
+    q = rng.standard_normal(N).astype(np.float32)
+    y = K.krr_kernel_mvp(_dev(X), _dev(q), 0.05, 1e-2, prec=prec).cpu().numpy()
+    err = scaled_error(oracle_mod, X, q, y, 0.05, 1e-2)
+    print(f"{prec} max scaled error {err:.2e}")
+    assert err <= bound
+    assert err > 1e-6  # it really ran in reduced precision
