@@ -403,6 +403,63 @@ __global__ void solve_init_kernel(KState* S, const float* __restrict__ b, int64_
   }
 }
 
+// CG restart setup: stop when the true relative residual meets tol_stop,
+// else aim the next CG run at reducing |r| to tol_stop |b| (residual
+// replacement: CG restarted on A z = r from the accurate residual).
+__global__ void cg_cycle_kernel(KState* S, double tol_stop, int maxit_total) {
+  const double rn = sqrt(S->rnorm2);
+  S->relres_true = S->bnorm > 0.0 ? rn / S->bnorm : 0.0;
+  const int left = maxit_total - S->inner_total;
+  bool more = S->bnorm > 0.0 && S->relres_true > tol_stop && isfinite(rn);
+  if (more && left <= 0) {
+    more = false;
+    S->status = KRR_NOT_CONVERGED;
+  }
+  if (!isfinite(rn)) S->status = KRR_ERR_NONFINITE;
+  S->restart_cont = more ? 1 : 0;
+  if (more) {
+    S->cycles += 1;
+    S->j = 0;
+    S->maxit = left;
+    const double target = 0.5 * tol_stop * S->bnorm / rn;  // relative to |r|
+    S->eps2 = fmax(target, 1e-7) * fmax(target, 1e-7);
+  }
+}
+
+// x += z in float-float
+__global__ void x_add_kernel(const float* __restrict__ z, int64_t Np, float* __restrict__ xh,
+                             float* __restrict__ xl) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = (double)xh[i] + (double)xl[i] + (double)z[i];
+    const float h = (float)t;
+    xh[i] = h;
+    xl[i] = (float)(t - (double)h);
+  }
+}
+
+// x = x0 (FP64, original order) gathered to sorted float-float; padding 0
+__global__ void x_from64_kernel(const double* __restrict__ x0, const int* __restrict__ perm,
+                                int64_t N, int64_t Np, float* __restrict__ xh, float* __restrict__ xl) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = i < N ? x0[perm[i]] : 0.0;
+    const float h = (float)v;
+    xh[i] = h;
+    xl[i] = (float)(v - (double)h);
+  }
+}
+
+__global__ void bnorm_kernel(KState* S, const float* __restrict__ b, int64_t Np, double* partials) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)b[i] * (double)b[i];
+  double tot;
+  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) S->bnorm = sqrt(tot);
+}
+
 // Xsol[perm[i]] = xh[i] + xl[i] (FP64, original order)
 __global__ void scatter_x64_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
                                    const int* __restrict__ perm, int64_t N, double* __restrict__ out) {
@@ -821,10 +878,104 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
   return worst;
 }
 
-krr_status krr_cg_solve(krr_handle h, const float*, int64_t, int, float, float, const float*,
-                        double*, double, int, krr_precision, krr_solve_info*, void*) {
+krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d, float sigma, float shift,
+                        const float* b, double* x, double tol, int maxit, krr_precision prec,
+                        krr_solve_info* info, void* stream) {
   if (!h) return KRR_ERR_INVALID_ARG;
-  return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_cg_solve: not built yet");
+  Ctx& c = h->ctx;
+  const char* fn = "krr_cg_solve";
+  krr_status s = check_points(c, fn, X, N, d, sigma);
+  if (s) return s;
+  if (!(shift >= 0.f) || !std::isfinite(shift))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: shift must be finite and >= 0", fn);
+  if (!(tol > 0.0) || !(tol < 1.0)) return set_error(c, KRR_ERR_INVALID_ARG, "%s: tol must be in (0, 1)", fn);
+  if (maxit < 0) return set_error(c, KRR_ERR_INVALID_ARG, "%s: maxit < 0", fn);
+  if (prec != KRR_FP32 && prec != KRR_BF16 && prec != KRR_FP16)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: unknown precision", fn);
+  if (N == 0) return KRR_OK;
+  if (!b || !x) return set_error(c, KRR_ERR_INVALID_ARG, "%s: b or x is NULL", fn);
+  cudaStream_t ust = (cudaStream_t)stream;
+  cudaStream_t st = c.work;
+  {
+    cudaError_t e0 = cudaEventRecord(c.ev_in, ust);
+    if (!e0) e0 = cudaStreamWaitEvent(st, c.ev_in, 0);
+    if (e0) return cuda_error(c, e0, fn);
+  }
+  struct Join {
+    Ctx& c;
+    cudaStream_t ust;
+    ~Join() {
+      cudaEventRecord(c.ev_out, c.work);
+      cudaStreamWaitEvent(ust, c.ev_out, 0);
+    }
+  } join{c, ust};
+  float *dX, *db;
+  double* dx;
+  bool sX, sb, sx;
+  if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
+  if ((s = device_view(c, "stage.B", b, (size_t)N, true, st, &db, &sb))) return s;
+  if ((s = device_view_d(c, "stage.Xsol", x, (size_t)N, true, st, &dx, &sx))) return s;
+  Solver sv(c);
+  sv.st = st;
+  cudaError_t e = prepare_points(c, dX, N, d, sigma, "kry.pts", sv.P, st);
+  if (e) return cuda_error(c, e, fn);
+  sv.Np = sv.P.Npad;
+  sv.gamma = shift;   // the operator of this solve is K_hat + shift I throughout
+  sv.mshift = shift;
+  sv.inner_prec = prec;
+  if ((e = sv.alloc(1))) return cuda_error(c, e, fn);
+  if ((e = mvp_reserve(c, sv.P, sv.P, st))) return cuda_error(c, e, fn);
+  if ((e = mvp_acc_reserve(c, sv.P, st))) return cuda_error(c, e, fn);
+  if (prec != KRR_FP32 && (e = mvp_multi_reserve(c, sv.P, sv.P, 1, prec, st))) return cuda_error(c, e, fn);
+  KState hs;
+  memset(&hs, 0, sizeof(hs));
+  hs.status = KRR_OK;
+  if ((e = cudaMemcpyAsync(sv.S, &hs, sizeof(KState), cudaMemcpyHostToDevice, st))) return cuda_error(c, e, fn);
+  if ((e = gather_sorted(db, N, 1, sv.P.perm, sv.Np, sv.b, st))) return cuda_error(c, e, fn);
+  cudaEventRecord(c.ev0, st);
+  x_from64_kernel<<<sv.vblocks, VT, 0, st>>>(dx, sv.P.perm, N, sv.Np, sv.xh, sv.xl); count_launch();
+  bnorm_kernel<<<sv.vblocks, VT, 0, st>>>(sv.S, sv.b, sv.Np, sv.partials); count_launch();
+  if ((e = sv.residual())) return cuda_error(c, e, fn);
+  const double tol_stop = tol;
+  for (;;) {
+    cg_cycle_kernel<<<1, 1, 0, st>>>(sv.S, tol_stop, maxit); count_launch();
+    KState hcur;
+    if ((e = read_state(c, sv.S, hcur, st))) return cuda_error(c, e, fn);
+    if (!hcur.restart_cont) break;
+    cg_init_kernel<<<sv.vblocks, VT, 0, st>>>(sv.S, sv.r64, nullptr, sv.Np, sv.z, sv.rr, sv.p,
+                                              sv.partials, Cond{}, nullptr); count_launch();
+    for (;;) {
+      for (int bt = 0; bt < 16; ++bt)
+        if ((e = sv.cg_iteration(&sv.S->cg_cont))) return cuda_error(c, e, fn);
+      if ((e = read_state(c, sv.S, hcur, st))) return cuda_error(c, e, fn);
+      if (!hcur.cg_cont) break;
+    }
+    x_add_kernel<<<sv.vblocks, VT, 0, st>>>(sv.z, sv.Np, sv.xh, sv.xl); count_launch();
+    if ((e = sv.residual())) return cuda_error(c, e, fn);
+  }
+  cudaEventRecord(c.ev1, st);
+  if ((e = cudaEventSynchronize(c.ev1))) return cuda_error(c, e, fn);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+  if ((e = read_state(c, sv.S, hs, st))) return cuda_error(c, e, fn);
+  scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, dx); count_launch();
+  if (sx && (e = cudaMemcpyAsync(x, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, st)))
+    return cuda_error(c, e, fn);
+  krr_status de = read_device_error(c, st, fn);
+  if (de) return de;
+  if (info) {
+    info->outer_iters = hs.inner_total;
+    info->inner_iters = 0;
+    info->cycles = hs.cycles;
+    info->breakdowns = hs.breakdowns;
+    info->relres_est = sqrt(hs.rho) / (hs.bnorm > 0 ? hs.bnorm : 1.0);
+    info->relres_true = hs.relres_true;
+    info->time_ms = ms;
+    info->status = (krr_status)hs.status;
+  }
+  if (hs.status != KRR_OK)
+    return set_error(c, (krr_status)hs.status, "%s: tolerance not reached in %d iterations", fn, maxit);
+  return KRR_OK;
 }
 
 krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem*, int, int, float, int,
@@ -833,11 +984,5 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem*, int, int, 
   return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_fgmres_solve_batched: not built yet");
 }
 
-krr_status krr_mll_grad(krr_handle h, const float*, int64_t, int, float, float, const float*, int,
-                        uint64_t, const krr_fgmres_opts*, double*, double*, float*,
-                        krr_solve_info*, void*) {
-  if (!h) return KRR_ERR_INVALID_ARG;
-  return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_mll_grad: not built yet");
-}
 
 }  // extern "C"

@@ -1,0 +1,58 @@
+"""GPU log-marginal-likelihood gradient (the ML fit of Sec. 2.1 / Sec. 6.1).
+
+The library draws its Rademacher probes from SplitMix64 with the same counter
+convention as the oracle, so the GPU gradient must match the oracle's
+Hutchinson gradient (exact solves, same probes) up to the solver tolerance;
+the oracle's estimator itself is pinned by finite differences and the
+exact-trace mode in test_oracle_mll.py.
+"""
+import numpy as np
+import pytest
+
+from paper_1408_1237_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1408_1237_gb300 import binding
+    return binding
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("N,d,P", [(300, 2, 4), (2000, 4, 32)])
+def test_mll_grad_matches_oracle_estimator(K, oracle_mod, N, d, P):
+    p = inputs.gradient_problem(seed=3, N=N, d=d, probes=P)
+    opts = K.default_opts(tol=1e-8, max_cycles=20)
+    gs, gg, gX, infos = K.krr_mll_grad(_dev(p["X"]), _dev(p["y"]), p["sigma"], p["gamma"],
+                                       n_probes=P, seed=p["seed"], opts=opts)
+    assert all(i["status"] == K.KRR_OK for i in infos), infos[:2]
+    Zp = oracle_mod.rademacher_probes(p["seed"], N, P)
+    os_, og, oX = oracle_mod.mll_grad_hutchinson(p["X"].astype(np.float64),
+                                                 p["y"].astype(np.float64),
+                                                 p["sigma"], p["gamma"], Zp)
+    assert gs == pytest.approx(os_, rel=1e-4, abs=1e-6 * abs(os_) + 1e-8)
+    assert gg == pytest.approx(og, rel=1e-4, abs=1e-8)
+    gX = gX.cpu().numpy()
+    assert np.max(np.abs(gX - oX)) <= 1e-4 * np.max(np.abs(oX))
+
+
+def test_mll_grad_host_arrays_and_no_dx(K):
+    p = inputs.gradient_problem(seed=4, N=500, d=3, probes=2)
+    gs1, gg1, gX, _ = K.krr_mll_grad(p["X"], p["y"], p["sigma"], p["gamma"], n_probes=2,
+                                     seed=1, want_dX=True)
+    assert isinstance(gX, np.ndarray) and gX.shape == (500, 3)
+    gs2, gg2, none, _ = K.krr_mll_grad(_dev(p["X"]), _dev(p["y"]), p["sigma"], p["gamma"],
+                                       n_probes=2, seed=1, want_dX=False)
+    assert none is None
+    assert gs1 == pytest.approx(gs2, rel=1e-9) and gg1 == pytest.approx(gg2, rel=1e-9)
