@@ -63,12 +63,22 @@ struct Ctx {
   // caller's stream by ev_in / ev_out
   cudaStream_t work = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // concurrent branches of a batched solve each get a sub-context with its
+  // own workspace and error word (sub-contexts own no streams or events)
+  std::vector<Ctx*> subs;
+  // CTA slots the product kernels plan for (0: 2 per SM); a batched solve
+  // lowers it so that concurrent small problems are not over-split
+  int plan_slots = 0;
   // profiling of the fast product kernel (krr_profile_enable / _read)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
   size_t prof_used = 0;              // events in use (even)
   double prof_pairs = 0.0;
 };
+
+// Sub-context k of c (created on first use; freed with the handle).
+cudaError_t sub_context(Ctx& c, size_t k, Ctx** out);
+void release_context(Ctx& c);
 
 // ---- prep.cu
 // Sort X (N x d row-major, device) along a Morton curve and pack the scaled,

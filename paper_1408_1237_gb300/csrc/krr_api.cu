@@ -42,6 +42,34 @@ void Workspace::release_all() {
   slots.clear();
 }
 
+cudaError_t sub_context(Ctx& c, size_t k, Ctx** out) {
+  while (c.subs.size() <= k) {
+    Ctx* s = new (std::nothrow) Ctx();
+    if (!s) return cudaErrorMemoryAllocation;
+    s->device = c.device;
+    s->num_sms = c.num_sms;
+    cudaError_t e = cudaMalloc(&s->d_err, sizeof(int));
+    if (!e) e = cudaMemset(s->d_err, 0, sizeof(int));
+    if (e) {
+      delete s;
+      return e;
+    }
+    c.subs.push_back(s);
+  }
+  *out = c.subs[k];
+  return cudaSuccess;
+}
+
+void release_context(Ctx& c) {
+  for (Ctx* s : c.subs) {
+    release_context(*s);
+    s->ws.release_all();
+    cudaFree(s->d_err);
+    delete s;
+  }
+  c.subs.clear();
+}
+
 krr_status set_error(Ctx& c, krr_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -199,6 +227,7 @@ krr_status krr_destroy(krr_handle h) {
   if (!h) return KRR_ERR_INVALID_ARG;
   Ctx& c = h->ctx;
   cudaDeviceSynchronize();
+  release_context(c);
   c.ws.release_all();
   cudaFree(c.d_err);
   cudaFreeHost(c.h_status);

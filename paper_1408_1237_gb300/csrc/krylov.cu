@@ -31,6 +31,8 @@
 //     true residual reaches tolerances the float32 products alone cannot.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <memory>
 #include <vector>
 
 #include "api_util.h"
@@ -643,12 +645,39 @@ cudaError_t capture_into(cudaStream_t st, cudaGraph_t into, F&& fn) {
   return fe ? fe : e;
 }
 
+// Fill the body of the restart WHILE node: v0; WHILE arnoldi { cg_init;
+// WHILE cg { CG iteration }; Arnoldi step }; least squares, x update, true
+// residual, restart check.
+cudaError_t fill_restart_body(Solver& s, cudaGraph_t rbody, double tol_stop) {
+  cudaError_t e;
+  cudaGraph_t abody, cbody;
+  if ((e = cudaGraphConditionalHandleCreate(&s.arn_c.h, rbody, 1, cudaGraphCondAssignDefault))) return e;
+  s.arn_c.use = 1;
+  if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t {
+         v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, s.arn_c); count_launch();
+         return cudaGetLastError();
+       })))
+    return e;
+  if ((e = add_while(rbody, s.arn_c.h, &abody))) return e;
+  if ((e = cudaGraphConditionalHandleCreate(&s.cg_c.h, abody, 0, cudaGraphCondAssignDefault))) return e;
+  s.cg_c.use = 1;
+  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t {
+         cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
+                                                    s.partials, s.cg_c, nullptr); count_launch();
+         return cudaGetLastError();
+       })))
+    return e;
+  if ((e = add_while(abody, s.cg_c.h, &cbody))) return e;
+  if ((e = capture_into(s.st, cbody, [&]() -> cudaError_t { return s.cg_iteration(nullptr); }))) return e;
+  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t { return s.arnoldi_tail(nullptr); }))) return e;
+  return capture_into(s.st, rbody, [&]() -> cudaError_t { return s.cycle_tail(tol_stop, nullptr); });
+}
+
 // The whole FGMRES solve (after solve_init and the first restart check) as
-// one graph:  WHILE restart { v0; WHILE arnoldi { cg_init; WHILE cg { CG
-// iteration }; Arnoldi step }; least squares, x update, true residual, check }.
+// one graph:  WHILE restart { restart body }.
 cudaError_t build_graph(Solver& s, double tol_stop, cudaGraphExec_t* exec) {
   cudaError_t e;
-  cudaGraph_t g, rbody, abody, cbody;
+  cudaGraph_t g, rbody;
   if ((e = cudaGraphCreate(&g, 0))) return e;
   auto fail = [&](cudaError_t ee) {
     cudaGraphDestroy(g);
@@ -657,32 +686,56 @@ cudaError_t build_graph(Solver& s, double tol_stop, cudaGraphExec_t* exec) {
   if ((e = cudaGraphConditionalHandleCreate(&s.rst_c.h, g, 1, cudaGraphCondAssignDefault))) return fail(e);
   s.rst_c.use = 1;
   if ((e = add_while(g, s.rst_c.h, &rbody))) return fail(e);
-  if ((e = cudaGraphConditionalHandleCreate(&s.arn_c.h, rbody, 1, cudaGraphCondAssignDefault))) return fail(e);
-  s.arn_c.use = 1;
-  if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t {
-         v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, s.arn_c); count_launch();
-         return cudaGetLastError();
-       })))
-    return fail(e);
-  if ((e = add_while(rbody, s.arn_c.h, &abody))) return fail(e);
-  if ((e = cudaGraphConditionalHandleCreate(&s.cg_c.h, abody, 0, cudaGraphCondAssignDefault))) return fail(e);
-  s.cg_c.use = 1;
-  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t {
-         cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
-                                                    s.partials, s.cg_c, nullptr); count_launch();
-         return cudaGetLastError();
-       })))
-    return fail(e);
-  if ((e = add_while(abody, s.cg_c.h, &cbody))) return fail(e);
-  if ((e = capture_into(s.st, cbody, [&]() -> cudaError_t { return s.cg_iteration(nullptr); })))
-    return fail(e);
-  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t { return s.arnoldi_tail(nullptr); })))
-    return fail(e);
-  if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t { return s.cycle_tail(tol_stop, nullptr); })))
-    return fail(e);
+  if ((e = fill_restart_body(s, rbody, tol_stop))) return fail(e);
   e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
   return e;
+}
+
+// Capture fn() into graph g after `deps`; the nodes that end the captured
+// work are returned in `frontier`.
+template <typename F>
+cudaError_t capture_after(cudaStream_t st, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+                          F&& fn, std::vector<cudaGraphNode_t>& frontier) {
+  cudaError_t e = cudaStreamBeginCaptureToGraph(st, g, deps.data(), nullptr, deps.size(),
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e) return e;
+  const cudaError_t fe = fn();
+  cudaStreamCaptureStatus status;
+  const cudaGraphNode_t* d = nullptr;
+  size_t nd = 0;
+  cudaError_t ie = cudaStreamGetCaptureInfo(st, &status, nullptr, nullptr, &d, nullptr, &nd);
+  if (!ie) frontier.assign(d, d + nd);
+  cudaGraph_t out;
+  e = cudaStreamEndCapture(st, &out);
+  return fe ? fe : (ie ? ie : e);
+}
+
+// One independent branch of a batched graph: solve init and first check,
+// WHILE restart { ... }, scatter of the solution to `xout` (original order).
+cudaError_t build_branch(cudaGraph_t g, Solver& s, double tol_stop, int64_t N, double* xout) {
+  cudaError_t e;
+  if ((e = cudaGraphConditionalHandleCreate(&s.rst_c.h, g, 0, cudaGraphCondAssignDefault))) return e;
+  s.rst_c.use = 1;
+  std::vector<cudaGraphNode_t> f0, f1;
+  if ((e = capture_after(s.st, g, {}, [&]() -> cudaError_t {
+         solve_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
+         restart_check_kernel<<<1, 1, 0, s.st>>>(s.S, s.rst_c, tol_stop); count_launch();
+         return cudaGetLastError();
+       }, f0)))
+    return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = s.rst_c.h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if ((e = cudaGraphAddNode(&wnode, g, f0.data(), nullptr, f0.size(), &np))) return e;
+  if ((e = fill_restart_body(s, np.conditional.phGraph_out[0], tol_stop))) return e;
+  return capture_after(s.st, g, {wnode}, [&]() -> cudaError_t {
+    scatter_x64_kernel<<<s.vblocks, VT, 0, s.st>>>(s.xh, s.xl, s.P.perm, N, xout); count_launch();
+    return cudaGetLastError();
+  }, f1);
 }
 
 }  // namespace
@@ -978,10 +1031,142 @@ krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d, float si
   return KRR_OK;
 }
 
-krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem*, int, int, float, int,
-                                    const krr_fgmres_opts*, krr_solve_info*, void*) {
+krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int nprob, int d,
+                                    float sigma, int m_rhs, const krr_fgmres_opts* opts,
+                                    krr_solve_info* info, void* stream) {
   if (!h) return KRR_ERR_INVALID_ARG;
-  return set_error(h->ctx, KRR_ERR_UNIMPLEMENTED, "krr_fgmres_solve_batched: not built yet");
+  Ctx& c = h->ctx;
+  const char* fn = "krr_fgmres_solve_batched";
+  if (nprob < 0 || nprob > 4096 || (nprob > 0 && !probs))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: nprob out of range [0, 4096] or probs NULL", fn);
+  if (m_rhs < 1 || m_rhs > 64) return set_error(c, KRR_ERR_INVALID_ARG, "%s: m_rhs out of range [1, 64]", fn);
+  if ((int64_t)nprob * m_rhs > 4096)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: nprob * m_rhs > 4096", fn);
+  krr_status s;
+  for (int k = 0; k < nprob; ++k) {
+    if ((s = check_points(c, fn, probs[k].X, probs[k].N, d, sigma))) return s;
+    if (!(probs[k].gamma >= 0.f) || !std::isfinite(probs[k].gamma))
+      return set_error(c, KRR_ERR_INVALID_ARG, "%s: problem %d: gamma must be finite and >= 0", fn, k);
+    if (probs[k].N > 0 && (!probs[k].B || !probs[k].Xsol || !is_device_ptr(c, probs[k].X) ||
+                           !is_device_ptr(c, probs[k].B) || !is_device_ptr(c, probs[k].Xsol)))
+      return set_error(c, KRR_ERR_INVALID_ARG, "%s: problem %d: arrays must be device arrays", fn, k);
+  }
+  SolveCfg cfg;
+  if ((s = resolve_opts(c, fn, opts, 0.f, cfg))) return s;
+  cudaStream_t ust = (cudaStream_t)stream;
+  cudaStream_t st = c.work;
+  {
+    cudaError_t e0 = cudaEventRecord(c.ev_in, ust);
+    if (!e0) e0 = cudaStreamWaitEvent(st, c.ev_in, 0);
+    if (e0) return cuda_error(c, e0, fn);
+  }
+  struct Join {
+    Ctx& c;
+    cudaStream_t ust;
+    ~Join() {
+      cudaEventRecord(c.ev_out, c.work);
+      cudaStreamWaitEvent(ust, c.ev_out, 0);
+    }
+  } join{c, ust};
+  cudaError_t e;
+  // One branch per (problem, right-hand side), each with its own context;
+  // problems share their prepared points among their branches.
+  const int nbr = nprob * m_rhs;
+  // concurrent branches share the SMs: plan each product for its share
+  const int slots = std::max(16, 2 * c.num_sms * 4 / std::max(1, nbr));
+  std::vector<std::unique_ptr<Solver>> sv;
+  std::vector<PointsDev> pts(nprob);
+  std::vector<int> branch_prob;
+  for (int k = 0; k < nprob; ++k) {
+    const krr_problem& pr = probs[k];
+    if (pr.N == 0) continue;
+    Ctx* pc;
+    if ((e = sub_context(c, (size_t)k * m_rhs, &pc))) return cuda_error(c, e, fn);
+    pc->plan_slots = slots;
+    if ((e = prepare_points(*pc, pr.X, pr.N, d, sigma, "bat.pts", pts[k], st))) return cuda_error(c, e, fn);
+    const double delta = opts && opts->delta >= 0.0 ? opts->delta : (pr.gamma > 0.f ? 10.0 * pr.gamma : 1e-3);
+    for (int r = 0; r < m_rhs; ++r) {
+      Ctx* bc;
+      if ((e = sub_context(c, (size_t)k * m_rhs + r, &bc))) return cuda_error(c, e, fn);
+      bc->plan_slots = slots;
+      auto so = std::make_unique<Solver>(*bc);
+      so->st = st;
+      so->P = pts[k];
+      so->Np = pts[k].Npad;
+      so->gamma = pr.gamma;
+      so->mshift = (float)(pr.gamma + delta);
+      so->inner_prec = cfg.inner_prec;
+      if ((e = so->alloc(cfg.restart))) return cuda_error(c, e, fn);
+      if ((e = mvp_reserve(*bc, so->P, so->P, st))) return cuda_error(c, e, fn);
+      if ((e = mvp_acc_reserve(*bc, so->P, st))) return cuda_error(c, e, fn);
+      if (cfg.inner_prec != KRR_FP32 && (e = mvp_multi_reserve(*bc, so->P, so->P, 1, cfg.inner_prec, st)))
+        return cuda_error(c, e, fn);
+      KState hs;
+      init_state(hs, cfg);
+      if ((e = cudaMemcpyAsync(so->S, &hs, sizeof(KState), cudaMemcpyHostToDevice, st)))
+        return cuda_error(c, e, fn);
+      if ((e = gather_sorted(pr.B + (size_t)r * pr.N, pr.N, 1, pts[k].perm, so->Np, so->b, st)))
+        return cuda_error(c, e, fn);
+      sv.push_back(std::move(so));
+      branch_prob.push_back(k * m_rhs + r);
+    }
+  }
+  if (sv.empty()) return KRR_OK;
+  // graphs of at most BRANCHES_PER_GRAPH independent branches, one solve
+  // each, launched in turn (larger graphs of nested conditional loops are not
+  // used: one of 1024 branches failed on the device)
+  constexpr size_t BRANCHES_PER_GRAPH = 32;
+  float ms = 0.f;
+  for (size_t b0 = 0; b0 < sv.size(); b0 += BRANCHES_PER_GRAPH) {
+    const size_t b1 = std::min(sv.size(), b0 + BRANCHES_PER_GRAPH);
+    cudaGraph_t g;
+    if ((e = cudaGraphCreate(&g, 0))) return cuda_error(c, e, fn);
+    for (size_t b = b0; b < b1; ++b) {
+      const int k = branch_prob[b] / m_rhs, r = branch_prob[b] % m_rhs;
+      if ((e = build_branch(g, *sv[b], 0.5 * cfg.tol, probs[k].N, probs[k].Xsol + (size_t)r * probs[k].N))) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_error(c, e, "krr_fgmres_solve_batched (graph build)");
+      }
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e) return cuda_error(c, e, "krr_fgmres_solve_batched (graph instantiate)");
+    cudaEventRecord(c.ev0, st);
+    e = cudaGraphLaunch(exec, st);
+    cudaEventRecord(c.ev1, st);
+    if (!e) e = cudaEventSynchronize(c.ev1);
+    cudaGraphExecDestroy(exec);
+    if (e) return cuda_error(c, e, fn);
+    float part_ms = 0.f;
+    cudaEventElapsedTime(&part_ms, c.ev0, c.ev1);
+    ms += part_ms;
+  }
+  krr_status worst = KRR_OK;
+  for (size_t b = 0; b < sv.size(); ++b) {
+    KState hs;
+    if ((e = read_state(c, sv[b]->S, hs, st))) return cuda_error(c, e, fn);
+    if (hs.status == KRR_OK && hs.relres_true > cfg.tol) hs.status = KRR_NOT_CONVERGED;
+    if (info) fill_info(hs, ms, info + branch_prob[b]);
+    if (hs.status != KRR_OK && worst == KRR_OK) worst = (krr_status)hs.status;
+  }
+  // device error words of the branches' contexts (read through this handle's
+  // pinned status word)
+  for (size_t b = 0; b < sv.size(); ++b) {
+    Ctx* bc = c.subs[branch_prob[b]];
+    if ((e = cudaMemcpyAsync(c.h_status, bc->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return cuda_error(c, e, fn);
+    if (*c.h_status != DEV_OK) {
+      const int v = *c.h_status;
+      cudaMemsetAsync(bc->d_err, 0, sizeof(int), st);
+      return set_error(c, v == DEV_TIMEOUT ? KRR_ERR_TIMEOUT : KRR_ERR_NONFINITE,
+                       "%s: problem %d: device error %d", fn, branch_prob[b] / m_rhs, v);
+    }
+  }
+  if (worst != KRR_OK) set_error(c, worst, "%s: a problem did not reach the tolerance", fn);
+  return worst;
 }
 
 

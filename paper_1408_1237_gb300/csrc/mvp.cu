@@ -420,8 +420,8 @@ struct Plan {
   int tiles_per_split = 1;
 };
 
-Plan make_plan(int64_t nblk, int ntiles, int num_sms) {
-  const int slots = num_sms * 2;
+Plan make_plan(int64_t nblk, int ntiles, int num_sms, int plan_slots = 0) {
+  const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   const int64_t ctas = (nblk + NW - 1) / NW;
   Plan pl;
   const int splits = choose_splits(ctas, ntiles, slots);
@@ -459,7 +459,7 @@ int mvp_targets_per_thread(int d, int64_t N) {
 cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
-  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms);
+  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
   void* v;
   cudaError_t e;
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
@@ -503,7 +503,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   p.direct_only = 0;
   p.err = c.d_err;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
-  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms);
+  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots);
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   void *part, *fac, *dpart, *dcnt;
@@ -564,7 +564,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   if (Tp.N == 0) return cudaSuccess;
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
-  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms);
+  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
   void* v;
   if ((e = c.ws.get("mvp.partm", sizeof(double) * pl.splits * (size_t)m * Tp.Npad, &v))) return e;
   return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pl.splits,
@@ -591,7 +591,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
   p.direct_only = 1;
-  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms);
+  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots);
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   void *part, *fac, *dpart, *dcnt;

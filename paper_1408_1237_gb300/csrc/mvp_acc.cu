@@ -347,10 +347,10 @@ struct AccPlan {
   int splits, tiles_per_split;
 };
 
-AccPlan acc_plan(const PointsDev& P, int num_sms) {
+AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots) {
   const int ntiles = (int)(P.Npad / TS);
   const int64_t ctas = (P.N + NT * ACC_TA - 1) / (NT * ACC_TA);
-  const int slots = num_sms * 2;
+  const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   // fill the GPU about four times over, never below one tile per split
   int splits = (int)std::min<int64_t>(ntiles, std::max<int64_t>(1, (4LL * slots + ctas - 1) / ctas));
   AccPlan pl;
@@ -363,7 +363,7 @@ AccPlan acc_plan(const PointsDev& P, int num_sms) {
 
 cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st) {
   if (P.N == 0) return cudaSuccess;
-  const AccPlan pl = acc_plan(P, c.num_sms);
+  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots);
   void* v;
   cudaError_t e;
   if ((e = c.ws.get("acc.part", sizeof(double) * pl.splits * (size_t)P.Npad, &v))) return e;
@@ -404,7 +404,7 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   // s^2 = log2(e) / (2 sigma^2) in float-float from the double value
   p.k.s2h = (float)P.s2;
   p.k.s2l = (float)(P.s2 - (double)p.k.s2h);
-  const AccPlan pl = acc_plan(P, c.num_sms);
+  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots);
   p.tiles_per_split = pl.tiles_per_split;
   void *part, *dpart, *dcnt;
   const unsigned fin_blocks = (unsigned)((P.Npad + 255) / 256);
