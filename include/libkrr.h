@@ -232,7 +232,7 @@ krr_status krr_profile_read(krr_handle h, krr_profile* out);
  * row-major), Q and Y (N x m column-major) with N <= 16384, d <= 8 and
  * m <= 16.  Larger problems return KRR_ERR_SIZE_LIMIT; host arrays and bad
  * values return KRR_ERR_INVALID_ARG.
- * It allocates nothing.  Its scratch is one fixed device array of 10,405,376
+ * It allocates nothing.  Its scratch is one fixed device array of 10,415,616
  * bytes, held by every GPU that loads the library until the process exits.
  * The first call made with a device current looks up that array's device
  * address (cudaGetSymbolAddress), so make it before any stream capture.  All

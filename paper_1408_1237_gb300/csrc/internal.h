@@ -12,6 +12,8 @@
 namespace krr {
 
 constexpr int PAD = 2048;  // prepared arrays are padded to a multiple of PAD points
+// Most columns one multi-column product (and one block of a block solve) takes.
+constexpr int MAX_COLS = 16;
 
 inline int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
 
@@ -44,7 +46,19 @@ struct PointsDev {
   int* order = nullptr; // nblk block indices, expanded-form blocks first
   int* n_exp = nullptr; // device scalar: number of expanded-form blocks
   float* tbox = nullptr;// Npad/TS source tiles x 2d: centre, then half-width per dim
+  // the same per super-block of SB = 256 consecutive targets (the target
+  // blocks of the multi-column products: one CTA each)
+  int64_t nsb = 0;
+  float* sb_ctr = nullptr;
+  int* sb_order = nullptr;
+  int* sb_nexp = nullptr;
+  int* sb_flag = nullptr;  // nsb flags: 1 = expanded form
+  // host copies of *n_exp and *sb_nexp (read once by prepare_points)
+  int64_t h_nexp = 0, h_sb_nexp = 0;
 };
+
+// Targets per super-block.
+constexpr int SB = 256;
 
 // Targets per thread the product kernels use for N targets in d dimensions.
 int mvp_targets_per_thread(int d, int64_t N);
@@ -97,10 +111,20 @@ cudaError_t scatter_orig(const float* in, int64_t Npad, int64_t N, int m, const 
 // Accurate product for true residuals: out = cu * u + cy * (K_hat q + shift q)
 // in FP64 (sorted order), q given as float-float (qh + ql), with the fused
 // squared norm *dot += |out|^2 when dot != null.  Per-term relative error
-// ~1e-9 on near tiles.
+// about 3e-12 on near tiles.
+//
+// Several columns at once (cols.n <= MAX_COLS, one grid z-slice each): qh,
+// ql, u and out hold cols.n columns Npad apart; column c's dot and active
+// word sit cols.state_stride bytes after column c-1's, and a column whose
+// active word is 0 is skipped.
+struct AccCols {
+  int n = 1;
+  const int* active = nullptr;
+  size_t state_stride = 0;
+};
 cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const float* ql,
                            float shift, double cu, const float* u, double cy, double* out,
-                           double* dot, cudaStream_t st);
+                           double* dot, cudaStream_t st, const AccCols& cols = AccCols{});
 
 // ---- mvp.cu
 struct MvpOut {
@@ -121,21 +145,28 @@ struct MvpOut {
   int* brk_flag = nullptr;
   // predication: when non-null and *active == 0 the launch does nothing
   const int* active = nullptr;
+  // several columns (mvp_multi_launch): column c's scalars (dot, ratio_num,
+  // ratio_out, brk_flag, col_active) sit state_stride bytes after column
+  // c-1's; a column whose *col_active is 0 writes nothing
+  const int* col_active = nullptr;
+  size_t state_stride = 0;
 };
 
 // Allocate the workspace and set the kernel attributes a later mvp_launch /
 // mvp_acc_launch on these point sets needs, so that launches captured into a
 // CUDA graph allocate nothing.
 cudaError_t mvp_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, cudaStream_t st);
-cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st);
+cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int ncols = 1);
 
 // Several right-hand sides at once: Y[:, c] = (K_hat + shift I) Q[:, c] for
-// c < m (m <= 16), Q sorted with column stride S.Npad, qdiag with column
-// stride T.Npad.  Output per column c: out_f + c*T.Npad (sorted) and/or
-// out_orig + c*T.N (original order); the dot / step-length epilogue of o
-// applies to column 0 only.  prec KRR_FP32 evaluates on the tensor cores
-// with hi/lo-split operands (float32-grade); KRR_FP16 / KRR_BF16 with single
-// half-precision operands.
+// c < m (m <= MAX_COLS), Q sorted with column stride S.Npad, qdiag, u, dotw
+// with column stride T.Npad.  Output per column c: out_f + c*T.Npad (sorted)
+// and/or out_orig + c*T.N (original order); the dot / step-length epilogue
+// applies to every column, with the column scalars o.state_stride bytes apart.
+// Expanded-form warp blocks run on the tensor cores (prec KRR_FP32 with
+// hi/lo-split operands, float32-grade; KRR_FP16 / KRR_BF16 with single
+// half-precision operands), direct-form blocks on a multi-column float32
+// CUDA-core kernel (one exponential per pair shared by all columns).
 cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
                              const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                              cudaStream_t st);

@@ -44,13 +44,17 @@ namespace {
 
 constexpr int MMAX = 64;      // largest restart length
 constexpr int VT = 256;       // threads of the vector kernels
+constexpr int MAX_VBLOCKS = 1024;
+// reduction partials per column: up to MMAX + 1 sums of up to MAX_VBLOCKS blocks
+constexpr int64_t PSTRIDE = (int64_t)(MMAX + 1) * MAX_VBLOCKS;
 
+// State of one right-hand side (one column of a block solve).
 struct KState {
   // conjugate gradient
   double rho, rho0, pAp, alpha, beta, eps2;  // eps2 = (inner tol)^2
   int k, maxit, cg_cont, cg_brk;
   // Arnoldi / Givens
-  int j, m, arn_cont, kcols;
+  int j, m, arn_cont, kcols, stepping;  // stepping: this column takes the current Arnoldi step
   double H[(MMAX + 1) * MMAX];  // column-major, leading dimension MMAX+1
   double cs[MMAX], sn[MMAX], g[MMAX + 1], y[MMAX];
   double h1[MMAX + 1], h2[MMAX + 1];
@@ -65,6 +69,14 @@ struct KState {
   unsigned ticket;
 };
 
+// Loop control of one block solve (its columns advance in lockstep): the
+// arrival ticket of group reductions and, per loop, whether some column
+// still continues.
+struct Group {
+  unsigned ticket;
+  int cg_any, arn_any, rst_any;
+};
+
 struct Cond {
   cudaGraphConditionalHandle h = 0;
   int use = 0;
@@ -72,6 +84,40 @@ struct Cond {
 
 __device__ __forceinline__ void set_cond(const Cond& c, int v) {
   if (c.use) cudaGraphSetConditional(c.h, (unsigned)v);
+}
+
+// Which columns a kernel works on.
+enum Pred : int {
+  PRED_ALL = 0,
+  PRED_CG,    // the column's inner CG continues
+  PRED_ARN,   // the column's Arnoldi process continues in this cycle
+  PRED_STEP,  // the column takes the current Arnoldi step
+  PRED_RST,   // the column is in a restart cycle (not yet converged)
+};
+
+__device__ __forceinline__ int col_flag(const KState* S, int pred) {
+  switch (pred) {
+    case PRED_CG: return *(const volatile int*)&S->cg_cont;
+    case PRED_ARN: return *(const volatile int*)&S->arn_cont;
+    case PRED_STEP: return *(const volatile int*)&S->stepping;
+    case PRED_RST: return *(const volatile int*)&S->restart_cont;
+    default: return 1;
+  }
+}
+
+// One arrival per column, by one thread, once the column's flag `pred` is
+// final.  The last column to arrive publishes whether any column's flag is
+// set (in G and, when cc is in use, as the loop condition).
+__device__ void group_arrive(const KState* S0, int ncols, Group* G, int pred, Cond cc) {
+  __threadfence();
+  if (atomicAdd(&G->ticket, 1u) != (unsigned)(ncols - 1)) return;
+  __threadfence();
+  int any = 0;
+  for (int c = 0; c < ncols; ++c) any |= col_flag(S0 + c, pred);
+  if (pred == PRED_CG) G->cg_any = any;
+  else G->arn_any = any;
+  G->ticket = 0u;
+  set_cond(cc, any);
 }
 
 // Block partial -> per-block slot; returns true in the last block to arrive,
@@ -95,54 +141,79 @@ __device__ __forceinline__ bool grid_sum_last(double v, double* partials, unsign
   return true;
 }
 
+// Vector kernels run on a grid (blocks, columns): column blockIdx.y has its
+// state at S0 + blockIdx.y, its float / double vectors Np apart, its Arnoldi
+// basis vstride apart, its Z basis zstride apart and its reduction partials
+// PSTRIDE apart.
+#define KRR_COL                                   \
+  const int col = blockIdx.y;                     \
+  KState* S = S0 + col;                           \
+  const int64_t co = (int64_t)col * Np;           \
+  (void)co
+
+#define KRR_GRID_LOOP(i) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np; i += (int64_t)gridDim.x * blockDim.x)
+
 // ------------------------------------------------------------------ CG ---
-// z = 0 (z = v when there is no preconditioner), r = p = v (v = V[j] in
-// FP64, or the float vector vf), rho0 = rho = |v|^2.
-__global__ void cg_init_kernel(KState* S, const double* __restrict__ V, const float* __restrict__ vf,
-                               int64_t Np, float* __restrict__ z, float* __restrict__ r,
-                               float* __restrict__ p, double* partials, Cond cc,
-                               const int* active) {
+// For the columns selected by pred: z = 0 (z = v without preconditioner),
+// r = p = v (v = V[j] in FP64, or the float vector vf), rho0 = rho = |v|^2.
+// The other columns sit out this Arnoldi step.
+__global__ void cg_init_kernel(KState* S0, const double* __restrict__ V, int64_t vstride,
+                               const float* __restrict__ vf, int64_t Np, float* __restrict__ z,
+                               float* __restrict__ r, float* __restrict__ p, double* partials,
+                               int pred, Group* G, Cond cc) {
   __shared__ double red[8];
-  if (active && *active == 0) return;
-  const double* v = V ? V + (int64_t)S->j * Np : nullptr;
+  KRR_COL;
+  if (!col_flag(S, pred)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->cg_cont = 0;
+      S->stepping = 0;
+      group_arrive(S0, gridDim.y, G, PRED_CG, cc);
+    }
+    return;
+  }
+  const double* v = V ? V + (int64_t)col * vstride + (int64_t)S->j * Np : nullptr;
   const bool identity = S->maxit == 0;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float vi = v ? (float)v[i] : vf[i];
-    r[i] = vi;
-    p[i] = vi;
-    z[i] = identity ? vi : 0.f;
+  KRR_GRID_LOOP(i) {
+    const float vi = v ? (float)v[i] : vf[co + i];
+    r[co + i] = vi;
+    p[co + i] = vi;
+    z[co + i] = identity ? vi : 0.f;
     acc += (double)vi * (double)vi;
   }
   double tot;
-  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) {
+  if (grid_sum_last(acc, partials + col * PSTRIDE, &S->ticket, red, tot) && threadIdx.x == 0) {
     S->rho = tot;
     S->rho0 = tot;
     S->k = 0;
     S->cg_brk = 0;
     S->cg_cont = (!identity && tot > 0.0) ? 1 : 0;
-    set_cond(cc, S->cg_cont);
+    S->stepping = 1;
+    group_arrive(S0, gridDim.y, G, PRED_CG, cc);
   }
 }
 
 // z += alpha p; r -= alpha Mp; rho' = |r|^2; beta = rho'/rho; continue test.
-__global__ void cg_update_kernel(KState* S, float* __restrict__ z, float* __restrict__ r,
+__global__ void cg_update_kernel(KState* S0, float* __restrict__ z, float* __restrict__ r,
                                  const float* __restrict__ p, const float* __restrict__ Mp,
-                                 int64_t Np, double* partials, Cond cc) {
+                                 int64_t Np, double* partials, Group* G, Cond cc) {
   __shared__ double red[8];
-  if (!S->cg_cont) return;
+  KRR_COL;
+  if (!S->cg_cont) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) group_arrive(S0, gridDim.y, G, PRED_CG, cc);
+    return;
+  }
   const float a = (float)S->alpha;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    z[i] = fmaf(a, p[i], z[i]);
-    const float ri = fmaf(-a, Mp[i], r[i]);
-    r[i] = ri;
+  KRR_GRID_LOOP(i) {
+    z[co + i] = fmaf(a, p[co + i], z[co + i]);
+    const float ri = fmaf(-a, Mp[co + i], r[co + i]);
+    r[co + i] = ri;
     acc += (double)ri * (double)ri;
   }
   double tot;
-  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) {
+  if (grid_sum_last(acc, partials + col * PSTRIDE, &S->ticket, red, tot) && threadIdx.x == 0) {
     S->beta = (S->rho > 0.0) ? tot / S->rho : 0.0;
     S->rho = tot;
     S->k += 1;
@@ -150,44 +221,44 @@ __global__ void cg_update_kernel(KState* S, float* __restrict__ z, float* __rest
     if (S->cg_brk) S->breakdowns += 1;
     const bool more = !S->cg_brk && S->k < S->maxit && tot > S->eps2 * S->rho0 && isfinite(tot);
     S->cg_cont = more ? 1 : 0;
-    set_cond(cc, S->cg_cont);
+    group_arrive(S0, gridDim.y, G, PRED_CG, cc);
   }
 }
 
-// p = r + beta p.  Runs after cg_update, whose last block may have cleared
-// cg_cont; the p update is then harmless (p is not used again).
-__global__ void cg_p_kernel(const KState* S, const float* __restrict__ r, float* __restrict__ p,
-                            int64_t Np, const int* active) {
-  if (active && *active == 0) return;
+// p = r + beta p for the columns whose CG continues.
+__global__ void cg_p_kernel(KState* S0, const float* __restrict__ r, float* __restrict__ p,
+                            int64_t Np) {
+  KRR_COL;
+  if (!S->cg_cont) return;
   const float b = (float)S->beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fmaf(b, p[i], r[i]);
+  KRR_GRID_LOOP(i) p[co + i] = fmaf(b, p[co + i], r[co + i]);
 }
 
 // ------------------------------------------------------------- Arnoldi ---
-__global__ void store_z_kernel(const KState* S, const float* __restrict__ z, float* __restrict__ Z,
-                               int64_t Np, const int* active) {
-  if (active && *active == 0) return;
-  float* zj = Z + (int64_t)S->j * Np;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x)
-    zj[i] = z[i];
+__global__ void store_z_kernel(KState* S0, const float* __restrict__ z, float* __restrict__ Z,
+                               int64_t zstride, int64_t Np, int pred) {
+  KRR_COL;
+  if (!col_flag(S, pred)) return;
+  float* zj = Z + (int64_t)col * zstride + (int64_t)S->j * Np;
+  KRR_GRID_LOOP(i) zj[i] = z[co + i];
 }
 
 // h1[i] = (w, v_i), i = 0..j  (first Gram-Schmidt pass).
-__global__ void cgs_dots_kernel(KState* S, const double* __restrict__ V, const double* __restrict__ w,
-                                int64_t Np, double* partials, const int* active) {
+__global__ void cgs_dots_kernel(KState* S0, const double* __restrict__ V, int64_t vstride,
+                                const double* __restrict__ w, int64_t Np, double* partials,
+                                int pred) {
   __shared__ double red[8];
   __shared__ bool is_last;
-  if (active && *active == 0) return;
+  KRR_COL;
+  if (!col_flag(S, pred)) return;
+  V += (int64_t)col * vstride;
+  w += co;
+  partials += col * PSTRIDE;
   const int nj = S->j + 1;
   for (int c = 0; c < nj; ++c) {
     const double* vc = V + (int64_t)c * Np;
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-         i += (int64_t)gridDim.x * blockDim.x)
-      acc += vc[i] * w[i];
+    KRR_GRID_LOOP(i) acc += vc[i] * w[i];
     const double bs = block_sum(acc, red);
     if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * (MMAX + 1) + c] = bs;
   }
@@ -211,17 +282,20 @@ __global__ void cgs_dots_kernel(KState* S, const double* __restrict__ V, const d
 // w -= sum_i h1[i] v_i; h2[i] = (w, v_i) (second pass); |w|^2; then, in the
 // last block, the Hessenberg column, the Givens update of Alg. 1's least
 // squares problem and the continuation test.
-__global__ void cgs_update_kernel(KState* S, const double* __restrict__ V, double* __restrict__ w,
-                                  int64_t Np, double* partials, Cond ac, const int* active) {
+__global__ void cgs_update_kernel(KState* S0, const double* __restrict__ V, int64_t vstride,
+                                  double* __restrict__ w, int64_t Np, double* partials, int pred) {
   __shared__ double red[8];
   __shared__ bool is_last;
   __shared__ double h1s[MMAX + 1];
-  if (active && *active == 0) return;
+  KRR_COL;
+  if (!col_flag(S, pred)) return;
+  V += (int64_t)col * vstride;
+  w += co;
+  partials += col * PSTRIDE;
   const int j = S->j, nj = j + 1;
   for (int c = threadIdx.x; c < nj; c += blockDim.x) h1s[c] = S->h1[c];
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  KRR_GRID_LOOP(i) {
     double wi = w[i];
     for (int c = 0; c < nj; ++c) wi -= h1s[c] * V[(int64_t)c * Np + i];
     w[i] = wi;
@@ -229,9 +303,7 @@ __global__ void cgs_update_kernel(KState* S, const double* __restrict__ V, doubl
   // second-pass dots and the norm of w, from this block's elements
   for (int c = 0; c <= nj; ++c) {
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-         i += (int64_t)gridDim.x * blockDim.x)
-      acc += (c < nj) ? V[(int64_t)c * Np + i] * w[i] : w[i] * w[i];
+    KRR_GRID_LOOP(i) acc += (c < nj) ? V[(int64_t)c * Np + i] * w[i] : w[i] * w[i];
     const double bs = block_sum(acc, red);
     if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * (MMAX + 1) + c] = bs;
   }
@@ -289,117 +361,151 @@ __global__ void cgs_update_kernel(KState* S, const double* __restrict__ V, doubl
   S->wnorm2 = hnext;  // reused by cgs_final as the normaliser
   const bool more = !lucky && (j + 1 < S->m) && S->relres_est > S->tol_cycle;
   S->arn_cont = more ? 1 : 0;
-  set_cond(ac, S->arn_cont);
 }
 
 // v_{j+1} = (w - V h2) / h_{j+1,j}
-__global__ void cgs_final_kernel(const KState* S, double* __restrict__ V, const double* __restrict__ w,
-                                 int64_t Np, const int* active) {
+__global__ void cgs_final_kernel(KState* S0, double* __restrict__ V, int64_t vstride,
+                                 const double* __restrict__ w, int64_t Np, int pred) {
   __shared__ double h2s[MMAX + 1];
-  if (active && *active == 0) return;
+  KRR_COL;
+  if (!col_flag(S, pred)) return;
   const int j = S->j, nj = j + 1;
   if (S->lucky || j + 1 > S->m) return;
+  V += (int64_t)col * vstride;
+  w += co;
   for (int c = threadIdx.x; c < nj; c += blockDim.x) h2s[c] = S->h2[c];
   __syncthreads();
   const double inv = 1.0 / S->wnorm2;
   double* vn = V + (int64_t)nj * Np;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  KRR_GRID_LOOP(i) {
     double wi = w[i];
     for (int c = 0; c < nj; ++c) wi -= h2s[c] * V[(int64_t)c * Np + i];
     vn[i] = wi * inv;
   }
 }
 
-__global__ void arn_advance_kernel(KState* S) {
-  if (S->arn_cont) S->j += 1;
+// One thread per column: advance the columns whose Arnoldi process
+// continues; the loop goes on while any does.
+__global__ void arn_advance_kernel(KState* S0, int ncols, Group* G, Cond ac) {
+  int any = 0;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    KState* S = S0 + c;
+    if (S->arn_cont) {
+      S->j += 1;
+      any = 1;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    G->arn_any = any;
+    set_cond(ac, any);
+  }
 }
 
 // ---------------------------------------------------------- restarts -----
-// Back-substitution R y = g (R upper triangular after the rotations, kcols
-// columns), then x += Z y in float-float.
-__global__ void lsq_kernel(KState* S, const int* active) {
-  if (active && *active == 0) return;
-  const int k = S->kcols;
-  for (int r = k - 1; r >= 0; --r) {
-    double t = S->g[r];
-    for (int c = r + 1; c < k; ++c) t -= S->H[(int64_t)c * (MMAX + 1) + r] * S->y[c];
-    const double d = S->H[(int64_t)r * (MMAX + 1) + r];
-    S->y[r] = d != 0.0 ? t / d : 0.0;
+// One thread per column: back-substitution R y = g (R upper triangular after
+// the rotations, kcols columns).
+__global__ void lsq_kernel(KState* S0, int ncols, int pred) {
+  for (int cix = threadIdx.x; cix < ncols; cix += blockDim.x) {
+    KState* S = S0 + cix;
+    if (!col_flag(S, pred)) continue;
+    const int k = S->kcols;
+    for (int r = k - 1; r >= 0; --r) {
+      double t = S->g[r];
+      for (int c = r + 1; c < k; ++c) t -= S->H[(int64_t)c * (MMAX + 1) + r] * S->y[c];
+      const double d = S->H[(int64_t)r * (MMAX + 1) + r];
+      S->y[r] = d != 0.0 ? t / d : 0.0;
+    }
   }
 }
 
-__global__ void x_update_kernel(const KState* S, const float* __restrict__ Z, int64_t Np,
-                                float* __restrict__ xh, float* __restrict__ xl, const int* active) {
+// x += Z y in float-float.
+__global__ void x_update_kernel(KState* S0, const float* __restrict__ Z, int64_t zstride,
+                                int64_t Np, float* __restrict__ xh, float* __restrict__ xl,
+                                int pred) {
   __shared__ double ys[MMAX];
-  if (active && *active == 0) return;
+  KRR_COL;
+  if (!col_flag(S, pred)) return;
+  Z += (int64_t)col * zstride;
   const int k = S->kcols;
   for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = S->y[c];
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double t = (double)xh[i] + (double)xl[i];
+  KRR_GRID_LOOP(i) {
+    double t = (double)xh[co + i] + (double)xl[co + i];
     for (int c = 0; c < k; ++c) t += ys[c] * (double)Z[(int64_t)c * Np + i];
     const float h = (float)t;
-    xh[i] = h;
-    xl[i] = (float)(t - (double)h);
+    xh[co + i] = h;
+    xl[co + i] = (float)(t - (double)h);
   }
 }
 
-// After the accurate residual: convergence test and the next cycle's start
-// (Alg. 1 lines 1 and 13).  tol_stop < tol leaves room for rounding the
-// FP64 iterate to the float32 output.
-__global__ void restart_check_kernel(KState* S, Cond rc, double tol_stop) {
-  const double beta = sqrt(S->rnorm2);
-  S->relres_true = S->bnorm > 0.0 ? beta / S->bnorm : 0.0;
-  bool more = S->bnorm > 0.0 && S->relres_true > tol_stop && isfinite(beta);
-  if (more && S->cycles >= S->max_cycles) {
-    more = false;
-    S->status = KRR_NOT_CONVERGED;
+// One thread per column, after the accurate residual: convergence test and
+// the next cycle's start (Alg. 1 lines 1 and 13).  tol_stop < tol leaves
+// room for rounding.  A column that has stopped keeps its verdict (its
+// residual is not recomputed, so the test repeats it).
+__global__ void restart_check_kernel(KState* S0, int ncols, Group* G, Cond rc, double tol_stop) {
+  int any = 0;
+  for (int cix = threadIdx.x; cix < ncols; cix += blockDim.x) {
+    KState* S = S0 + cix;
+    const double beta = sqrt(S->rnorm2);
+    S->relres_true = S->bnorm > 0.0 ? beta / S->bnorm : 0.0;
+    bool more = S->bnorm > 0.0 && S->relres_true > tol_stop && isfinite(beta);
+    if (more && S->cycles >= S->max_cycles) {
+      more = false;
+      S->status = KRR_NOT_CONVERGED;
+    }
+    if (!isfinite(beta)) S->status = KRR_ERR_NONFINITE;
+    S->restart_cont = more ? 1 : 0;
+    if (more) {
+      S->cycles += 1;
+      S->beta0 = beta;
+      S->g[0] = beta;
+      for (int c = 1; c <= MMAX; ++c) S->g[c] = 0.0;
+      S->j = 0;
+      S->kcols = 0;
+      S->arn_cont = 1;
+      S->lucky = 0;
+      any = 1;
+    }
   }
-  if (!isfinite(beta)) S->status = KRR_ERR_NONFINITE;
-  S->restart_cont = more ? 1 : 0;
-  if (more) {
-    S->cycles += 1;
-    S->beta0 = beta;
-    S->g[0] = beta;
-    for (int c = 1; c <= MMAX; ++c) S->g[c] = 0.0;
-    S->j = 0;
-    S->kcols = 0;
-    S->arn_cont = 1;
-    S->lucky = 0;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    G->rst_any = any;
+    set_cond(rc, any);
   }
-  set_cond(rc, S->restart_cont);
 }
 
-// V[0] = r / beta0; re-arms the Arnoldi loop (a WHILE condition takes its
-// default only once per graph launch).
-__global__ void v0_kernel(const KState* S, const double* __restrict__ r, double* __restrict__ V,
-                          int64_t Np, const int* active, Cond ac) {
-  if (active && *active == 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(ac, 1);
+// V[0] = r / beta0 for the columns in a cycle; re-arms the Arnoldi loop (a
+// WHILE condition takes its default only once per graph launch).
+__global__ void v0_kernel(KState* S0, const double* __restrict__ r, double* __restrict__ V,
+                          int64_t vstride, int64_t Np, int pred, Group* G, Cond ac) {
+  KRR_COL;
+  if (blockIdx.x == 0 && col == 0 && threadIdx.x == 0) {
+    G->arn_any = 1;
+    set_cond(ac, 1);
+  }
+  if (!col_flag(S, pred)) return;
   const double inv = 1.0 / S->beta0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x)
-    V[i] = r[i] * inv;
+  V += (int64_t)col * vstride;
+  KRR_GRID_LOOP(i) V[i] = r[co + i] * inv;
 }
 
 // x = 0, r = b (the residual of x0 = 0), |b|^2.
-__global__ void solve_init_kernel(KState* S, const float* __restrict__ b, int64_t Np,
+__global__ void solve_init_kernel(KState* S0, const float* __restrict__ b, int64_t Np,
                                   float* __restrict__ xh, float* __restrict__ xl,
                                   double* __restrict__ r, double* partials) {
   __shared__ double red[8];
+  KRR_COL;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    xh[i] = 0.f;
-    xl[i] = 0.f;
-    const double bi = b[i];
-    r[i] = bi;
+  KRR_GRID_LOOP(i) {
+    xh[co + i] = 0.f;
+    xl[co + i] = 0.f;
+    const double bi = b[co + i];
+    r[co + i] = bi;
     acc += bi * bi;
   }
   double tot;
-  if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) {
+  if (grid_sum_last(acc, partials + col * PSTRIDE, &S->ticket, red, tot) && threadIdx.x == 0) {
     S->rnorm2 = tot;
     S->bnorm = sqrt(tot);
   }
@@ -431,8 +537,7 @@ __global__ void cg_cycle_kernel(KState* S, double tol_stop, int maxit_total) {
 // x += z in float-float
 __global__ void x_add_kernel(const float* __restrict__ z, int64_t Np, float* __restrict__ xh,
                              float* __restrict__ xl) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  KRR_GRID_LOOP(i) {
     const double t = (double)xh[i] + (double)xl[i] + (double)z[i];
     const float h = (float)t;
     xh[i] = h;
@@ -443,8 +548,7 @@ __global__ void x_add_kernel(const float* __restrict__ z, int64_t Np, float* __r
 // x = x0 (FP64, original order) gathered to sorted float-float; padding 0
 __global__ void x_from64_kernel(const double* __restrict__ x0, const int* __restrict__ perm,
                                 int64_t N, int64_t Np, float* __restrict__ xh, float* __restrict__ xl) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  KRR_GRID_LOOP(i) {
     const double v = i < N ? x0[perm[i]] : 0.0;
     const float h = (float)v;
     xh[i] = h;
@@ -455,19 +559,20 @@ __global__ void x_from64_kernel(const double* __restrict__ x0, const int* __rest
 __global__ void bnorm_kernel(KState* S, const float* __restrict__ b, int64_t Np, double* partials) {
   __shared__ double red[8];
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
-       i += (int64_t)gridDim.x * blockDim.x)
-    acc += (double)b[i] * (double)b[i];
+  KRR_GRID_LOOP(i) acc += (double)b[i] * (double)b[i];
   double tot;
   if (grid_sum_last(acc, partials, &S->ticket, red, tot) && threadIdx.x == 0) S->bnorm = sqrt(tot);
 }
 
-// Xsol[perm[i]] = xh[i] + xl[i] (FP64, original order)
+// Column blockIdx.y: out[col * N + perm[i]] = xh[i] + xl[i] (FP64, original order)
 __global__ void scatter_x64_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
-                                   const int* __restrict__ perm, int64_t N, double* __restrict__ out) {
+                                   const int* __restrict__ perm, int64_t N, int64_t Np,
+                                   double* __restrict__ out) {
+  const int64_t co = (int64_t)blockIdx.y * Np;
+  out += (int64_t)blockIdx.y * N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[perm[i]] = (double)xh[i] + (double)xl[i];
+    out[perm[i]] = (double)xh[co + i] + (double)xl[co + i];
 }
 
 __global__ void fill_zero_kernel(float* __restrict__ a, int64_t n) {
@@ -476,11 +581,17 @@ __global__ void fill_zero_kernel(float* __restrict__ a, int64_t n) {
     a[i] = 0.f;
 }
 
-__global__ void final_report_kernel(KState* S) {
-  S->relres_true = S->bnorm > 0.0 ? sqrt(S->rnorm2) / S->bnorm : 0.0;
-}
+#undef KRR_COL
+#undef KRR_GRID_LOOP
 
 // ---------------------------------------------------------------- driver --
+// One solve of mc right-hand sides of one problem in lockstep (a block
+// solve): every column runs its own FGMRES (its own Krylov basis, Givens
+// rotations and restarts), but each inner CG step applies the operator to
+// all columns' search directions in one multi-column product, and the outer
+// products and residuals of all columns go out in one launch.  Columns that
+// have finished their CG, Arnoldi step or solve sit out (predicated per
+// column) until the block's loop ends.
 struct Solver {
   Ctx& c;
   cudaStream_t st;
@@ -489,9 +600,11 @@ struct Solver {
   unsigned vblocks = 1;
   float gamma = 0.f, mshift = 0.f;
   krr_precision inner_prec = KRR_FP32;
-  int m = 30;
-  // device buffers
+  int m = 30;   // restart length
+  int mc = 1;   // columns
+  // device buffers (column-major blocks of mc columns)
   KState* S = nullptr;
+  Group* G = nullptr;
   float *b = nullptr, *xh = nullptr, *xl = nullptr, *zero = nullptr;
   double *r64 = nullptr, *V = nullptr, *w = nullptr, *partials = nullptr;
   float *Z = nullptr, *z = nullptr, *rr = nullptr, *p = nullptr, *Mp = nullptr;
@@ -499,15 +612,21 @@ struct Solver {
 
   explicit Solver(Ctx& cc) : c(cc) {}
 
-  cudaError_t alloc(int restart) {
+  int64_t vstride() const { return (int64_t)(m + 1) * Np; }
+  int64_t zstride() const { return (int64_t)m * Np; }
+  dim3 vgrid() const { return dim3(vblocks, (unsigned)mc); }
+
+  cudaError_t alloc(int restart, int ncols) {
     cudaError_t e;
     void* v;
-    const size_t n = (size_t)Np;
+    const size_t n = (size_t)Np * ncols;
     m = restart;
+    mc = ncols;
 #define KRR_WS(name, ptr, bytes)                      \
   if ((e = c.ws.get(name, bytes, &v))) return e;       \
   ptr = (decltype(ptr))v;
-    KRR_WS("kry.state", S, sizeof(KState));
+    KRR_WS("kry.state", S, sizeof(KState) * mc);
+    KRR_WS("kry.group", G, sizeof(Group));
     KRR_WS("kry.b", b, n * 4);
     KRR_WS("kry.xh", xh, n * 4);
     KRR_WS("kry.xl", xl, n * 4);
@@ -515,7 +634,7 @@ struct Solver {
     KRR_WS("kry.r64", r64, n * 8);
     KRR_WS("kry.V", V, n * 8 * (m + 1));
     KRR_WS("kry.w", w, n * 8);
-    KRR_WS("kry.partials", partials, sizeof(double) * (MMAX + 1) * 1024);
+    KRR_WS("kry.partials", partials, sizeof(double) * PSTRIDE * mc);
     KRR_WS("kry.Z", Z, n * 4 * m);
     KRR_WS("kry.z", z, n * 4);
     KRR_WS("kry.r", rr, n * 4);
@@ -523,12 +642,24 @@ struct Solver {
     KRR_WS("kry.Mp", Mp, n * 4);
 #undef KRR_WS
     vblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Np + VT - 1) / VT, 4LL * c.num_sms));
-    fill_zero_kernel<<<vblocks, VT, 0, st>>>(zero, Np); count_launch();
+    if (vblocks > (unsigned)MAX_VBLOCKS) vblocks = MAX_VBLOCKS;
+    fill_zero_kernel<<<vblocks, VT, 0, st>>>(zero, (int64_t)n); count_launch();
+    if ((e = cudaMemsetAsync(G, 0, sizeof(Group), st))) return e;
     return cudaGetLastError();
   }
 
-  // ---- one CG iteration on the inner operator: M p = K_hat p + mshift p
-  cudaError_t cg_iteration(const int* active) {
+  // Workspace and kernel attributes of every product this solver launches,
+  // so that nothing allocates inside a graph capture.
+  cudaError_t reserve() {
+    cudaError_t e = mvp_reserve(c, P, P, st);
+    if (!e && (mc > 1 || inner_prec != KRR_FP32)) e = mvp_multi_reserve(c, P, P, mc, inner_prec, st);
+    if (!e) e = mvp_acc_reserve(c, P, st, mc);
+    return e;
+  }
+
+  // ---- one CG iteration on the inner operator M p = K_hat p + mshift p,
+  // for every column whose CG continues
+  cudaError_t cg_iteration() {
     MvpOut o;
     o.out_f = Mp;
     o.dotw = p;
@@ -536,40 +667,52 @@ struct Solver {
     o.ratio_num = &S->rho;
     o.ratio_out = &S->alpha;
     o.brk_flag = &S->cg_brk;
-    o.active = active;
-    cudaError_t e = mvp_launch(c, P, P, p, p, mshift, inner_prec, o, st);
+    o.active = &G->cg_any;
+    o.col_active = &S->cg_cont;
+    o.state_stride = sizeof(KState);
+    cudaError_t e = mc == 1 ? mvp_launch(c, P, P, p, p, mshift, inner_prec, o, st)
+                            : mvp_multi_launch(c, P, P, p, mc, p, mshift, inner_prec, o, st);
     if (e) return e;
-    cg_update_kernel<<<vblocks, VT, 0, st>>>(S, z, rr, p, Mp, Np, partials, cg_c); count_launch();
-    cg_p_kernel<<<vblocks, VT, 0, st>>>(S, rr, p, Np, active); count_launch();
+    cg_update_kernel<<<vgrid(), VT, 0, st>>>(S, z, rr, p, Mp, Np, partials, G, cg_c); count_launch();
+    cg_p_kernel<<<vgrid(), VT, 0, st>>>(S, rr, p, Np); count_launch();
     return cudaGetLastError();
   }
 
   // ---- Arnoldi step after the inner solve: Z[j] = z, w = K z, CGS2, Givens
-  cudaError_t arnoldi_tail(const int* active) {
-    store_z_kernel<<<vblocks, VT, 0, st>>>(S, z, Z, Np, active); count_launch();
+  cudaError_t arnoldi_tail() {
+    store_z_kernel<<<vgrid(), VT, 0, st>>>(S, z, Z, zstride(), Np, PRED_STEP); count_launch();
     // w = K z_j with the compensated product: its error enters the flexible
     // Arnoldi relation K Z = V Hbar, and through it the true residual
-    cudaError_t e = mvp_acc_launch(c, P, z, zero, gamma, 0.0, nullptr, 1.0, w, nullptr, st);
+    AccCols cols;
+    cols.n = mc;
+    cols.active = &S->stepping;
+    cols.state_stride = sizeof(KState);
+    cudaError_t e = mvp_acc_launch(c, P, z, zero, gamma, 0.0, nullptr, 1.0, w, nullptr, st, cols);
     if (e) return e;
-    cgs_dots_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, active); count_launch();
-    cgs_update_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, partials, arn_c, active); count_launch();
-    cgs_final_kernel<<<vblocks, VT, 0, st>>>(S, V, w, Np, active); count_launch();
-    arn_advance_kernel<<<1, 1, 0, st>>>(S); count_launch();
+    cgs_dots_kernel<<<vgrid(), VT, 0, st>>>(S, V, vstride(), w, Np, partials, PRED_STEP); count_launch();
+    cgs_update_kernel<<<vgrid(), VT, 0, st>>>(S, V, vstride(), w, Np, partials, PRED_STEP); count_launch();
+    cgs_final_kernel<<<vgrid(), VT, 0, st>>>(S, V, vstride(), w, Np, PRED_STEP); count_launch();
+    arn_advance_kernel<<<1, 32, 0, st>>>(S, mc, G, arn_c); count_launch();
     return cudaGetLastError();
   }
 
-  cudaError_t cycle_tail(double tol_stop, const int* active) {
-    lsq_kernel<<<1, 1, 0, st>>>(S, active); count_launch();
-    x_update_kernel<<<vblocks, VT, 0, st>>>(S, Z, Np, xh, xl, active); count_launch();
-    cudaError_t e = residual();
+  cudaError_t cycle_tail(double tol_stop) {
+    lsq_kernel<<<1, 32, 0, st>>>(S, mc, PRED_RST); count_launch();
+    x_update_kernel<<<vgrid(), VT, 0, st>>>(S, Z, zstride(), Np, xh, xl, PRED_RST); count_launch();
+    cudaError_t e = residual(true);
     if (e) return e;
-    restart_check_kernel<<<1, 1, 0, st>>>(S, rst_c, tol_stop); count_launch();
+    restart_check_kernel<<<1, 32, 0, st>>>(S, mc, G, rst_c, tol_stop); count_launch();
     return cudaGetLastError();
   }
 
-  // r64 = b - K x (accurate), rnorm2 = |r|^2
-  cudaError_t residual() {
-    return mvp_acc_launch(c, P, xh, xl, gamma, 1.0, b, -1.0, r64, &S->rnorm2, st);
+  // r64 = b - K x (accurate), rnorm2 = |r|^2; only for the columns in a
+  // restart cycle when in_cycle is set
+  cudaError_t residual(bool in_cycle) {
+    AccCols cols;
+    cols.n = mc;
+    cols.active = in_cycle ? &S->restart_cont : nullptr;
+    cols.state_stride = sizeof(KState);
+    return mvp_acc_launch(c, P, xh, xl, gamma, 1.0, b, -1.0, r64, &S->rnorm2, st, cols);
   }
 };
 
@@ -579,9 +722,10 @@ cudaError_t read_state(Ctx& c, const KState* S, KState& h, cudaStream_t st) {
   return e;
 }
 
-template <typename T>
-cudaError_t put_field(KState* S, size_t off, T v, cudaStream_t st) {
-  return cudaMemcpyAsync(reinterpret_cast<char*>(S) + off, &v, sizeof(T), cudaMemcpyHostToDevice, st);
+cudaError_t read_group(const Group* G, Group& h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(&h, G, sizeof(Group), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  return e;
 }
 
 struct SolveCfg {
@@ -601,6 +745,16 @@ void init_state(KState& h, const SolveCfg& cfg) {
   h.tol_cycle = 0.5 * cfg.tol;
   h.max_cycles = cfg.max_cycles;
   h.status = KRR_OK;
+}
+
+// Initial states of all columns of s (host copy, then one upload).
+cudaError_t upload_states(Solver& s, const SolveCfg& cfg, std::vector<KState>& hs) {
+  hs.resize(s.mc);
+  for (auto& h : hs) init_state(h, cfg);
+  cudaError_t e = cudaMemcpyAsync(s.S, hs.data(), sizeof(KState) * s.mc, cudaMemcpyHostToDevice, s.st);
+  if (!e) e = cudaMemsetAsync(s.G, 0, sizeof(Group), s.st);
+  if (!e) e = cudaStreamSynchronize(s.st);  // hs is pageable and reused
+  return e;
 }
 
 std::vector<cudaGraphNode_t> sinks(cudaGraph_t g) {
@@ -654,7 +808,8 @@ cudaError_t fill_restart_body(Solver& s, cudaGraph_t rbody, double tol_stop) {
   if ((e = cudaGraphConditionalHandleCreate(&s.arn_c.h, rbody, 1, cudaGraphCondAssignDefault))) return e;
   s.arn_c.use = 1;
   if ((e = capture_into(s.st, rbody, [&]() -> cudaError_t {
-         v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, s.arn_c); count_launch();
+         v0_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.r64, s.V, s.vstride(), s.Np, PRED_RST, s.G,
+                                                s.arn_c); count_launch();
          return cudaGetLastError();
        })))
     return e;
@@ -662,19 +817,19 @@ cudaError_t fill_restart_body(Solver& s, cudaGraph_t rbody, double tol_stop) {
   if ((e = cudaGraphConditionalHandleCreate(&s.cg_c.h, abody, 0, cudaGraphCondAssignDefault))) return e;
   s.cg_c.use = 1;
   if ((e = capture_into(s.st, abody, [&]() -> cudaError_t {
-         cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
-                                                    s.partials, s.cg_c, nullptr); count_launch();
+         cg_init_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.V, s.vstride(), nullptr, s.Np, s.z, s.rr,
+                                                    s.p, s.partials, PRED_ARN, s.G, s.cg_c); count_launch();
          return cudaGetLastError();
        })))
     return e;
   if ((e = add_while(abody, s.cg_c.h, &cbody))) return e;
-  if ((e = capture_into(s.st, cbody, [&]() -> cudaError_t { return s.cg_iteration(nullptr); }))) return e;
-  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t { return s.arnoldi_tail(nullptr); }))) return e;
-  return capture_into(s.st, rbody, [&]() -> cudaError_t { return s.cycle_tail(tol_stop, nullptr); });
+  if ((e = capture_into(s.st, cbody, [&]() -> cudaError_t { return s.cg_iteration(); }))) return e;
+  if ((e = capture_into(s.st, abody, [&]() -> cudaError_t { return s.arnoldi_tail(); }))) return e;
+  return capture_into(s.st, rbody, [&]() -> cudaError_t { return s.cycle_tail(tol_stop); });
 }
 
-// The whole FGMRES solve (after solve_init and the first restart check) as
-// one graph:  WHILE restart { restart body }.
+// The whole FGMRES block solve (after solve_init and the first restart
+// check) as one graph:  WHILE restart { restart body }.
 cudaError_t build_graph(Solver& s, double tol_stop, cudaGraphExec_t* exec) {
   cudaError_t e;
   cudaGraph_t g, rbody;
@@ -712,15 +867,17 @@ cudaError_t capture_after(cudaStream_t st, cudaGraph_t g, const std::vector<cuda
 }
 
 // One independent branch of a batched graph: solve init and first check,
-// WHILE restart { ... }, scatter of the solution to `xout` (original order).
-cudaError_t build_branch(cudaGraph_t g, Solver& s, double tol_stop, int64_t N, double* xout) {
+// WHILE restart { ... }, scatter of the first `ncols_out` solution columns
+// to `xout` (original order, columns N apart).
+cudaError_t build_branch(cudaGraph_t g, Solver& s, double tol_stop, int64_t N, double* xout,
+                         int ncols_out) {
   cudaError_t e;
   if ((e = cudaGraphConditionalHandleCreate(&s.rst_c.h, g, 0, cudaGraphCondAssignDefault))) return e;
   s.rst_c.use = 1;
   std::vector<cudaGraphNode_t> f0, f1;
   if ((e = capture_after(s.st, g, {}, [&]() -> cudaError_t {
-         solve_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
-         restart_check_kernel<<<1, 1, 0, s.st>>>(s.S, s.rst_c, tol_stop); count_launch();
+         solve_init_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
+         restart_check_kernel<<<1, 32, 0, s.st>>>(s.S, s.mc, s.G, s.rst_c, tol_stop); count_launch();
          return cudaGetLastError();
        }, f0)))
     return e;
@@ -733,9 +890,30 @@ cudaError_t build_branch(cudaGraph_t g, Solver& s, double tol_stop, int64_t N, d
   if ((e = cudaGraphAddNode(&wnode, g, f0.data(), nullptr, f0.size(), &np))) return e;
   if ((e = fill_restart_body(s, np.conditional.phGraph_out[0], tol_stop))) return e;
   return capture_after(s.st, g, {wnode}, [&]() -> cudaError_t {
-    scatter_x64_kernel<<<s.vblocks, VT, 0, s.st>>>(s.xh, s.xl, s.P.perm, N, xout); count_launch();
+    scatter_x64_kernel<<<dim3(s.vblocks, (unsigned)ncols_out), VT, 0, s.st>>>(s.xh, s.xl, s.P.perm, N,
+                                                                                s.Np, xout); count_launch();
     return cudaGetLastError();
   }, f1);
+}
+
+// Columns per block for m right-hand sides: as few blocks of at most
+// MAX_COLS columns as possible, all of the same width (the last one padded
+// with zero right-hand sides, which stop at the first check).
+int block_width(int m_rhs) {
+  const int nblocks = (m_rhs + MAX_COLS - 1) / MAX_COLS;
+  return (m_rhs + nblocks - 1) / nblocks;
+}
+
+// Sorted right-hand sides of columns [col0, col0 + ncols) of B (N x m, columns
+// N apart) into s.b, the remaining columns of the block zero.
+cudaError_t load_rhs(Solver& s, const float* B, int64_t N, int ncols) {
+  cudaError_t e = gather_sorted(B, N, ncols, s.P.perm, s.Np, s.b, s.st);
+  if (!e && ncols < s.mc) {
+    fill_zero_kernel<<<s.vblocks, VT, 0, s.st>>>(s.b + (size_t)ncols * s.Np, (int64_t)(s.mc - ncols) * s.Np);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace
@@ -784,48 +962,45 @@ void fill_info(const KState& h, float ms, krr_solve_info* info) {
   info->status = (krr_status)h.status;
 }
 
-// One FGMRES solve of the sorted right-hand side already in s.b (exec: the
-// solve graph, or null for the host-driven loop).
-krr_status fgmres_one(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec, KState& hs,
-                      float* ms_out) {
+// One block solve of the sorted right-hand sides already in s.b (exec: the
+// solve graph, or null for the host-driven loop); final states in hs.
+krr_status fgmres_block(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec,
+                        std::vector<KState>& hs, float* ms_out) {
   Ctx& c = s.c;
   const char* fn = "krr_fgmres_solve";
   cudaError_t e;
-  init_state(hs, cfg);
-  if ((e = cudaMemcpyAsync(s.S, &hs, sizeof(KState), cudaMemcpyHostToDevice, s.st)))
-    return cuda_error(c, e, fn);
-  cudaEventRecord(c.ev0, s.st);
-  solve_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
-  // the first restart check turns x0 = 0, r0 = b into the first cycle
-  restart_check_kernel<<<1, 1, 0, s.st>>>(s.S, Cond{}, 0.5 * cfg.tol); count_launch();
+  if ((e = upload_states(s, cfg, hs))) return cuda_error(c, e, fn);
   const double tol_stop = 0.5 * cfg.tol;
+  cudaEventRecord(c.ev0, s.st);
+  solve_init_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
+  // the first restart check turns x0 = 0, r0 = b into the first cycle
+  restart_check_kernel<<<1, 32, 0, s.st>>>(s.S, s.mc, s.G, Cond{}, tol_stop); count_launch();
+  Group g;
   if (exec) {
     // the restart loop's default condition is 1: skip the graph when the
-    // first check already stopped (b = 0)
-    KState chk;
-    if ((e = read_state(c, s.S, chk, s.st))) return cuda_error(c, e, fn);
-    if (chk.restart_cont && (e = cudaGraphLaunch(exec, s.st))) return cuda_error(c, e, fn);
+    // first check already stopped every column (b = 0)
+    if ((e = read_group(s.G, g, s.st))) return cuda_error(c, e, fn);
+    if (g.rst_any && (e = cudaGraphLaunch(exec, s.st))) return cuda_error(c, e, fn);
   } else {
     for (;;) {
-      KState h;
-      if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
-      if (!h.restart_cont) break;
-      v0_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.r64, s.V, s.Np, nullptr, Cond{}); count_launch();
+      if ((e = read_group(s.G, g, s.st))) return cuda_error(c, e, fn);
+      if (!g.rst_any) break;
+      v0_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.r64, s.V, s.vstride(), s.Np, PRED_RST, s.G, Cond{}); count_launch();
       for (;;) {
-        cg_init_kernel<<<s.vblocks, VT, 0, s.st>>>(s.S, s.V, nullptr, s.Np, s.z, s.rr, s.p,
-                                                   s.partials, Cond{}, nullptr); count_launch();
+        cg_init_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.V, s.vstride(), nullptr, s.Np, s.z, s.rr, s.p,
+                                                   s.partials, PRED_ARN, s.G, Cond{}); count_launch();
         for (;;) {
-          if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
-          if (!h.cg_cont) break;
+          if ((e = read_group(s.G, g, s.st))) return cuda_error(c, e, fn);
+          if (!g.cg_any) break;
           // predicated batch: iterations after convergence do nothing
           for (int b = 0; b < 8; ++b)
-            if ((e = s.cg_iteration(&s.S->cg_cont))) return cuda_error(c, e, fn);
+            if ((e = s.cg_iteration())) return cuda_error(c, e, fn);
         }
-        if ((e = s.arnoldi_tail(nullptr))) return cuda_error(c, e, fn);
-        if ((e = read_state(c, s.S, h, s.st))) return cuda_error(c, e, fn);
-        if (!h.arn_cont) break;
+        if ((e = s.arnoldi_tail())) return cuda_error(c, e, fn);
+        if ((e = read_group(s.G, g, s.st))) return cuda_error(c, e, fn);
+        if (!g.arn_any) break;
       }
-      if ((e = s.cycle_tail(tol_stop, nullptr))) return cuda_error(c, e, fn);
+      if ((e = s.cycle_tail(tol_stop))) return cuda_error(c, e, fn);
     }
   }
   cudaEventRecord(c.ev1, s.st);
@@ -833,9 +1008,28 @@ krr_status fgmres_one(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec, KSta
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c.ev0, c.ev1);
   *ms_out = ms;
-  if ((e = read_state(c, s.S, hs, s.st))) return cuda_error(c, e, fn);
-  if (hs.status == KRR_OK && hs.relres_true > cfg.tol) hs.status = KRR_NOT_CONVERGED;
+  if ((e = cudaMemcpyAsync(hs.data(), s.S, sizeof(KState) * s.mc, cudaMemcpyDeviceToHost, s.st)) ||
+      (e = cudaStreamSynchronize(s.st)))
+    return cuda_error(c, e, fn);
+  for (auto& h : hs)
+    if (h.status == KRR_OK && h.relres_true > cfg.tol) h.status = KRR_NOT_CONVERGED;
   return KRR_OK;
+}
+
+// Enqueue the caller-stream join for the handle's work stream.
+struct Join {
+  Ctx& c;
+  cudaStream_t ust;
+  ~Join() {
+    cudaEventRecord(c.ev_out, c.work);
+    cudaStreamWaitEvent(ust, c.ev_out, 0);
+  }
+};
+
+cudaError_t fork_work(Ctx& c, cudaStream_t ust) {
+  cudaError_t e = cudaEventRecord(c.ev_in, ust);
+  if (!e) e = cudaStreamWaitEvent(c.work, c.ev_in, 0);
+  return e;
 }
 
 }  // namespace
@@ -862,18 +1056,10 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
   cudaStream_t ust = (cudaStream_t)stream;
   cudaStream_t st = c.work;
   {
-    cudaError_t e0 = cudaEventRecord(c.ev_in, ust);
-    if (!e0) e0 = cudaStreamWaitEvent(st, c.ev_in, 0);
+    cudaError_t e0 = fork_work(c, ust);
     if (e0) return cuda_error(c, e0, fn);
   }
-  struct Join {
-    Ctx& c;
-    cudaStream_t ust;
-    ~Join() {
-      cudaEventRecord(c.ev_out, c.work);
-      cudaStreamWaitEvent(ust, c.ev_out, 0);
-    }
-  } join{c, ust};
+  Join join{c, ust};
   float *dX, *dB;
   double* dXs;
   bool sX, sB, sXs;
@@ -888,12 +1074,10 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
   sv.gamma = gamma;
   sv.mshift = (float)(gamma + cfg.delta);
   sv.inner_prec = cfg.inner_prec;
-  if ((e = sv.alloc(cfg.restart))) return cuda_error(c, e, fn);
+  const int width = block_width(m_rhs);
+  if ((e = sv.alloc(cfg.restart, width))) return cuda_error(c, e, fn);
   // size every workspace buffer now: nothing may allocate inside a capture
-  if ((e = mvp_reserve(c, sv.P, sv.P, st))) return cuda_error(c, e, fn);
-  if (cfg.inner_prec != KRR_FP32 && (e = mvp_multi_reserve(c, sv.P, sv.P, 1, cfg.inner_prec, st)))
-    return cuda_error(c, e, fn);
-  if ((e = mvp_acc_reserve(c, sv.P, st))) return cuda_error(c, e, fn);
+  if ((e = sv.reserve())) return cuda_error(c, e, fn);
   cudaGraphExec_t exec = nullptr;
   sv.cg_c = sv.arn_c = sv.rst_c = Cond{};
   if (cfg.graph) {
@@ -909,16 +1093,19 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
     }
   } guard{exec};
   krr_status worst = KRR_OK;
-  for (int col = 0; col < m_rhs; ++col) {
-    if ((e = gather_sorted(dB + (size_t)col * N, N, 1, sv.P.perm, sv.Np, sv.b, st)))
-      return cuda_error(c, e, fn);
-    KState hs;
+  std::vector<KState> hs;
+  for (int col0 = 0; col0 < m_rhs; col0 += width) {
+    const int ncols = std::min(width, m_rhs - col0);
+    if ((e = load_rhs(sv, dB + (size_t)col0 * N, N, ncols))) return cuda_error(c, e, fn);
     float ms = 0.f;
-    if ((s = fgmres_one(sv, cfg, exec, hs, &ms))) return s;
-    scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, dXs + (size_t)col * N); count_launch();
+    if ((s = fgmres_block(sv, cfg, exec, hs, &ms))) return s;
+    scatter_x64_kernel<<<dim3(sv.vblocks, (unsigned)ncols), VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, sv.Np,
+                                                                          dXs + (size_t)col0 * N); count_launch();
     if ((e = cudaGetLastError())) return cuda_error(c, e, fn);
-    if (info) fill_info(hs, ms, info + col);
-    if (hs.status != KRR_OK && worst == KRR_OK) worst = (krr_status)hs.status;
+    for (int k = 0; k < ncols; ++k) {
+      if (info) fill_info(hs[k], ms, info + col0 + k);
+      if (hs[k].status != KRR_OK && worst == KRR_OK) worst = (krr_status)hs[k].status;
+    }
   }
   if (sXs && (e = cudaMemcpyAsync(Xsol, dXs, sizeof(double) * N * m_rhs, cudaMemcpyDeviceToHost, st)))
     return cuda_error(c, e, fn);
@@ -950,18 +1137,10 @@ krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d, float si
   cudaStream_t ust = (cudaStream_t)stream;
   cudaStream_t st = c.work;
   {
-    cudaError_t e0 = cudaEventRecord(c.ev_in, ust);
-    if (!e0) e0 = cudaStreamWaitEvent(st, c.ev_in, 0);
+    cudaError_t e0 = fork_work(c, ust);
     if (e0) return cuda_error(c, e0, fn);
   }
-  struct Join {
-    Ctx& c;
-    cudaStream_t ust;
-    ~Join() {
-      cudaEventRecord(c.ev_out, c.work);
-      cudaStreamWaitEvent(ust, c.ev_out, 0);
-    }
-  } join{c, ust};
+  Join join{c, ust};
   float *dX, *db;
   double* dx;
   bool sX, sb, sx;
@@ -976,42 +1155,42 @@ krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d, float si
   sv.gamma = shift;   // the operator of this solve is K_hat + shift I throughout
   sv.mshift = shift;
   sv.inner_prec = prec;
-  if ((e = sv.alloc(1))) return cuda_error(c, e, fn);
-  if ((e = mvp_reserve(c, sv.P, sv.P, st))) return cuda_error(c, e, fn);
-  if ((e = mvp_acc_reserve(c, sv.P, st))) return cuda_error(c, e, fn);
-  if (prec != KRR_FP32 && (e = mvp_multi_reserve(c, sv.P, sv.P, 1, prec, st))) return cuda_error(c, e, fn);
+  if ((e = sv.alloc(1, 1))) return cuda_error(c, e, fn);
+  if ((e = sv.reserve())) return cuda_error(c, e, fn);
   KState hs;
   memset(&hs, 0, sizeof(hs));
   hs.status = KRR_OK;
   if ((e = cudaMemcpyAsync(sv.S, &hs, sizeof(KState), cudaMemcpyHostToDevice, st))) return cuda_error(c, e, fn);
+  if ((e = cudaStreamSynchronize(st))) return cuda_error(c, e, fn);
   if ((e = gather_sorted(db, N, 1, sv.P.perm, sv.Np, sv.b, st))) return cuda_error(c, e, fn);
   cudaEventRecord(c.ev0, st);
   x_from64_kernel<<<sv.vblocks, VT, 0, st>>>(dx, sv.P.perm, N, sv.Np, sv.xh, sv.xl); count_launch();
   bnorm_kernel<<<sv.vblocks, VT, 0, st>>>(sv.S, sv.b, sv.Np, sv.partials); count_launch();
-  if ((e = sv.residual())) return cuda_error(c, e, fn);
+  if ((e = sv.residual(false))) return cuda_error(c, e, fn);
   const double tol_stop = tol;
   for (;;) {
     cg_cycle_kernel<<<1, 1, 0, st>>>(sv.S, tol_stop, maxit); count_launch();
     KState hcur;
     if ((e = read_state(c, sv.S, hcur, st))) return cuda_error(c, e, fn);
     if (!hcur.restart_cont) break;
-    cg_init_kernel<<<sv.vblocks, VT, 0, st>>>(sv.S, sv.r64, nullptr, sv.Np, sv.z, sv.rr, sv.p,
-                                              sv.partials, Cond{}, nullptr); count_launch();
+    cg_init_kernel<<<sv.vblocks, VT, 0, st>>>(sv.S, sv.r64, 0, nullptr, sv.Np, sv.z, sv.rr, sv.p,
+                                              sv.partials, PRED_ALL, sv.G, Cond{}); count_launch();
+    Group g;
     for (;;) {
       for (int bt = 0; bt < 16; ++bt)
-        if ((e = sv.cg_iteration(&sv.S->cg_cont))) return cuda_error(c, e, fn);
-      if ((e = read_state(c, sv.S, hcur, st))) return cuda_error(c, e, fn);
-      if (!hcur.cg_cont) break;
+        if ((e = sv.cg_iteration())) return cuda_error(c, e, fn);
+      if ((e = read_group(sv.G, g, st))) return cuda_error(c, e, fn);
+      if (!g.cg_any) break;
     }
     x_add_kernel<<<sv.vblocks, VT, 0, st>>>(sv.z, sv.Np, sv.xh, sv.xl); count_launch();
-    if ((e = sv.residual())) return cuda_error(c, e, fn);
+    if ((e = sv.residual(false))) return cuda_error(c, e, fn);
   }
   cudaEventRecord(c.ev1, st);
   if ((e = cudaEventSynchronize(c.ev1))) return cuda_error(c, e, fn);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c.ev0, c.ev1);
   if ((e = read_state(c, sv.S, hs, st))) return cuda_error(c, e, fn);
-  scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, dx); count_launch();
+  scatter_x64_kernel<<<sv.vblocks, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, sv.Np, dx); count_launch();
   if (sx && (e = cudaMemcpyAsync(x, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, st)))
     return cuda_error(c, e, fn);
   krr_status de = read_device_error(c, st, fn);
@@ -1056,39 +1235,42 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
   cudaStream_t ust = (cudaStream_t)stream;
   cudaStream_t st = c.work;
   {
-    cudaError_t e0 = cudaEventRecord(c.ev_in, ust);
-    if (!e0) e0 = cudaStreamWaitEvent(st, c.ev_in, 0);
+    cudaError_t e0 = fork_work(c, ust);
     if (e0) return cuda_error(c, e0, fn);
   }
-  struct Join {
-    Ctx& c;
-    cudaStream_t ust;
-    ~Join() {
-      cudaEventRecord(c.ev_out, c.work);
-      cudaStreamWaitEvent(ust, c.ev_out, 0);
-    }
-  } join{c, ust};
+  Join join{c, ust};
   cudaError_t e;
-  // One branch per (problem, right-hand side), each with its own context;
-  // problems share their prepared points among their branches.
-  const int nbr = nprob * m_rhs;
+  // One branch per (problem, block of right-hand sides): a block solve with
+  // its own context; a problem's blocks share its prepared points.
+  const int width = block_width(m_rhs);
+  const int per_prob = (m_rhs + width - 1) / width;
+  // graphs of at most BRANCHES_PER_GRAPH independent branches, launched in
+  // turn (larger graphs of nested conditional loops are not used: one of
+  // 1024 branches failed on the device)
+  constexpr int BRANCHES_PER_GRAPH = 32;
+  int nbr = 0;
+  for (int k = 0; k < nprob; ++k)
+    if (probs[k].N > 0) nbr += per_prob;
+  if (nbr == 0) return KRR_OK;
   // concurrent branches share the SMs: plan each product for its share
-  const int slots = std::max(16, 2 * c.num_sms * 4 / std::max(1, nbr));
-  std::vector<std::unique_ptr<Solver>> sv;
+  const int slots = std::max(16, 2 * c.num_sms * 4 / std::min(nbr, BRANCHES_PER_GRAPH));
+  struct Branch {
+    std::unique_ptr<Solver> sv;
+    int prob, col0, ncols;
+    Ctx* ctx;
+  };
+  std::vector<Branch> br;
   std::vector<PointsDev> pts(nprob);
-  std::vector<int> branch_prob;
   for (int k = 0; k < nprob; ++k) {
     const krr_problem& pr = probs[k];
     if (pr.N == 0) continue;
-    Ctx* pc;
-    if ((e = sub_context(c, (size_t)k * m_rhs, &pc))) return cuda_error(c, e, fn);
-    pc->plan_slots = slots;
-    if ((e = prepare_points(*pc, pr.X, pr.N, d, sigma, "bat.pts", pts[k], st))) return cuda_error(c, e, fn);
     const double delta = opts && opts->delta >= 0.0 ? opts->delta : (pr.gamma > 0.f ? 10.0 * pr.gamma : 1e-3);
-    for (int r = 0; r < m_rhs; ++r) {
+    for (int col0 = 0; col0 < m_rhs; col0 += width) {
       Ctx* bc;
-      if ((e = sub_context(c, (size_t)k * m_rhs + r, &bc))) return cuda_error(c, e, fn);
+      if ((e = sub_context(c, br.size(), &bc))) return cuda_error(c, e, fn);
       bc->plan_slots = slots;
+      if (col0 == 0 && (e = prepare_points(*bc, pr.X, pr.N, d, sigma, "bat.pts", pts[k], st)))
+        return cuda_error(c, e, fn);
       auto so = std::make_unique<Solver>(*bc);
       so->st = st;
       so->P = pts[k];
@@ -1096,34 +1278,24 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
       so->gamma = pr.gamma;
       so->mshift = (float)(pr.gamma + delta);
       so->inner_prec = cfg.inner_prec;
-      if ((e = so->alloc(cfg.restart))) return cuda_error(c, e, fn);
-      if ((e = mvp_reserve(*bc, so->P, so->P, st))) return cuda_error(c, e, fn);
-      if ((e = mvp_acc_reserve(*bc, so->P, st))) return cuda_error(c, e, fn);
-      if (cfg.inner_prec != KRR_FP32 && (e = mvp_multi_reserve(*bc, so->P, so->P, 1, cfg.inner_prec, st)))
-        return cuda_error(c, e, fn);
-      KState hs;
-      init_state(hs, cfg);
-      if ((e = cudaMemcpyAsync(so->S, &hs, sizeof(KState), cudaMemcpyHostToDevice, st)))
-        return cuda_error(c, e, fn);
-      if ((e = gather_sorted(pr.B + (size_t)r * pr.N, pr.N, 1, pts[k].perm, so->Np, so->b, st)))
-        return cuda_error(c, e, fn);
-      sv.push_back(std::move(so));
-      branch_prob.push_back(k * m_rhs + r);
+      const int ncols = std::min(width, m_rhs - col0);
+      if ((e = so->alloc(cfg.restart, width))) return cuda_error(c, e, fn);
+      if ((e = so->reserve())) return cuda_error(c, e, fn);
+      std::vector<KState> hs;
+      if ((e = upload_states(*so, cfg, hs))) return cuda_error(c, e, fn);
+      if ((e = load_rhs(*so, pr.B + (size_t)col0 * pr.N, pr.N, ncols))) return cuda_error(c, e, fn);
+      br.push_back(Branch{std::move(so), k, col0, ncols, bc});
     }
   }
-  if (sv.empty()) return KRR_OK;
-  // graphs of at most BRANCHES_PER_GRAPH independent branches, one solve
-  // each, launched in turn (larger graphs of nested conditional loops are not
-  // used: one of 1024 branches failed on the device)
-  constexpr size_t BRANCHES_PER_GRAPH = 32;
   float ms = 0.f;
-  for (size_t b0 = 0; b0 < sv.size(); b0 += BRANCHES_PER_GRAPH) {
-    const size_t b1 = std::min(sv.size(), b0 + BRANCHES_PER_GRAPH);
+  for (size_t b0 = 0; b0 < br.size(); b0 += BRANCHES_PER_GRAPH) {
+    const size_t b1 = std::min(br.size(), b0 + (size_t)BRANCHES_PER_GRAPH);
     cudaGraph_t g;
     if ((e = cudaGraphCreate(&g, 0))) return cuda_error(c, e, fn);
     for (size_t b = b0; b < b1; ++b) {
-      const int k = branch_prob[b] / m_rhs, r = branch_prob[b] % m_rhs;
-      if ((e = build_branch(g, *sv[b], 0.5 * cfg.tol, probs[k].N, probs[k].Xsol + (size_t)r * probs[k].N))) {
+      const Branch& x = br[b];
+      const krr_problem& pr = probs[x.prob];
+      if ((e = build_branch(g, *x.sv, 0.5 * cfg.tol, pr.N, pr.Xsol + (size_t)x.col0 * pr.N, x.ncols))) {
         cudaGraphDestroy(g);
         cudaGetLastError();
         return cuda_error(c, e, "krr_fgmres_solve_batched (graph build)");
@@ -1144,30 +1316,33 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
     ms += part_ms;
   }
   krr_status worst = KRR_OK;
-  for (size_t b = 0; b < sv.size(); ++b) {
-    KState hs;
-    if ((e = read_state(c, sv[b]->S, hs, st))) return cuda_error(c, e, fn);
-    if (hs.status == KRR_OK && hs.relres_true > cfg.tol) hs.status = KRR_NOT_CONVERGED;
-    if (info) fill_info(hs, ms, info + branch_prob[b]);
-    if (hs.status != KRR_OK && worst == KRR_OK) worst = (krr_status)hs.status;
+  for (const Branch& x : br) {
+    std::vector<KState> hs(x.sv->mc);
+    if ((e = cudaMemcpyAsync(hs.data(), x.sv->S, sizeof(KState) * x.sv->mc, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return cuda_error(c, e, fn);
+    for (int k = 0; k < x.ncols; ++k) {
+      KState& hk = hs[k];
+      if (hk.status == KRR_OK && hk.relres_true > cfg.tol) hk.status = KRR_NOT_CONVERGED;
+      if (info) fill_info(hk, ms, info + (size_t)x.prob * m_rhs + x.col0 + k);
+      if (hk.status != KRR_OK && worst == KRR_OK) worst = (krr_status)hk.status;
+    }
   }
   // device error words of the branches' contexts (read through this handle's
   // pinned status word)
-  for (size_t b = 0; b < sv.size(); ++b) {
-    Ctx* bc = c.subs[branch_prob[b]];
-    if ((e = cudaMemcpyAsync(c.h_status, bc->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+  for (const Branch& x : br) {
+    if ((e = cudaMemcpyAsync(c.h_status, x.ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
       return cuda_error(c, e, fn);
     if (*c.h_status != DEV_OK) {
       const int v = *c.h_status;
-      cudaMemsetAsync(bc->d_err, 0, sizeof(int), st);
+      cudaMemsetAsync(x.ctx->d_err, 0, sizeof(int), st);
       return set_error(c, v == DEV_TIMEOUT ? KRR_ERR_TIMEOUT : KRR_ERR_NONFINITE,
-                       "%s: problem %d: device error %d", fn, branch_prob[b] / m_rhs, v);
+                       "%s: problem %d: device error %d", fn, x.prob, v);
     }
   }
   if (worst != KRR_OK) set_error(c, worst, "%s: a problem did not reach the tolerance", fn);
   return worst;
 }
-
 
 }  // extern "C"

@@ -66,7 +66,6 @@ struct MvpParams {
   float s;              // sqrt(log2(e) / (2 sigma^2))
   const int* active;    // predication flag (null: always run)
   int64_t part_stride;  // distance between splits in part (Nt_pad for one column)
-  int direct_only;      // skip expanded-form warp blocks (the tensor-core kernel does them)
 };
 
 // Warp-cooperative transform of one raw source tile for this warp's centre:
@@ -181,8 +180,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   // ---- this warp's target block
   const int64_t slot = (int64_t)blockIdx.x * NW + warp;
   const int64_t nexp = *p.tn_exp;
-  if (p.direct_only && ((int64_t)blockIdx.x + 1) * NW <= nexp) return;  // CTA fully expanded
-  const bool live = slot < p.nblk && !(p.direct_only && slot < nexp);
+  const bool live = slot < p.nblk;
   const int64_t blk = live ? p.torder[slot] : 0;
   const int64_t last = min(((int64_t)blockIdx.x + 1) * NW, p.nblk);  // CTA's block slots end
   const bool expanded = last <= nexp;  // uniform over the CTA
@@ -294,60 +292,211 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   }
 }
 
+// Direct-form warp blocks for several columns at once: one exponential per
+// pair, shared by the m <= MC weight columns (a pair costs d subtractions, d
+// multiply-adds, a multiply by -s^2, one MUFU.EX2 and m FMAs).  One target
+// per thread; the eight warps of a CTA cover 256 consecutive targets, that is
+// 8 / T target blocks of 32 T points (T = 8: one super-block).  Coordinates and the m weight columns of
+// a source tile arrive by 1-D TMA bulk copies (RS-stage ring); weight rows
+// m..MC-1 of every stage are zero.  Per-tile float32 sums fold with Kahan
+// compensation into one FP64 partial per (split, column, target).
+template <int D, int MC>
+constexpr size_t dirm_smem_bytes() {
+  return sizeof(float) * 3 * (D + MC) * TS;
+}
+
+template <int D, int MC>
+__global__ void __launch_bounds__(NT, 2) mvp_dirm_kernel(const MvpParams p, const float* __restrict__ Q,
+                                                         int64_t q_stride, int m, int T, int64_t slot0) {
+  constexpr int RS = 3;
+  constexpr uint32_t kStage = (D + MC) * TS;
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t bars[RS];
+  __shared__ volatile int abort_flag;
+  if (p.active && *p.active == 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bpc = NW / T;  // warp blocks per CTA
+  const int64_t nexp = *p.tn_exp;
+  const int64_t cta_end = min(slot0 + ((int64_t)blockIdx.x + 1) * bpc, p.nblk);
+  if (cta_end <= nexp) return;  // every block of this CTA is expanded-form
+  const int64_t slot = slot0 + (int64_t)blockIdx.x * bpc + warp / T;
+  const bool live = slot < p.nblk && slot >= nexp;
+  const int64_t blk = live ? p.torder[slot] : 0;
+  const int64_t i = blk * 32 * T + 32 * (warp % T) + lane;
+  const bool valid = live && i < p.Nt_pad;
+  float xi[D];
+  {
+    const int64_t base = (i / TS) * (int64_t)D * TS + (i % TS);
+#pragma unroll
+    for (int k = 0; k < D; ++k) xi[k] = valid ? p.xt[base + (int64_t)k * TS] : 0.f;
+  }
+  if (blockIdx.y == 0 && valid) p.fac[i] = 1.f;
+  const float ns2 = -(p.s * p.s);
+
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+
+  float sum[MC], comp[MC];
+#pragma unroll
+  for (int c = 0; c < MC; ++c) sum[c] = comp[c] = 0.f;
+
+  auto issue = [&](int r) {
+    const int stage = r % RS;
+    const int64_t tile = t_begin + r;
+    float* dst = smem + stage * kStage;
+    mbar_arrive_expect_tx(&bars[stage], (uint32_t)(D + m) * TS * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    for (int c = 0; c < m; ++c)
+      bulk_g2s(dst + (D + c) * TS, Q + c * q_stride + tile * (int64_t)TS, TS * 4, &bars[stage]);
+  };
+
+  // weight rows of absent columns stay zero in every stage
+  for (int idx = tid; idx < RS * (MC - m) * TS; idx += NT) {
+    const int stage = idx / ((MC - m) * TS), rem = idx % ((MC - m) * TS);
+    smem[stage * kStage + (D + m) * TS + rem] = 0.f;
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < RS; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RS, nt); ++issued) issue(issued);
+
+  for (int r = 0; r < nt; ++r) {
+    if (tid == 0 && r >= 1 && r - 1 + RS < nt) {
+      fence_proxy_async_smem();
+      issue(r - 1 + RS);
+      ++issued;
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[r % RS], (r / RS) & 1));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    } else if (live) {
+      const float* cx = smem + (r % RS) * kStage;
+      const float* cq = cx + D * TS;
+      float acc[MC];
+#pragma unroll
+      for (int c = 0; c < MC; ++c) acc[c] = 0.f;
+#pragma unroll 1
+      for (int j = 0; j < TS; j += 4) {
+        float e[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) e[v] = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float4 xk = *reinterpret_cast<const float4*>(cx + k * TS + j);
+          const float d0 = xi[k] - xk.x, d1 = xi[k] - xk.y, d2 = xi[k] - xk.z, d3 = xi[k] - xk.w;
+          e[0] = fmaf(d0, d0, e[0]);
+          e[1] = fmaf(d1, d1, e[1]);
+          e[2] = fmaf(d2, d2, e[2]);
+          e[3] = fmaf(d3, d3, e[3]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) e[v] = ex2(e[v] * ns2);
+#pragma unroll
+        for (int c = 0; c < MC; ++c) {
+          const float4 qq = *reinterpret_cast<const float4*>(cq + c * TS + j);
+          acc[c] = fmaf(qq.x, e[0], acc[c]);
+          acc[c] = fmaf(qq.y, e[1], acc[c]);
+          acc[c] = fmaf(qq.z, e[2], acc[c]);
+          acc[c] = fmaf(qq.w, e[3], acc[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < MC; ++c) kahan_add(sum[c], comp[c], acc[c]);
+    }
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RS], (r / RS) & 1);
+    __syncthreads();
+    return;
+  }
+  if (valid) {
+    double* part = p.part + (int64_t)blockIdx.y * p.part_stride + i;
+#pragma unroll
+    for (int c = 0; c < MC; ++c)
+      if (c < m) part[(int64_t)c * p.Nt_pad] = (double)sum[c] - (double)comp[c];
+  }
+}
+
 struct FinParams {
   const double* part;
   int splits;
+  // multi-column products: targets of direct-form super-blocks (sb_flag 0)
+  // take their sums from part2 (splits2 splits) instead
+  const double* part2;
+  int splits2;
+  const int* sb_flag;
   int64_t part_stride;
   int64_t N, Npad;
   const float* fac;
   const float* qdiag;
   float shift;
   MvpOut o;
-  double* dot_part;        // [gridDim.x] per-block dot partials
-  unsigned int* dot_count; // arrival counter (reset by the last block)
+  double* dot_part;        // [columns][gridDim.x] per-block dot partials
+  unsigned int* dot_count; // [columns] arrival counters (reset by the last block)
 };
 
 __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
   __shared__ double red[8];
   __shared__ bool is_last;
   if (f.o.active && *f.o.active == 0) return;
+  // column blockIdx.y: its vectors are Npad (original order: N) apart, its
+  // scalars state_stride bytes apart
+  const int col = blockIdx.y;
+  const size_t so = (size_t)col * f.o.state_stride;
+  auto at = [so](auto* ptr) { return (decltype(ptr))((const char*)ptr + so); };
+  if (f.o.col_active && *at(f.o.col_active) == 0) return;
+  const int64_t cv = (int64_t)col * f.Npad;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double out = 0.0, dotv = 0.0;
   if (i < f.N) {
+    const bool second = f.sb_flag && f.sb_flag[i / SB] == 0;
+    const double* part = (second ? f.part2 : f.part) + cv;
+    const int splits = second ? f.splits2 : f.splits;
     double s = 0.0;
-    for (int sp = 0; sp < f.splits; ++sp) s += f.part[(int64_t)sp * f.part_stride + i];
+    for (int sp = 0; sp < splits; ++sp) s += part[(int64_t)sp * f.part_stride + i];
     double y = (double)f.fac[i] * s;
-    if (f.qdiag) y += (double)f.shift * (double)f.qdiag[i];
+    if (f.qdiag) y += (double)f.shift * (double)f.qdiag[cv + i];
     out = (double)f.o.alpha * y;
-    if (f.o.u) out += (double)f.o.beta * (double)f.o.u[i];
-    if (f.o.out_orig) f.o.out_orig[f.o.perm[i]] = (float)out;
-    if (f.o.dotw) dotv = out * (double)f.o.dotw[i];
+    if (f.o.u) out += (double)f.o.beta * (double)f.o.u[cv + i];
+    if (f.o.out_orig) f.o.out_orig[(int64_t)col * f.N + f.o.perm[i]] = (float)out;
+    if (f.o.dotw) dotv = out * (double)f.o.dotw[cv + i];
   }
   if (i < f.Npad) {
-    if (f.o.out_f) f.o.out_f[i] = (float)out;
-    if (f.o.out_d) f.o.out_d[i] = out;
+    if (f.o.out_f) f.o.out_f[cv + i] = (float)out;
+    if (f.o.out_d) f.o.out_d[cv + i] = out;
   }
   if (f.o.dot) {
+    double* dot_part = f.dot_part + (int64_t)col * gridDim.x;
+    unsigned* dot_count = f.dot_count + col;
     const double bs = block_sum(dotv, red);
     if (threadIdx.x == 0) {
-      f.dot_part[blockIdx.x] = bs;
+      dot_part[blockIdx.x] = bs;
       __threadfence();
-      is_last = atomicAdd(f.dot_count, 1u) == gridDim.x - 1;
+      is_last = atomicAdd(dot_count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (is_last) {
       __threadfence();
       double t = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += f.dot_part[b];
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += dot_part[b];
       t = block_sum(t, red);
       if (threadIdx.x == 0) {
-        *f.o.dot = t;
+        *at(f.o.dot) = t;
         if (f.o.ratio_out) {
           const bool good = t > 0.0 && isfinite(t);
-          *f.o.ratio_out = good ? *f.o.ratio_num / t : 0.0;
-          if (!good) *f.o.brk_flag = 1;
+          *at(f.o.ratio_out) = good ? *at(f.o.ratio_num) / t : 0.0;
+          if (!good) *at(f.o.brk_flag) = 1;
         }
-        *f.dot_count = 0u;
+        *dot_count = 0u;
       }
     }
   }
@@ -447,6 +596,68 @@ cudaError_t dispatch_T(MvpParams p, int T, const Plan& pl, cudaStream_t st) {
   return cudaErrorNotSupported;
 }
 
+template <int D, int MC>
+cudaError_t set_dirm_attr() {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mvp_dirm_kernel<D, MC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dirm_smem_bytes<D, MC>());
+  if (!e && dev < 128) done[dev] = true;
+  return e;
+}
+
+// Multi-column direct-form launch (or, with launch = false, only its
+// attribute), MC the smallest of 4, 8, 16 that holds m columns.
+template <int D>
+cudaError_t dirm_typed(const MvpParams& p, const float* Q, int64_t q_stride, int m, int T,
+                       int64_t slot0, const Plan& pl, cudaStream_t st, bool launch) {
+  const int bpc = NW / T;
+  dim3 grid((unsigned)std::max<int64_t>(1, (p.nblk - slot0 + bpc - 1) / bpc), (unsigned)pl.splits);
+  MvpParams pp = p;
+  pp.tiles_per_split = pl.tiles_per_split;
+  cudaError_t e;
+#define KRR_DIRM(MCV)                                                                       \
+  if ((e = set_dirm_attr<D, MCV>())) return e;                                             \
+  if (launch) {                                                                            \
+    mvp_dirm_kernel<D, MCV><<<grid, NT, dirm_smem_bytes<D, MCV>(), st>>>(pp, Q, q_stride, m, T, slot0); \
+    count_launch();                                                                        \
+  }                                                                                        \
+  return cudaGetLastError();
+  if (m <= 4) { KRR_DIRM(4) }
+  if (m <= 8) { KRR_DIRM(8) }
+  KRR_DIRM(16)
+#undef KRR_DIRM
+}
+
+cudaError_t dirm_dispatch(const MvpParams& p, int d, const float* Q, int64_t q_stride, int m, int T,
+                          int64_t slot0, const Plan& pl, cudaStream_t st, bool launch) {
+  if (T < 1 || T > NW || NW % T) return cudaErrorNotSupported;
+  switch (d) {
+    case 1: return dirm_typed<1>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 2: return dirm_typed<2>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 3: return dirm_typed<3>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 4: return dirm_typed<4>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 5: return dirm_typed<5>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 6: return dirm_typed<6>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 7: return dirm_typed<7>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 8: return dirm_typed<8>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// Source splits of the multi-column kernels (one CTA per super-block): the
+// tensor-core kernel over the expanded-form super-blocks, the CUDA-core
+// kernel over the direct-form ones, each planned for its own grid.
+Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+  return make_plan(Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+}
+Plan multi_plan_dir(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+  return make_plan((Tp.nsb - Tp.h_sb_nexp) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+}
+
 }  // namespace
 
 int mvp_targets_per_thread(int d, int64_t N) {
@@ -465,10 +676,10 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
   if ((e = c.ws.get("mvp.part", sizeof(double) * pl.splits * (size_t)Tp.Npad, &v))) return e;
   if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &v))) return e;
-  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &v))) return e;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &v))) return e;
   const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
-  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &v))) return e;
-  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned), st))) return e;
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
+  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
   switch (Tp.d) {
     case 1: return attrs_T<1>(Tp.T);
     case 2: return attrs_T<2>(Tp.T);
@@ -500,7 +711,6 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   p.s = Sp.scale;
   p.active = o.active;
   p.part_stride = Tp.Npad;
-  p.direct_only = 0;
   p.err = c.d_err;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
   const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots);
@@ -510,8 +720,8 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
   if ((e = c.ws.get("mvp.part", sizeof(double) * pl.splits * (size_t)Tp.Npad, &part))) return e;
   if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &fac))) return e;
-  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
-  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &dcnt))) return e;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.part = (double*)part;
   p.fac = (float*)fac;
   cudaEvent_t pev1 = nullptr;
@@ -562,93 +772,78 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
 cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m,
                               krr_precision prec, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
+  if (m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
-  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+  const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
   void* v;
-  if ((e = c.ws.get("mvp.partm", sizeof(double) * pl.splits * (size_t)m * Tp.Npad, &v))) return e;
-  return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pl.splits,
-                         pl.tiles_per_split, nullptr, nullptr, nullptr, st, true);
+  if ((e = c.ws.get("mvp.partm", sizeof(double) * pt.splits * (size_t)m * Tp.Npad, &v))) return e;
+  if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)m * Tp.Npad, &v))) return e;
+  MvpParams p{};
+  p.nblk = Tp.nsb;
+  if ((e = dirm_dispatch(p, Tp.d, nullptr, 0, m, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+  return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
+                         pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
 }
 
 cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* Q, int m,
                              const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                              cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
-  if (Tp.d < 1 || Tp.d > 8 || m < 1 || m > 16) return cudaErrorNotSupported;
+  if (Tp.d < 1 || Tp.d > 8 || m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
   MvpParams p{};
   p.xt = Tp.xs;
   p.Nt = Tp.N;
   p.Nt_pad = Tp.Npad;
-  p.tctr = Tp.ctr;
-  p.torder = Tp.order;
-  p.tn_exp = Tp.n_exp;
-  p.nblk = Tp.nblk;
+  // super-blocks of SB targets, expanded-form first
+  p.tctr = Tp.sb_ctr;
+  p.torder = Tp.sb_order;
+  p.tn_exp = Tp.sb_nexp;
+  p.nblk = Tp.nsb;
   p.xs = Sp.xs;
   p.ntiles = (int)(Sp.Npad / TS);
   p.err = c.d_err;
   p.s = Sp.scale;
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
-  p.direct_only = 1;
-  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots);
+  const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
-  void *part, *fac, *dpart, *dcnt;
+  void *part, *partd, *fac, *dpart, *dcnt;
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
-  if ((e = c.ws.get("mvp.partm", sizeof(double) * pl.splits * (size_t)m * Tp.Npad, &part))) return e;
+  if ((e = c.ws.get("mvp.partm", sizeof(double) * pt.splits * (size_t)m * Tp.Npad, &part))) return e;
+  if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)m * Tp.Npad, &partd))) return e;
   if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &fac))) return e;
-  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
-  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned), &dcnt))) return e;
-  p.part = (double*)part;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.fac = (float*)fac;
-  // expanded-form blocks: all columns on the tensor cores
-  if ((e = mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pl.splits,
-                           pl.tiles_per_split, p.part, p.fac, o.active, st)))
+  // expanded-form super-blocks: all columns on the tensor cores
+  if (Tp.h_sb_nexp > 0 &&
+      (e = mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
+                           pt.tiles_per_split, (double*)part, p.fac, o.active, st)))
     return e;
-  // direct-form blocks: float32 CUDA-core kernel, one column at a time
-  for (int col = 0; col < m; ++col) {
-    MvpParams pc = p;
-    pc.q = Q + (size_t)col * Sp.Npad;
-    pc.part = p.part + (size_t)col * Tp.Npad;
-    switch (Tp.d) {
-      case 1: e = dispatch_T<1>(pc, Tp.T, pl, st); break;
-      case 2: e = dispatch_T<2>(pc, Tp.T, pl, st); break;
-      case 3: e = dispatch_T<3>(pc, Tp.T, pl, st); break;
-      case 4: e = dispatch_T<4>(pc, Tp.T, pl, st); break;
-      case 5: e = dispatch_T<5>(pc, Tp.T, pl, st); break;
-      case 6: e = dispatch_T<6>(pc, Tp.T, pl, st); break;
-      case 7: e = dispatch_T<7>(pc, Tp.T, pl, st); break;
-      default: e = dispatch_T<8>(pc, Tp.T, pl, st); break;
-    }
-    if (e) return e;
+  // direct-form super-blocks: all columns in one CUDA-core launch
+  if (Tp.nsb > Tp.h_sb_nexp) {
+    p.part = (double*)partd;
+    if ((e = dirm_dispatch(p, Tp.d, Q, Sp.Npad, m, SB / 32, Tp.h_sb_nexp, pd, st, true))) return e;
   }
-  for (int col = 0; col < m; ++col) {
-    FinParams f{};
-    f.part = p.part + (size_t)col * Tp.Npad;
-    f.splits = pl.splits;
-    f.part_stride = (int64_t)m * Tp.Npad;
-    f.N = Tp.N;
-    f.Npad = Tp.Npad;
-    f.fac = p.fac;
-    f.qdiag = qdiag ? qdiag + (size_t)col * Tp.Npad : nullptr;
-    f.shift = shift;
-    f.o = o;
-    if (col > 0) {
-      f.o.dot = nullptr;
-      f.o.dotw = nullptr;
-      f.o.ratio_out = nullptr;
-    }
-    if (o.out_f) f.o.out_f = o.out_f + (size_t)col * Tp.Npad;
-    if (o.out_d) f.o.out_d = o.out_d + (size_t)col * Tp.Npad;
-    if (o.out_orig) f.o.out_orig = o.out_orig + (size_t)col * Tp.N;
-    if (o.u) f.o.u = o.u + (size_t)col * Tp.Npad;
-    f.dot_part = (double*)dpart;
-    f.dot_count = (unsigned*)dcnt;
-    mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
-    if ((e = cudaGetLastError())) return e;
-  }
-  return cudaSuccess;
+  FinParams f{};
+  f.part = (const double*)part;
+  f.splits = pt.splits;
+  f.part2 = (const double*)partd;
+  f.splits2 = pd.splits;
+  f.sb_flag = Tp.sb_flag;
+  f.part_stride = (int64_t)m * Tp.Npad;
+  f.N = Tp.N;
+  f.Npad = Tp.Npad;
+  f.fac = p.fac;
+  f.qdiag = qdiag;
+  f.shift = shift;
+  f.o = o;
+  f.dot_part = (double*)dpart;
+  f.dot_count = (unsigned*)dcnt;
+  mvp_finalize_kernel<<<dim3(fin_blocks, (unsigned)m), 256, 0, st>>>(f); count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace krr

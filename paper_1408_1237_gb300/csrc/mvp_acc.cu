@@ -14,7 +14,7 @@
 //   * 2^e by table-driven reduction e = n + k/64 + t, |t| <= 1/128: 2^(k/64)
 //     from a 64-entry float-float table, 2^t = 1 + u with u from the Taylor
 //     series of exp(t ln 2) to degree 4 (remainder < 1e-13), u itself in
-//     float-float; the result is accurate to about 1e-12;
+//     float-float; the result is within about 3e-12 (relative);
 //   * q_j (the FP64 iterate) arrives as float hi + lo; each product q_j Phi_ij
 //     is split exactly (FMA error term) and summed with TwoSum.
 // A (warp, source tile) pair whose bounding boxes are farther apart than
@@ -50,8 +50,13 @@ struct AccParams {
   const float* ql;   // source weights lo
   const float* tbox; // source tile boxes
   int ntiles, tiles_per_split;
-  double* part;      // [splits][Npad]
+  double* part;      // [columns][splits][Npad]
+  int splits;
   int* err;
+  // columns (blockIdx.z): qh, ql Npad apart; column c runs when its active
+  // word (state_stride bytes after column c-1's) is nonzero
+  const int* active;
+  size_t state_stride;
   AccConst k;
 };
 
@@ -101,10 +106,14 @@ __device__ __forceinline__ void acc_pair(const float (&xi)[D], const float* __re
   const int m = __float_as_int(tm) - 0x4B400000;
   const int n = m >> 6;                     // floor(m / 64)
   const int jt = m - (n << 6);              // 0..63
-  // 2^(r + el) = 1 + uh + ul
+  // 2^(r + el) = 1 + uh + ul: the linear term ln2 (r + el) in float-float,
+  // the series tail c2 r^2 + c3 r^3 + c4 r^4 at r plus its first-order
+  // change (2 c2 + 3 c3 r) r el (el is up to ~2e-6: leaving the change out
+  // costs ~4e-9 relative, with it the result is within ~3e-12)
   const float uh = k.c1h * r;
   const float ul = fmaf(k.c1h, r, -uh) + fmaf(k.c1l, r, k.c1h * el) +
-                   (r * r) * fmaf(fmaf(k.c4, r, k.c3), r, k.c2);
+                   fmaf(r * r, fmaf(fmaf(k.c4, r, k.c3), r, k.c2),
+                        (fmaf(3.f * k.c3, r, 2.f * k.c2) * r) * el);
   // (Th + Tl)(1 + uh + ul) = H + L2
   const float Th = tab_h[jt], Tl = tab_l[jt];
   const float P = Th * uh;
@@ -131,6 +140,10 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
   __shared__ volatile int abort_flag;
   __shared__ float tab_h[64], tab_l[64];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int col = blockIdx.z;
+  if (p.active && *(const int*)((const char*)p.active + col * p.state_stride) == 0) return;
+  const float* qhc = p.qh + (int64_t)col * p.Npad;
+  const float* qlc = p.ql + (int64_t)col * p.Npad;
   if (tid < 64) {
     tab_h[tid] = p.k.th[tid];
     tab_l[tid] = p.k.tl[tid];
@@ -175,8 +188,8 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
     float* dst = smem + stage * kStageFloats;
     mbar_arrive_expect_tx(&bars[stage], kStageFloats * 4);
     bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
-    bulk_g2s(dst + D * TS, p.qh + tile * (int64_t)TS, TS * 4, &bars[stage]);
-    bulk_g2s(dst + (D + 1) * TS, p.ql + tile * (int64_t)TS, TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS, qhc + tile * (int64_t)TS, TS * 4, &bars[stage]);
+    bulk_g2s(dst + (D + 1) * TS, qlc + tile * (int64_t)TS, TS * 4, &bars[stage]);
   };
   if (tid == 0) {
     abort_flag = 0;
@@ -244,7 +257,7 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
     __syncthreads();
     return;
   }
-  double* part = p.part + (int64_t)blockIdx.y * p.Npad;
+  double* part = p.part + ((int64_t)col * p.splits + blockIdx.y) * p.Npad;
 #pragma unroll
   for (int u = 0; u < TA; ++u) {
     const int64_t i = t0 + lane + 32 * u;
@@ -264,37 +277,44 @@ struct AccFin {
   double* dot;
   double* dot_part;
   unsigned* dot_count;
+  const int* active;
+  size_t state_stride;
 };
 
 __global__ void __launch_bounds__(256) acc_finalize_kernel(const AccFin f) {
   __shared__ double red[8];
   __shared__ bool is_last;
+  const int col = blockIdx.y;
+  if (f.active && *(const int*)((const char*)f.active + col * f.state_stride) == 0) return;
+  const int64_t cv = (int64_t)col * f.Npad;
+  const double* part = f.part + cv * f.splits;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double o = 0.0;
   if (i < f.N) {
     double y = 0.0;
-    for (int s = 0; s < f.splits; ++s) y += f.part[(int64_t)s * f.Npad + i];
-    y += f.shift * ((double)f.qh[i] + (double)f.ql[i]);
+    for (int s = 0; s < f.splits; ++s) y += part[(int64_t)s * f.Npad + i];
+    y += f.shift * ((double)f.qh[cv + i] + (double)f.ql[cv + i]);
     o = f.cy * y;
-    if (f.u) o += f.cu * (double)f.u[i];
+    if (f.u) o += f.cu * (double)f.u[cv + i];
   }
-  if (i < f.Npad) f.out[i] = o;
+  if (i < f.Npad) f.out[cv + i] = o;
   if (f.dot) {
+    double* dot_part = f.dot_part + (int64_t)col * gridDim.x;
     const double bs = block_sum(o * o, red);
     if (threadIdx.x == 0) {
-      f.dot_part[blockIdx.x] = bs;
+      dot_part[blockIdx.x] = bs;
       __threadfence();
-      is_last = atomicAdd(f.dot_count, 1u) == gridDim.x - 1;
+      is_last = atomicAdd(f.dot_count + col, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (is_last) {
       __threadfence();
       double t = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += f.dot_part[b];
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += dot_part[b];
       t = block_sum(t, red);
       if (threadIdx.x == 0) {
-        *f.dot = t;
-        *f.dot_count = 0u;
+        *(double*)((char*)f.dot + col * f.state_stride) = t;
+        f.dot_count[col] = 0u;
       }
     }
   }
@@ -332,11 +352,11 @@ cudaError_t set_acc_attr() {
 }
 
 template <int D, int TA>
-cudaError_t launch_acc(const AccParams& p, int splits, cudaStream_t st) {
+cudaError_t launch_acc(const AccParams& p, int splits, int ncols, cudaStream_t st) {
   const size_t shm = sizeof(float) * RS * (D + 2) * TS;
   cudaError_t e = set_acc_attr<D, TA>();
   if (e) return e;
-  dim3 grid((unsigned)((p.N + NT * TA - 1) / (NT * TA)), (unsigned)splits);
+  dim3 grid((unsigned)((p.N + NT * TA - 1) / (NT * TA)), (unsigned)splits, (unsigned)ncols);
   mvp_acc_kernel<D, TA><<<grid, NT, shm, st>>>(p); count_launch();
   return cudaGetLastError();
 }
@@ -361,17 +381,18 @@ AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots) {
 
 }  // namespace
 
-cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st) {
+cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int ncols) {
   if (P.N == 0) return cudaSuccess;
+  if (ncols < 1 || ncols > MAX_COLS) return cudaErrorNotSupported;
   const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots);
   void* v;
   cudaError_t e;
-  if ((e = c.ws.get("acc.part", sizeof(double) * pl.splits * (size_t)P.Npad, &v))) return e;
+  if ((e = c.ws.get("acc.part", sizeof(double) * ncols * pl.splits * (size_t)P.Npad, &v))) return e;
   const unsigned fin_blocks = (unsigned)((P.Npad + 255) / 256);
-  if ((e = c.ws.get("acc.dotpart", sizeof(double) * fin_blocks, &v))) return e;
+  if ((e = c.ws.get("acc.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &v))) return e;
   const bool fresh = c.ws.slots.find("acc.dotcnt") == c.ws.slots.end();
-  if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned), &v))) return e;
-  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned), st))) return e;
+  if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
+  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
   switch (P.d) {
     case 1: return set_acc_attr<1, ACC_TA>();
     case 2: return set_acc_attr<2, ACC_TA>();
@@ -387,9 +408,10 @@ cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st) {
 
 cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const float* ql,
                            float shift, double cu, const float* u, double cy, double* out,
-                           double* dot, cudaStream_t st) {
+                           double* dot, cudaStream_t st, const AccCols& cols) {
   if (P.N == 0) return cudaSuccess;
-  cudaError_t e = mvp_acc_reserve(c, P, st);
+  const int ncols = cols.n;
+  cudaError_t e = mvp_acc_reserve(c, P, st, ncols);
   if (e) return e;
   AccParams p{};
   p.xs = P.xs;
@@ -406,21 +428,24 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   p.k.s2l = (float)(P.s2 - (double)p.k.s2h);
   const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots);
   p.tiles_per_split = pl.tiles_per_split;
+  p.splits = pl.splits;
+  p.active = cols.active;
+  p.state_stride = cols.state_stride;
   void *part, *dpart, *dcnt;
   const unsigned fin_blocks = (unsigned)((P.Npad + 255) / 256);
-  if ((e = c.ws.get("acc.part", sizeof(double) * pl.splits * (size_t)P.Npad, &part))) return e;
-  if ((e = c.ws.get("acc.dotpart", sizeof(double) * fin_blocks, &dpart))) return e;
-  if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned), &dcnt))) return e;
+  if ((e = c.ws.get("acc.part", sizeof(double) * ncols * pl.splits * (size_t)P.Npad, &part))) return e;
+  if ((e = c.ws.get("acc.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
+  if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.part = (double*)part;
   switch (P.d) {
-    case 1: e = launch_acc<1, ACC_TA>(p, pl.splits, st); break;
-    case 2: e = launch_acc<2, ACC_TA>(p, pl.splits, st); break;
-    case 3: e = launch_acc<3, ACC_TA>(p, pl.splits, st); break;
-    case 4: e = launch_acc<4, ACC_TA>(p, pl.splits, st); break;
-    case 5: e = launch_acc<5, ACC_TA>(p, pl.splits, st); break;
-    case 6: e = launch_acc<6, ACC_TA>(p, pl.splits, st); break;
-    case 7: e = launch_acc<7, ACC_TA>(p, pl.splits, st); break;
-    case 8: e = launch_acc<8, ACC_TA>(p, pl.splits, st); break;
+    case 1: e = launch_acc<1, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 2: e = launch_acc<2, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 3: e = launch_acc<3, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 4: e = launch_acc<4, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 5: e = launch_acc<5, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 6: e = launch_acc<6, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 7: e = launch_acc<7, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 8: e = launch_acc<8, ACC_TA>(p, pl.splits, ncols, st); break;
     default: return cudaErrorNotSupported;
   }
   if (e) return e;
@@ -439,7 +464,9 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   f.dot = dot;
   f.dot_part = (double*)dpart;
   f.dot_count = (unsigned*)dcnt;
-  acc_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
+  f.active = cols.active;
+  f.state_stride = cols.state_stride;
+  acc_finalize_kernel<<<dim3(fin_blocks, (unsigned)ncols), 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
 }
 

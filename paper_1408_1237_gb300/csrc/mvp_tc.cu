@@ -3,7 +3,7 @@
 //
 //   Y[i, c] = sum_j 2^(-s^2 |x_i - x_j|^2) Q[j, c]        (Eqs. 1-2)
 //
-// over the expanded-form warp blocks of prep.cu (compact target blocks with
+// over the expanded-form super-blocks of prep.cu (compact blocks of 256 targets with
 // centre c, x^ = s (x - c), |x^_i|^2 <= EXPANDED_R2), written as two dense
 // contractions on the tensor cores (mma.sync m16n8k16, f16 or bf16 inputs,
 // f32 accumulation) around one special-function step:
@@ -47,7 +47,7 @@ struct TcParams {
   const float* tctr;  // warp-block centres
   const int* torder;
   const int* tn_exp;
-  int64_t nblk;
+  int64_t nblk;       // CTAs: the expanded-form super-blocks
   int WB;             // warp-block size (targets)
   const float* xs;    // sources (tile-blocked SoA, raw)
   const float* Q;     // sorted source weights, m columns of stride Ns_pad
@@ -468,16 +468,16 @@ cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, cons
                             bool split, bool bf, int splits, int tiles_per_split, double* part,
                             float* fac, const int* active, cudaStream_t st, bool dry) {
   if (m < 1 || m > 16) return cudaErrorNotSupported;
-  if ((32 * T.T) % 32 != 0 || 32 * T.T < 32) return cudaErrorNotSupported;
   TcParams p{};
   p.xt = T.xs;
   p.Nt = T.N;
   p.Nt_pad = T.Npad;
-  p.tctr = T.ctr;
-  p.torder = T.order;
-  p.tn_exp = T.n_exp;
-  p.nblk = T.nblk;
-  p.WB = 32 * T.T;
+  // one CTA per expanded-form super-block
+  p.tctr = T.sb_ctr;
+  p.torder = T.sb_order;
+  p.tn_exp = T.sb_nexp;
+  p.nblk = std::max<int64_t>(1, T.h_sb_nexp);
+  p.WB = SB;
   p.xs = S.xs;
   p.Q = Q;
   p.Ns_pad = S.Npad;

@@ -68,11 +68,15 @@ constexpr Region kRegions[] = {
     {"na.nexp", sizeof(int)},
     {"sort.flag", sizeof(int) * NBLK},
     {"na.tbox", sizeof(float) * 2 * NA_MAX_D * NTILE},
+    {"na.sbctr", sizeof(float) * (NA_MAX_N / SB) * NA_MAX_D},
+    {"na.sborder", sizeof(int) * (NA_MAX_N / SB)},
+    {"na.sbnexp", sizeof(int)},
+    {"na.sbflag", sizeof(int) * (NA_MAX_N / SB)},
     {"mvp.qs", sizeof(float) * NPAD * NA_MAX_M},
     {"mvp.part", sizeof(double) * MAX_SPLITS * NPAD},
     {"mvp.fac", sizeof(float) * NPAD},
-    {"mvp.dotpart", sizeof(double) * (NPAD / 256)},
-    {"mvp.dotcnt", sizeof(unsigned)},
+    {"mvp.dotpart", sizeof(double) * MAX_COLS * (NPAD / 256)},
+    {"mvp.dotcnt", sizeof(unsigned) * MAX_COLS},
     {"na.err", sizeof(int)},
 };
 
@@ -89,7 +93,7 @@ constexpr size_t total_bytes() {
 
 #define KRR_NOALLOC_SCRATCH_BYTES (krr::total_bytes())
 
-// The scratch array: 10,405,376 bytes (about 10 MB).  Host code must not take its address
+// The scratch array: 10,415,616 bytes (about 10 MB).  Host code must not take its address
 // directly: use the pointer from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KRR_NOALLOC_SCRATCH_BYTES];
 
@@ -179,7 +183,7 @@ extern "C" krr_status krr_kernel_mvp_noalloc(const float* X, int64_t N, int d, f
   const size_t nslots = c.ws.slots.size();
   // counters that must start at zero: the error word and the dot ticket
   cudaError_t e = cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
-  if (!e) e = cudaMemsetAsync(c.ws.slots["mvp.dotcnt"].p, 0, sizeof(unsigned), st);
+  if (!e) e = cudaMemsetAsync(c.ws.slots["mvp.dotcnt"].p, 0, sizeof(unsigned) * MAX_COLS, st);
   if (e) return cuda_error(c, e, "krr_kernel_mvp_noalloc");
   PointsDev P;
   if ((e = prepare_points(c, X, N, d, sigma, "na", P, st))) return cuda_error(c, e, "krr_kernel_mvp_noalloc");

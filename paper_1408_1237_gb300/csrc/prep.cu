@@ -364,12 +364,34 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   blkinfo_kernel<<<blocks_for(P.nblk, 8), 256, 0, st>>>(P.xs, N, d, P.T, P.scale, P.nblk, P.ctr,
                                                        (int*)flag); count_launch();
   order_kernel<<<1, SCAN_THREADS, 0, st>>>((const int*)flag, P.nblk, P.order, P.n_exp); count_launch();
+  // super-blocks of SB targets (nsb <= nblk: the flag scratch fits)
+  P.nsb = (N + SB - 1) / SB;
+  if ((e = c.ws.get(t + ".sbctr", sizeof(float) * P.nsb * d, &ctr))) return e;
+  if ((e = c.ws.get(t + ".sborder", sizeof(int) * P.nsb, &order))) return e;
+  if ((e = c.ws.get(t + ".sbnexp", sizeof(int), &nexp))) return e;
+  if ((e = c.ws.get(t + ".sbflag", sizeof(int) * P.nsb, &flag))) return e;
+  P.sb_ctr = (float*)ctr;
+  P.sb_order = (int*)order;
+  P.sb_nexp = (int*)nexp;
+  P.sb_flag = (int*)flag;
+  blkinfo_kernel<<<blocks_for(P.nsb, 8), 256, 0, st>>>(P.xs, N, d, SB / 32, P.scale, P.nsb, P.sb_ctr,
+                                                       P.sb_flag); count_launch();
+  order_kernel<<<1, SCAN_THREADS, 0, st>>>(P.sb_flag, P.nsb, P.sb_order, P.sb_nexp); count_launch();
   const int64_t ntiles = P.Npad / TS;
   void* tbox;
   if ((e = c.ws.get(t + ".tbox", sizeof(float) * 2 * d * ntiles, &tbox))) return e;
   P.tbox = (float*)tbox;
   tilebox_kernel<<<blocks_for(ntiles, 8), 256, 0, st>>>(P.xs, ntiles, d, P.tbox); count_launch();
-  return cudaGetLastError();
+  if ((e = cudaGetLastError())) return e;
+  // the block counts size the product grids: read them once (a short wait
+  // for the preparation; never inside a graph capture)
+  int counts[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(&counts[0], P.n_exp, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(&counts[1], P.sb_nexp, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  P.h_nexp = counts[0];
+  P.h_sb_nexp = counts[1];
+  return cudaSuccess;
 }
 
 }  // namespace krr

@@ -18,3 +18,11 @@ def oracle_mod():
     import oracle
     oracle.build_oracle()
     return oracle
+
+
+def f32(v):
+    """The value a float scalar takes at the C boundary (sigma, gamma and the
+    shift are float there): the oracle is given exactly the operator the
+    library receives."""
+    import numpy as np
+    return float(np.float32(v))

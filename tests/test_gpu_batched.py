@@ -10,6 +10,8 @@ import pytest
 
 from paper_1408_1237_gb300 import inputs
 
+from conftest import f32
+
 pytestmark = pytest.mark.gpu
 
 
@@ -45,7 +47,7 @@ def test_batched_uneven_problems(K, oracle_mod):
             i = infos[k * 3 + r]
             assert i["status"] == K.KRR_OK, (k, r, i)
             b = pr["B"][:, r].astype(np.float64)
-            Kx = oracle_mod.mvp(pr["X"].astype(np.float64), Xs[r], bp["sigma"], pr["gamma"])
+            Kx = oracle_mod.mvp(pr["X"].astype(np.float64), Xs[r], f32(bp["sigma"]), f32(pr["gamma"]))
             rel = np.linalg.norm(b - Kx) / np.linalg.norm(b)
             assert rel <= 1e-6, (k, r, rel, i)
             assert abs(i["relres_true"] - rel) <= 2e-8 + 0.02 * rel

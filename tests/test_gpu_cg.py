@@ -9,6 +9,8 @@ import pytest
 
 from paper_1408_1237_gb300 import inputs
 
+from conftest import f32
+
 pytestmark = pytest.mark.gpu
 
 
@@ -33,7 +35,7 @@ def test_cg_small_problem(K, oracle_mod):
     x, info = K.krr_cg_solve(_dev(p["X"]), _dev(p["b"]), p["sigma"], p["gamma"], tol=1e-6,
                              maxit=5000)
     X64, b64 = p["X"].astype(np.float64), p["b"].astype(np.float64)
-    Kd = oracle_mod.regularised_matrix(X64, p["sigma"], p["gamma"])
+    Kd = oracle_mod.regularised_matrix(X64, f32(p["sigma"]), f32(p["gamma"]))
     rel = np.linalg.norm(b64 - Kd @ x.cpu().numpy()) / np.linalg.norm(b64)
     assert info["status"] == K.KRR_OK, info
     assert rel <= 1e-6, (rel, info)
@@ -48,7 +50,7 @@ def test_cg_shifted_operator_and_initial_guess(K, oracle_mod):
     p = inputs.small_problem(seed=1, N=1200)
     shift = p["gamma"] + p["delta"]
     X64, b64 = p["X"].astype(np.float64), p["b"].astype(np.float64)
-    M = oracle_mod.regularised_matrix(X64, p["sigma"], shift)
+    M = oracle_mod.regularised_matrix(X64, f32(p["sigma"]), f32(shift))
     x_star = oracle_mod.direct_solve(M, b64)
     x0 = _dev((x_star + 1e-3 * np.random.default_rng(2).standard_normal(1200)).astype(np.float64))
     x, info = K.krr_cg_solve(_dev(p["X"]), _dev(p["b"]), p["sigma"], shift, tol=1e-6,

@@ -11,6 +11,8 @@ import pytest
 
 from paper_1408_1237_gb300 import inputs
 
+from conftest import f32
+
 pytestmark = pytest.mark.gpu
 
 
@@ -32,7 +34,7 @@ def _dev(a):
 
 def _oracle_relres(oracle_mod, X, b, x, sigma, gamma):
     X64, b64, x64 = X.astype(np.float64), b.astype(np.float64), x.astype(np.float64)
-    Kx = oracle_mod.mvp(X64, x64, sigma, gamma)
+    Kx = oracle_mod.mvp(X64, x64, f32(sigma), f32(gamma))
     return np.linalg.norm(b64 - Kx) / np.linalg.norm(b64)
 
 
@@ -44,7 +46,7 @@ def test_fgmres_small_problem_vs_cholesky(K, oracle_mod, graph):
     x, info = K.krr_fgmres_solve(_dev(p["X"]), _dev(p["b"]), p["sigma"], p["gamma"], opts=opts)
     x = x.cpu().numpy()
     X64, b64 = p["X"].astype(np.float64), p["b"].astype(np.float64)
-    Kd = oracle_mod.regularised_matrix(X64, p["sigma"], p["gamma"])
+    Kd = oracle_mod.regularised_matrix(X64, f32(p["sigma"]), f32(p["gamma"]))
     rel = np.linalg.norm(b64 - Kd @ x.astype(np.float64)) / np.linalg.norm(b64)
     assert info[0]["status"] == K.KRR_OK, info
     assert rel <= p["tol"], (rel, info)

@@ -11,6 +11,8 @@ import pytest
 
 from paper_1408_1237_gb300 import inputs
 
+from conftest import f32
+
 pytestmark = pytest.mark.gpu
 
 
@@ -40,7 +42,7 @@ def test_mll_grad_matches_oracle_estimator(K, oracle_mod, N, d, P):
     Zp = oracle_mod.rademacher_probes(p["seed"], N, P)
     os_, og, oX = oracle_mod.mll_grad_hutchinson(p["X"].astype(np.float64),
                                                  p["y"].astype(np.float64),
-                                                 p["sigma"], p["gamma"], Zp)
+                                                 f32(p["sigma"]), f32(p["gamma"]), Zp)
     assert gs == pytest.approx(os_, rel=1e-4, abs=1e-6 * abs(os_) + 1e-8)
     assert gg == pytest.approx(og, rel=1e-4, abs=1e-8)
     gX = gX.cpu().numpy()

@@ -11,6 +11,8 @@ import pytest
 
 from paper_1408_1237_gb300 import inputs
 
+from conftest import f32
+
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
@@ -35,6 +37,7 @@ def _dev(a):
 def scaled_error(oracle_mod, X, q, y, sigma, gamma, rows=None):
     X64 = X.astype(np.float64)
     q64 = q.astype(np.float64)
+    sigma, gamma = f32(sigma), f32(gamma)
     ref = oracle_mod.mvp(X64, q64, sigma, gamma, rows=rows)
     scale = oracle_mod.mvp(X64, np.abs(q64), sigma, gamma, rows=rows)
     yy = y if rows is None else y[rows]
@@ -187,3 +190,18 @@ def test_mvp_reduced_precision_error(K, oracle_mod, prec, bound):
     print(f"{prec} max scaled error {err:.2e}")
     assert err <= bound
     assert err > 1e-6  # it really ran in reduced precision
+
+
+@pytest.mark.parametrize("m,d,sigma,normal", [(16, 8, 1.0, True), (7, 3, 0.01, False),
+                                              (3, 2, 0.004, False), (12, 5, 0.05, False)])
+def test_mvp_multi_rhs_direct_form_blocks(K, oracle_mod, m, d, sigma, normal):
+    # clouds whose target blocks are mostly too wide for the expanded form:
+    # the multi-column CUDA-core kernel (one exponential per pair, shared by
+    # all columns) carries them, the tensor cores the compact rest
+    rng = np.random.default_rng(200 + m + d)
+    N = 5000
+    X = (rng.standard_normal((N, d)) if normal else rng.random((N, d))).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    Y = K.krr_kernel_mvp(_dev(X), _dev(Q), sigma, 1e-2).cpu().numpy()
+    for c in range(m):
+        assert scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-2) <= TOL_FP32, c
