@@ -45,8 +45,16 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libkrr", choices=["libkrr", "reference"])
-    ap.add_argument("--solve-n", type=int, default=1 << 16,
-                    help="points of the mixture-cloud FGMRES solve (0 skips it)")
+    ap.add_argument("--solve-n", type=int, default=1 << 15,
+                    help="points of the mixture-cloud FGMRES solves (0 skips them)")
+    ap.add_argument("--plain-cols", type=int, default=4,
+                    help="right-hand sides solved one at a time for the per-RHS plain FP32 time")
+    ap.add_argument("--batch-probs", type=int, default=4,
+                    help="problems of the batching-form subset (0 skips it)")
+    ap.add_argument("--batch-nmax", type=int, default=8192,
+                    help="largest problem of the batching-form subset")
+    ap.add_argument("--grad-n", type=int, default=1 << 16,
+                    help="points of the log-marginal-likelihood gradient (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -272,19 +280,19 @@ def run_libkrr(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     e2e_value = whole_job_rate(pairs, world, e2e_s)
 
-    # ---- FGMRES time to a 1e-6 relative residual
+    # ---- FGMRES time to a 1e-6 relative residual: the plain FP32 form next
+    # to the precision, block (many right-hand sides) and batching forms
     solve = {}
     sp = inputs.small_problem(seed=rank)
-    solve["small_2000pt_2d"] = solve_once(K, torch, sp, dev, stream, "fp32")
+    solve["small_2000pt_2d"] = {"fgmres": solve_once(K, torch, sp, dev, stream, "fp32"),
+                                "cg": cg_once(K, torch, sp, dev, stream)}
     if args.solve_n > 0:
-        mp = inputs.mixture_problem(seed=rank, N=args.solve_n)
-        forms = {}
-        for form in ("fp32", "bf16", "fp16"):
-            try:
-                forms[form] = solve_once(K, torch, mp, dev, stream, form)
-            except K.KrrError as e:
-                forms[form] = {"unavailable": str(e)}
-        solve[f"mixture_{args.solve_n}pt_2d"] = forms
+        solve[f"mixture_{args.solve_n}pt_2d"] = mixture_forms(K, torch, inputs, args, rank, dev, stream)
+    if args.batch_probs > 0:
+        solve["batching_d8"] = batching_form(K, torch, inputs, args, rank, dev, stream)
+    grad = None
+    if args.grad_n > 0:
+        grad = gradient_form(K, torch, inputs, args, rank, dev, stream)
 
     # ---- FP64 oracle on the host cores (rank 0, one GPU only)
     cpu = None
@@ -321,6 +329,7 @@ def run_libkrr(args):
             "clocks": clk,
             "mvp_m16": {"ms": m16_ms, "Gpair_rhs_per_s": pairs * 16 / (m16_ms / 1e3) / 1e9},
             "fgmres": solve,
+            "mll_grad": grad,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -362,6 +371,115 @@ def solve_once(K, torch, p, dev, stream, inner_prec):
             "outer": i["outer_iters"], "inner": i["inner_iters"], "cycles": i["cycles"],
             "status": K.status_string(i["status"]), "inner_prec": inner_prec,
             "N": int(p["X"].shape[0])}
+
+
+def _timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def _report(K, infos):
+    return {"relres_true_max": max(i["relres_true"] for i in infos),
+            "outer_max": max(i["outer_iters"] for i in infos),
+            "inner_max": max(i["inner_iters"] for i in infos),
+            "all_ok": all(i["status"] == K.KRR_OK for i in infos)}
+
+
+def cg_once(K, torch, p, dev, stream):
+    X = torch.from_numpy(p["X"]).to(dev)
+    b = torch.from_numpy(p["b"]).to(dev)
+    K.krr_cg_solve(X, b, p["sigma"], p["gamma"], tol=1e-6, maxit=1)  # workspace
+    (x, info), ms = _timed(torch, stream, lambda: K.krr_cg_solve(X, b, p["sigma"], p["gamma"],
+                                                                 tol=1e-6, maxit=20000))
+    return {"time_to_solution_ms": ms, "relres_true": info["relres_true"],
+            "iters": info["outer_iters"], "status": K.status_string(info["status"])}
+
+
+def mixture_forms(K, torch, inputs, args, rank, dev, stream):
+    """The mixture cloud (kernel sigma 0.03, gamma 1e-3, delta 0.03, inner tol
+    1e-2, at most 200 inner steps, restart 30) with 16 right-hand sides (the
+    smooth field and 15 N(0,1) columns): per-RHS time to 1e-6 of the plain
+    float32 form (single-column solves of the first plain-cols columns), of the
+    half-precision inner form, and of 16-column lockstep block solves."""
+    import numpy as np
+    mp = inputs.mixture_problem(seed=rank, N=args.solve_n)
+    rng = np.random.default_rng(100 + rank)
+    B = np.stack([mp["b"]] + [rng.standard_normal(args.solve_n).astype(np.float32) for _ in range(15)])
+    X = torch.from_numpy(mp["X"]).to(dev)
+    Bd = torch.from_numpy(B).to(dev)
+    out = {"N": args.solve_n, "rhs": 16}
+
+    def opts(prec):
+        return K.default_opts(delta=0.03, inner_tol=1e-2, inner_maxit=200, restart=30, inner_prec=prec)
+
+    K.krr_fgmres_solve(X, Bd[0].contiguous(), mp["sigma"], mp["gamma"],
+                       opts=K.default_opts(max_cycles=1, inner_maxit=1))  # workspace
+    for form, prec in (("plain_fp32", "fp32"), ("single_fp16_inner", "fp16")):
+        ms_all, infos = [], []
+        for c in range(min(args.plain_cols, 16)):
+            (x, info), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+                X, Bd[c].contiguous(), mp["sigma"], mp["gamma"], opts=opts(prec)))
+            ms_all.append(ms)
+            infos += info
+        out[form] = dict(per_rhs_ms=sum(ms_all) / len(ms_all), rhs_timed=len(ms_all), **_report(K, infos))
+    for form, prec in (("block16_fp32", "fp32"), ("block16_fp16_inner", "fp16")):
+        (x, infos), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+            X, Bd, mp["sigma"], mp["gamma"], opts=opts(prec)))
+        out[form] = dict(total_ms=ms, per_rhs_ms=ms / 16, **_report(K, infos))
+    plain = out["plain_fp32"]["per_rhs_ms"]
+    for form in ("single_fp16_inner", "block16_fp32", "block16_fp16_inner"):
+        out[form]["speedup_vs_plain_fp32"] = plain / out[form]["per_rhs_ms"]
+    return out
+
+
+def batching_form(K, torch, inputs, args, rank, dev, stream):
+    """A subset of the batching workload (d = 8, N(0, I) points, sigma 1,
+    gamma log-uniform in [1e-4, 1e-1], 16 N(0,1) right-hand sides each, N
+    log-uniform in [1024, batch-nmax]): all problems in one batched call vs
+    the plain float32 form (single-column solves of 2 columns per problem,
+    per-RHS mean)."""
+    import numpy as np
+    bp = inputs.batch_problems(seed=rank, nprob=args.batch_probs, d=8, m=16, n_lo=1024,
+                               n_hi=args.batch_nmax)
+    probs = []
+    for pr in bp["problems"]:
+        N = pr["X"].shape[0]
+        probs.append(dict(X=torch.from_numpy(pr["X"]).to(dev),
+                          B=torch.from_numpy(np.ascontiguousarray(pr["B"].T)).to(dev),
+                          gamma=pr["gamma"],
+                          Xsol=torch.empty((16, N), dtype=torch.float64, device=dev)))
+    infos, ms = _timed(torch, stream, lambda: K.krr_fgmres_solve_batched(probs, d=8, sigma=bp["sigma"],
+                                                                         m_rhs=16))
+    out = {"N": [int(p["X"].shape[0]) for p in probs], "rhs_per_problem": 16,
+           "batched": dict(total_ms=ms, per_rhs_ms=ms / (16 * len(probs)), **_report(K, infos))}
+    tot, n, pinfos = 0.0, 0, []
+    for pr in probs:
+        for c in range(2):
+            (x, info), ms1 = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+                pr["X"], pr["B"][c].contiguous(), bp["sigma"], pr["gamma"]))
+            tot += ms1
+            n += 1
+            pinfos += info
+    out["plain_fp32"] = dict(per_rhs_ms=tot / n, rhs_timed=n, **_report(K, pinfos))
+    out["batched"]["speedup_vs_plain_fp32"] = out["plain_fp32"]["per_rhs_ms"] / out["batched"]["per_rhs_ms"]
+    return out
+
+
+def gradient_form(K, torch, inputs, args, rank, dev, stream):
+    """Log-marginal-likelihood gradient (log sigma, log gamma, X) with 32
+    Rademacher probes on the uniform 4-D cloud (sigma 0.2, gamma 1e-2): the
+    33 right-hand sides solve as lockstep blocks, then the adjoint kernel."""
+    gp = inputs.gradient_problem(seed=rank, N=args.grad_n, d=4, probes=32)
+    X = torch.from_numpy(gp["X"]).to(dev)
+    y = torch.from_numpy(gp["y"]).to(dev)
+    (gs, gg, gX, infos), ms = _timed(torch, stream, lambda: K.krr_mll_grad(
+        X, y, gp["sigma"], gp["gamma"], n_probes=32, seed=gp["seed"]))
+    return dict(N=args.grad_n, d=4, probes=32, time_ms=ms, dlogsigma=gs, dloggamma=gg, **_report(K, infos))
 
 
 def main(argv=None):

@@ -73,12 +73,12 @@ __device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) - (b + bb);
 }
 
-// Accurate q * exp2(-s^2 |xi - xj|^2) added into (S, L).
+// exp2(-s^2 |xi - xj|^2) as the float-float H + L2 (xj: source coordinates,
+// TS apart).
 template <int D>
-__device__ __forceinline__ void acc_pair(const float (&xi)[D], const float* __restrict__ xj,
-                                         float qh, float ql, float& S, float& L,
-                                         const AccConst& k, const float* __restrict__ tab_h,
-                                         const float* __restrict__ tab_l) {
+__device__ __forceinline__ void acc_exp(const float (&xi)[D], const float* __restrict__ xj,
+                                        const AccConst& k, const float* __restrict__ tab_h,
+                                        const float* __restrict__ tab_l, float& Hout, float& Lout) {
   // r^2 = sum_k (dh + dl)^2 in float-float, the differences exact
   float dh, dl;
   two_diff(xi[0], xj[0], dh, dl);
@@ -121,15 +121,30 @@ __device__ __forceinline__ void acc_pair(const float (&xi)[D], const float* __re
   float H = Th + P;                          // |Th| >= 1 > |P|: Fast2Sum
   float L2 = ((Th - H) + P) + Pe + fmaf(Th, ul, Tl * (1.f + uh));
   const float sc = (n >= -126) ? __int_as_float((n + 127) << 23) : 0.f;
-  H *= sc;
-  L2 *= sc;
-  // (qh + ql)(H + L2)
+  Hout = H * sc;
+  Lout = L2 * sc;
+}
+
+// (qh + ql)(H + L2) added into (S, L): the product's high part exactly split
+// (FMA error term) and added with TwoSum.
+__device__ __forceinline__ void acc_fma(float qh, float ql, float H, float L2, float& S, float& L) {
   const float a = qh * H;
   const float ae = fmaf(qh, H, -a);
   float s, e;
   two_sum(S, a, s, e);
   S = s;
   L += e + ae + fmaf(qh, L2, ql * H);
+}
+
+// Accurate q * exp2(-s^2 |xi - xj|^2) added into (S, L).
+template <int D>
+__device__ __forceinline__ void acc_pair(const float (&xi)[D], const float* __restrict__ xj,
+                                         float qh, float ql, float& S, float& L,
+                                         const AccConst& k, const float* __restrict__ tab_h,
+                                         const float* __restrict__ tab_l) {
+  float H, L2;
+  acc_exp<D>(xi, xj, k, tab_h, tab_l, H, L2);
+  acc_fma(qh, ql, H, L2, S, L);
 }
 
 template <int D, int TA>
@@ -265,6 +280,156 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
   }
 }
 
+// Several columns at once: the float-float exponential of a pair is formed
+// once and applied to every active column (a near pair costs one
+// exponential plus about a dozen operations per column instead of both per
+// column).  One target per thread; per column a (S, L) accumulator pair;
+// coordinates, qh and ql of up to AM columns per source tile in shared memory
+// (RSM-stage TMA ring).  Columns that are inactive (or beyond m) are skipped
+// uniformly across the CTA.
+constexpr int AM = MAX_COLS;
+constexpr int RSM = 2;
+
+template <int D>
+constexpr size_t accm_smem_bytes() {
+  return sizeof(float) * RSM * (D + 2 * AM) * TS;
+}
+
+template <int D>
+__global__ void __launch_bounds__(NT, 2) mvp_accm_kernel(const AccParams p, int m) {
+  constexpr uint32_t kStage = (D + 2 * AM) * TS;
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t bars[RSM];
+  __shared__ volatile int abort_flag;
+  __shared__ float tab_h[64], tab_l[64];
+  __shared__ unsigned act_s;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 64) {
+    tab_h[tid] = p.k.th[tid];
+    tab_l[tid] = p.k.tl[tid];
+  }
+  if (tid == 0) {
+    unsigned a = 0u;
+    for (int c = 0; c < m; ++c)
+      if (!p.active || *(const int*)((const char*)p.active + c * p.state_stride) != 0) a |= 1u << c;
+    act_s = a;
+  }
+  __syncthreads();
+  const unsigned act = act_s;
+  if (act == 0u) return;
+  int na = 0;  // active columns, packed to the front of each stage
+  int cols[AM];
+#pragma unroll
+  for (int c = 0; c < AM; ++c) cols[c] = 0;
+  for (int c = 0; c < m; ++c)
+    if (act & (1u << c)) cols[na++] = c;
+
+  const int64_t i = (int64_t)blockIdx.x * NT + tid;
+  const bool valid = i < p.N;
+  const int64_t ii = valid ? i : (p.N - 1);
+  float xi[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) xi[k] = p.xs[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
+  float bc[D], bh[D];  // warp box: centre, half-width
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float lo = warp_min(xi[k]), hi = warp_max(xi[k]);
+    bc[k] = 0.5f * (lo + hi);
+    bh[k] = 0.5f * (hi - lo);
+  }
+
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+  float S[AM], L[AM];
+#pragma unroll
+  for (int c = 0; c < AM; ++c) S[c] = L[c] = 0.f;
+
+  auto issue = [&](int r) {
+    const int stage = r % RSM;
+    const int64_t tile = t_begin + r;
+    float* dst = smem + stage * kStage;
+    mbar_arrive_expect_tx(&bars[stage], (uint32_t)(D + 2 * na) * TS * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    for (int a = 0; a < na; ++a) {
+      const int64_t off = (int64_t)cols[a] * p.Npad + tile * (int64_t)TS;
+      bulk_g2s(dst + (D + a) * TS, p.qh + off, TS * 4, &bars[stage]);
+      bulk_g2s(dst + (D + AM + a) * TS, p.ql + off, TS * 4, &bars[stage]);
+    }
+  };
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < RSM; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RSM, nt); ++issued) issue(issued);
+  const float s2h = p.k.s2h;
+
+  for (int r = 0; r < nt; ++r) {
+    if (tid == 0 && r >= 1 && r - 1 + RSM < nt) {
+      fence_proxy_async_smem();
+      issue(r - 1 + RSM);
+      ++issued;
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[r % RSM], (r / RSM) & 1));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    } else {
+      const float* st = smem + (r % RSM) * kStage;
+      const float* sq = st + D * TS;
+      const float* sl = st + (D + AM) * TS;
+      const float* tb = p.tbox + (int64_t)(t_begin + r) * 2 * D;
+      float dist2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float g = fmaxf(0.f, fabsf(bc[k] - tb[k]) - bh[k] - tb[D + k]);
+        dist2 = fmaf(g, g, dist2);
+      }
+      if (s2h * dist2 <= FAR_E) {
+#pragma unroll 1
+        for (int j = 0; j < TS; ++j) {
+          float H, L2;
+          acc_exp<D>(xi, st + j, p.k, tab_h, tab_l, H, L2);
+#pragma unroll
+          for (int a = 0; a < AM; ++a)
+            if (a < na) acc_fma(sq[a * TS + j], sl[a * TS + j], H, L2, S[a], L[a]);
+        }
+      } else {
+#pragma unroll 1
+        for (int j = 0; j < TS; ++j) {
+          float r2 = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const float dd = xi[k] - st[k * TS + j];
+            r2 = fmaf(dd, dd, r2);
+          }
+          const float E = ex2(-s2h * r2);
+#pragma unroll
+          for (int a = 0; a < AM; ++a)
+            if (a < na) L[a] = fmaf(sq[a * TS + j], E, L[a]);
+        }
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RSM], (r / RSM) & 1);
+    __syncthreads();
+    return;
+  }
+  if (valid) {
+#pragma unroll
+    for (int a = 0; a < AM; ++a)
+      if (a < na)
+        p.part[((int64_t)cols[a] * p.splits + blockIdx.y) * p.Npad + i] = (double)S[a] + (double)L[a];
+  }
+}
+
 struct AccFin {
   const double* part;
   int splits;
@@ -363,13 +528,64 @@ cudaError_t launch_acc(const AccParams& p, int splits, int ncols, cudaStream_t s
 
 constexpr int ACC_TA = 2;
 
+template <int D>
+cudaError_t accm_attr_typed() {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mvp_accm_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)accm_smem_bytes<D>());
+  if (!e && dev < 128) done[dev] = true;
+  return e;
+}
+
+cudaError_t set_accm_attr(int d) {
+  switch (d) {
+    case 1: return accm_attr_typed<1>();
+    case 2: return accm_attr_typed<2>();
+    case 3: return accm_attr_typed<3>();
+    case 4: return accm_attr_typed<4>();
+    case 5: return accm_attr_typed<5>();
+    case 6: return accm_attr_typed<6>();
+    case 7: return accm_attr_typed<7>();
+    case 8: return accm_attr_typed<8>();
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <int D>
+cudaError_t launch_accm_typed(const AccParams& p, int splits, int ncols, cudaStream_t st) {
+  cudaError_t e = accm_attr_typed<D>();
+  if (e) return e;
+  dim3 grid((unsigned)((p.N + NT - 1) / NT), (unsigned)splits);
+  mvp_accm_kernel<D><<<grid, NT, accm_smem_bytes<D>(), st>>>(p, ncols); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accm(const AccParams& p, int d, int splits, int ncols, cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_accm_typed<1>(p, splits, ncols, st);
+    case 2: return launch_accm_typed<2>(p, splits, ncols, st);
+    case 3: return launch_accm_typed<3>(p, splits, ncols, st);
+    case 4: return launch_accm_typed<4>(p, splits, ncols, st);
+    case 5: return launch_accm_typed<5>(p, splits, ncols, st);
+    case 6: return launch_accm_typed<6>(p, splits, ncols, st);
+    case 7: return launch_accm_typed<7>(p, splits, ncols, st);
+    case 8: return launch_accm_typed<8>(p, splits, ncols, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 struct AccPlan {
   int splits, tiles_per_split;
 };
 
-AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots) {
+AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots, int ncols) {
   const int ntiles = (int)(P.Npad / TS);
-  const int64_t ctas = (P.N + NT * ACC_TA - 1) / (NT * ACC_TA);
+  // one target per thread in the multi-column kernel, ACC_TA otherwise
+  const int ta = ncols > 1 ? 1 : ACC_TA;
+  const int64_t ctas = (P.N + NT * ta - 1) / (NT * ta);
   const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   // fill the GPU about four times over, never below one tile per split
   int splits = (int)std::min<int64_t>(ntiles, std::max<int64_t>(1, (4LL * slots + ctas - 1) / ctas));
@@ -384,7 +600,7 @@ AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots) {
 cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int ncols) {
   if (P.N == 0) return cudaSuccess;
   if (ncols < 1 || ncols > MAX_COLS) return cudaErrorNotSupported;
-  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots);
+  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols);
   void* v;
   cudaError_t e;
   if ((e = c.ws.get("acc.part", sizeof(double) * ncols * pl.splits * (size_t)P.Npad, &v))) return e;
@@ -393,6 +609,7 @@ cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int nco
   const bool fresh = c.ws.slots.find("acc.dotcnt") == c.ws.slots.end();
   if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
   if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
+  if (ncols > 1) return set_accm_attr(P.d);
   switch (P.d) {
     case 1: return set_acc_attr<1, ACC_TA>();
     case 2: return set_acc_attr<2, ACC_TA>();
@@ -426,7 +643,7 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   // s^2 = log2(e) / (2 sigma^2) in float-float from the double value
   p.k.s2h = (float)P.s2;
   p.k.s2l = (float)(P.s2 - (double)p.k.s2h);
-  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots);
+  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols);
   p.tiles_per_split = pl.tiles_per_split;
   p.splits = pl.splits;
   p.active = cols.active;
@@ -437,7 +654,9 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   if ((e = c.ws.get("acc.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
   if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.part = (double*)part;
-  switch (P.d) {
+  if (ncols > 1) {
+    e = launch_accm(p, P.d, pl.splits, ncols, st);
+  } else switch (P.d) {
     case 1: e = launch_acc<1, ACC_TA>(p, pl.splits, ncols, st); break;
     case 2: e = launch_acc<2, ACC_TA>(p, pl.splits, ncols, st); break;
     case 3: e = launch_acc<3, ACC_TA>(p, pl.splits, ncols, st); break;
