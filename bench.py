@@ -162,8 +162,9 @@ def cpu_oracle_rate(X, q, sigma, gamma, rows):
 
 
 def run_reference(args):
-    rank, world, _ = dist_setup(args.gpus)
-    if rank != 0:
+    # host-only: rank 0 times the oracle, the other ranks exit without work
+    # (no process group is needed)
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
     from paper_1408_1237_gb300 import inputs
     p = inputs.mvp_problem(seed=0, N=MVP_N, d=MVP_D)
