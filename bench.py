@@ -34,8 +34,8 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 # DRAM bytes (read + write) of one product-kernel launch on the 2^20-point
 # workload, from one ncu capture (profiles/mvp_f32_kernel_cube1M_d3.md); valid
 # only for the kernel source it was taken on.
-TRAFFIC = {"source": "paper_1408_1237_gb300/csrc/mvp.cu", "sha1": "c6b59369cc94b9a6bbcad94ae2afbf5950649c4c",
-           "bytes": 23.76e6 + 84.93e6}
+TRAFFIC = {"source": "paper_1408_1237_gb300/csrc/mvp.cu", "sha1": "9775246cbc799cc4467e0840befecdb000cb45d1",
+           "bytes": 22374656 + 83717888}
 MVP_N, MVP_D = 1 << 20, 3
 
 
