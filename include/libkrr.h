@@ -123,10 +123,14 @@ void krr_fgmres_default_opts(krr_fgmres_opts* opts);
  *     Y[i,c] = sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) Q[j,c] + gamma Q[i,c]
  * over all N^2 pairs (no cut-off), summed on the fly in O(N) memory.
  * X: N x d; Q, Y: N x m column-major, 1 <= m <= 64.  Y must not alias X or Q.
+ * m = 1 runs the float32 CUDA-core product; m >= 2 evaluates each kernel
+ * value once for up to 16 columns (tensor cores for compact target blocks).
  * prec: KRR_FP32 (max relative error per element, against the FP64 sum
  * scaled by sum_j |Q_jc| K_hat_ij + gamma |Q_ic|, below 1e-5) or KRR_BF16 /
  * KRR_FP16 (reduced-precision kernel values, float32 accumulation).
- * Asynchronous on device arrays. */
+ * The call waits briefly for the point preparation (Morton sort and block
+ * metadata) to read the block counts that size the product grids; the
+ * product itself is asynchronous on device arrays. */
 krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d,
                           float sigma, float gamma, const float* Q, int m,
                           float* Y, krr_precision prec, void* stream);
@@ -156,12 +160,18 @@ krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d,
 /* ----------------------------------------------------------- FGMRES solve
  * Algorithm 1 on K = K_hat + gamma I with the paper's preconditioner:
  * truncated CG on M = K + delta I (Sec. 5), restart m, x0 = 0.  Arnoldi
- * (modified Gram-Schmidt) and the Givens least-squares update run in FP64;
- * the outer products K z_j and the true residual in FP32 with compensated
- * summation; the inner products M p in opts->inner_prec.
+ * (classical Gram-Schmidt applied twice, equal to the modified Gram-Schmidt
+ * of Alg. 1 to working precision) and the Givens least-squares update run in
+ * FP64; the outer products K z_j and the true residual in float32 with
+ * compensated (float-float) arithmetic; the inner products M p in
+ * opts->inner_prec.
  * B: N x m_rhs right-hand sides (float32), Xsol: N x m_rhs FP64 solutions
- * (column-major),
- * each column solved to |b - K x| / |b| <= opts->tol (true residual).
+ * (column-major), each column solved to |b - K x| / |b| <= opts->tol (true
+ * residual).  Several right-hand sides are solved in lockstep blocks of at
+ * most 16 columns (as few blocks as possible, of equal width): every column
+ * runs its own Alg. 1 with its own Krylov basis and restarts, and each inner
+ * CG step applies M to all columns' directions in one multi-column product.
+ * info[c].time_ms is the time of the block that solved column c.
  * opts = NULL takes the defaults.  info: NULL or an array of m_rhs reports.
  * The call waits for the solve when info != NULL.  Returns the worst status
  * over the columns. */
@@ -171,10 +181,13 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d,
                             krr_solve_info* info, void* stream);
 
 /* Many independent problems (same d, sigma, opts; own N_k, gamma_k, m_rhs
- * right-hand sides each) solved together.  probs: HOST array of nprob
- * krr_problem records whose arrays are DEVICE pointers.  info: NULL or
- * nprob * m_rhs reports (problem-major).  Waits for the solve when
- * info != NULL.  Returns the worst status. */
+ * right-hand sides each) solved together: one lockstep block solve per
+ * problem (and block of right-hand sides), each an independent branch with
+ * its own workspace, launched as CUDA graphs of at most 32 concurrent
+ * branches.  probs: HOST array of nprob krr_problem records whose arrays are
+ * DEVICE pointers.  info: NULL or nprob * m_rhs reports (problem-major);
+ * time_ms is the time of the whole batch.  Waits for the solve.  Returns the
+ * worst status. */
 krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs,
                                     int nprob, int d, float sigma, int m_rhs,
                                     const krr_fgmres_opts* opts,

@@ -1,5 +1,6 @@
 // C-ABI entry points of libkrr: handle, workspace, argument checks, host
 // array staging and the kernel-product calls.  The solvers live in krylov.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -298,21 +299,25 @@ krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float 
   void* qs;
   if ((e = c.ws.get("mvp.qs", sizeof(float) * P.Npad * m, &qs))) return cuda_error(c, e, fn);
   if ((e = gather_sorted(dQ, N, m, P.perm, P.Npad, (float*)qs, st))) return cuda_error(c, e, fn);
-  if (m == 1 || m > 16) {
-    for (int col = 0; col < m; ++col) {
-      const float* qc = (const float*)qs + (size_t)col * P.Npad;
-      MvpOut o;
-      o.perm = P.perm;
-      o.out_orig = dY + (size_t)col * N;
-      if ((e = mvp_launch(c, P, P, qc, qc, gamma, prec, o, st))) return cuda_error(c, e, fn);
-    }
-  } else {
-    // all columns in one pass: each kernel value serves m columns on the tensor cores
+  if (m == 1) {
     MvpOut o;
     o.perm = P.perm;
     o.out_orig = dY;
-    if ((e = mvp_multi_launch(c, P, P, (const float*)qs, m, (const float*)qs, gamma, prec, o, st)))
+    if ((e = mvp_launch(c, P, P, (const float*)qs, (const float*)qs, gamma, prec, o, st)))
       return cuda_error(c, e, fn);
+  } else {
+    // columns in as few passes of at most MAX_COLS as possible: each kernel
+    // value serves every column of a pass
+    const int passes = (m + MAX_COLS - 1) / MAX_COLS;
+    const int width = (m + passes - 1) / passes;
+    for (int col0 = 0; col0 < m; col0 += width) {
+      const int mc = std::min(width, m - col0);
+      const float* qc = (const float*)qs + (size_t)col0 * P.Npad;
+      MvpOut o;
+      o.perm = P.perm;
+      o.out_orig = dY + (size_t)col0 * N;
+      if ((e = mvp_multi_launch(c, P, P, qc, mc, qc, gamma, prec, o, st))) return cuda_error(c, e, fn);
+    }
   }
   if (sY) {
     if ((e = cudaMemcpyAsync(Y, dY, sizeof(float) * N * m, cudaMemcpyDeviceToHost, st)))

@@ -154,9 +154,10 @@ def test_nonfinite_input_reported(K):
     assert ei.value.status == K.KRR_ERR_NONFINITE
 
 
-@pytest.mark.parametrize("m,d", [(2, 3), (5, 2), (16, 3), (16, 4), (8, 8), (3, 1)])
+@pytest.mark.parametrize("m,d", [(2, 3), (5, 2), (16, 3), (16, 4), (8, 8), (3, 1), (20, 3), (33, 2)])
 def test_mvp_multi_rhs_tensor_cores_fp32(K, oracle_mod, m, d):
-    # m >= 2 runs the tensor-core kernel with hi/lo-split operands
+    # m >= 2 runs the tensor-core kernel with hi/lo-split operands (m > 16:
+    # several passes of equal width)
     rng = np.random.default_rng(100 + m * 10 + d)
     N = 6000
     X = rng.random((N, d)).astype(np.float32)
