@@ -34,8 +34,12 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 # DRAM bytes (read + write) of one product-kernel launch on the 2^20-point
 # workload, from one ncu capture (profiles/mvp_f32_kernel_cube1M_d3.md); valid
 # only for the kernel source it was taken on.
-TRAFFIC = {"source": "paper_1408_1237_gb300/csrc/mvp.cu", "sha1": "9775246cbc799cc4467e0840befecdb000cb45d1",
+TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
+# the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "",
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": ""},
+               "bytes": None}
 MVP_N, MVP_D = 1 << 20, 3
 
 
@@ -225,8 +229,6 @@ def run_libkrr(args):
 
     ex2_rate, ffma_rate, ffma2_lanes = K.krr_measure_alu_peaks()
     fp32_lanes = max(ffma_rate, ffma2_lanes)
-    # one MUFU.EX2 and d + 1 FP32 operations per pair (expanded form)
-    peak_pairs = min(ex2_rate, fp32_lanes / (MVP_D + 1))
 
     barrier(world, dev)
     torch.cuda.synchronize(dev)
@@ -256,6 +258,14 @@ def run_libkrr(args):
     launches = prof["launches"] - launches0
     kern_ms = prof["product_ms"] / max(prof["product_launches"], 1)
     achieved = pairs / (kern_ms / 1e3) / 1e9
+    # CUDA-core work per pair of the product's path (expanded form): one
+    # MUFU.EX2, plus d + 1 FP32 operations when the exponent is formed on the
+    # CUDA cores, or 1 (the weighted accumulate) when the tensor cores form it
+    tensor_exp = prof["tensor_exponent_launches"] == prof["product_launches"] > 0
+    fp32_per_pair = 1 if tensor_exp else MVP_D + 1
+    peak_pairs = min(ex2_rate, fp32_lanes / fp32_per_pair)
+    kernel_name = ("mvp_tcx_kernel (exponent on the tensor cores) + direct-form tail"
+                   if tensor_exp else "mvp_f32_kernel")
 
     # ---- 16 right-hand sides (one launch over all columns)
     Q16 = torch.from_numpy(inputs.mvp_problem(seed=rank + 7, N=MVP_N, d=MVP_D, m=16)["Q"].T.copy()).to(dev)
@@ -319,10 +329,12 @@ def run_libkrr(args):
             },
             "roofline": {
                 "bound": "alu", "achieved": achieved, "peak": peak_pairs / 1e9,
-                "unit": "Gpairs/s", "frac": achieved * 1e9 / peak_pairs, "traffic": traffic_bytes(),
-                "kernel": "mvp_f32_kernel", "launch_ms": kern_ms,
-                "peak_source": "measured on this GPU: min(MUFU.EX2 rate, FP32 lane rate/(d+1)) = "
-                               f"min({ex2_rate / 1e12:.2f}e12, {fp32_lanes / 1e12:.2f}e12/{MVP_D + 1})",
+                "unit": "Gpairs/s", "frac": achieved * 1e9 / peak_pairs,
+                "traffic": traffic_bytes(tensor_exp),
+                "kernel": kernel_name, "launch_ms": kern_ms,
+                "peak_source": "measured on this GPU: min(MUFU.EX2 rate, FP32 lane rate / FP32 "
+                               f"operations per pair) = min({ex2_rate / 1e12:.2f}e12, "
+                               f"{fp32_lanes / 1e12:.2f}e12/{fp32_per_pair})",
             },
             "e2e": {"value": e2e_value, "unit": "Gpairs/s",
                     "h2d_bytes_per_step": MVP_N * (MVP_D + 1) * 4, "d2h_bytes_per_step": MVP_N * 4},
@@ -340,15 +352,19 @@ def run_libkrr(args):
     return 0
 
 
-def traffic_bytes():
-    """ncu DRAM bytes per product launch, or None once the kernel changed."""
+def traffic_bytes(tensor_exp):
+    """ncu DRAM bytes of one product (all its kernels) on this workload, or
+    None once a kernel source changed since the capture."""
     import hashlib
-    path = os.path.join(ROOT, TRAFFIC["source"])
-    try:
-        h = hashlib.sha1(open(path, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    return TRAFFIC["bytes"] if h == TRAFFIC["sha1"] else None
+    t = TRAFFIC_TCX if tensor_exp else TRAFFIC
+    for src, sha in t["sources"].items():
+        try:
+            h = hashlib.sha1(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        except OSError:
+            return None
+        if h != sha:
+            return None
+    return t["bytes"]
 
 
 def solve_once(K, torch, p, dev, stream, inner_prec):

@@ -227,6 +227,11 @@ typedef struct {
     double product_ms;      /* their summed device time (CUDA events recorded
                                on the stream each launch ran on)                */
     double product_pairs;   /* target x source pairs they evaluated, per column */
+    int tensor_exponent_launches; /* of the timed launches, those that took the
+                               tensor-core exponent path (the exponent
+                               contraction on the tensor cores, one MUFU.EX2
+                               and one FMA per pair on the CUDA cores); the
+                               rest ran the all-CUDA-core kernel              */
 } krr_profile;
 /* Start (enable != 0) or stop timing the fast-product kernel on h; resets the
  * timed list.  Timing adds two event records per product launch. */

@@ -50,7 +50,8 @@ class krr_solve_info(ctypes.Structure):
 
 class krr_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("product_launches", ctypes.c_int),
-                ("product_ms", ctypes.c_double), ("product_pairs", ctypes.c_double)]
+                ("product_ms", ctypes.c_double), ("product_pairs", ctypes.c_double),
+                ("tensor_exponent_launches", ctypes.c_int)]
 
 
 class krr_problem(ctypes.Structure):
@@ -335,7 +336,8 @@ def krr_profile_enable(enable=True, handle=None):
 
 
 def krr_profile_read(handle=None):
-    """dict(launches, product_launches, product_ms, product_pairs); resets the timed list."""
+    """dict(launches, product_launches, product_ms, product_pairs,
+    tensor_exponent_launches); resets the timed list."""
     h = handle or default_handle()
     p = krr_profile()
     h.check(lib().krr_profile_read(h.h, ctypes.byref(p)))

@@ -83,11 +83,16 @@ struct Ctx {
   // CTA slots the product kernels plan for (0: 2 per SM); a batched solve
   // lowers it so that concurrent small problems are not over-split
   int plan_slots = 0;
+  // single-column float32 products may take the tensor-core exponent path
+  // (the no-allocation entry point keeps to the CUDA-core kernel, whose
+  // scratch its fixed array holds)
+  bool allow_tcx = true;
   // profiling of the fast product kernel (krr_profile_enable / _read)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
   size_t prof_used = 0;              // events in use (even)
   double prof_pairs = 0.0;
+  int prof_tensor_exp = 0;           // timed launches on the tensor-core exponent path
 };
 
 // Sub-context k of c (created on first use; freed with the handle).
@@ -175,6 +180,12 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& T, const PointsDev& S, con
 cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
                             bool split, bool bf, int splits, int tiles_per_split, double* part,
                             float* fac, const int* active, cudaStream_t st, bool dry = false);
+// ---- mvp_tc.cu: single-column float32-grade partial sums of the
+// expanded-form super-blocks (exponent on the tensor cores, EX2 + FMA per
+// pair on the CUDA cores); part: [splits][T.Npad].
+cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* q,
+                             int splits, int tiles_per_split, double* part, float* fac,
+                             const int* active, cudaStream_t st, bool dry = false);
 // Workspace and attributes of mvp_multi_launch with m columns and prec.
 cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, int m,
                               krr_precision prec, cudaStream_t st);

@@ -249,6 +249,7 @@ krr_status krr_profile_enable(krr_handle h, int enable) {
   h->ctx.profiling = enable != 0;
   h->ctx.prof_used = 0;
   h->ctx.prof_pairs = 0.0;
+  h->ctx.prof_tensor_exp = 0;
   return KRR_OK;
 }
 
@@ -259,6 +260,7 @@ krr_status krr_profile_read(krr_handle h, krr_profile* out) {
   out->product_launches = (int)(c.prof_used / 2);
   out->product_ms = 0.0;
   out->product_pairs = c.prof_pairs;
+  out->tensor_exponent_launches = c.prof_tensor_exp;
   for (size_t k = 0; k + 1 < c.prof_used; k += 2) {
     cudaError_t e = cudaEventSynchronize(c.prof_ev[k + 1]);
     if (e) return cuda_error(c, e, "krr_profile_read");
@@ -268,6 +270,7 @@ krr_status krr_profile_read(krr_handle h, krr_profile* out) {
   }
   c.prof_used = 0;
   c.prof_pairs = 0.0;
+  c.prof_tensor_exp = 0;
   return KRR_OK;
 }
 

@@ -66,6 +66,7 @@ struct MvpParams {
   float s;              // sqrt(log2(e) / (2 sigma^2))
   const int* active;    // predication flag (null: always run)
   int64_t part_stride;  // distance between splits in part (Nt_pad for one column)
+  int64_t slot0;        // first block slot of the grid (blocks before it are not processed)
 };
 
 // Warp-cooperative transform of one raw source tile for this warp's centre:
@@ -178,11 +179,11 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   if (p.active && *p.active == 0) return;
 
   // ---- this warp's target block
-  const int64_t slot = (int64_t)blockIdx.x * NW + warp;
+  const int64_t slot = p.slot0 + (int64_t)blockIdx.x * NW + warp;
   const int64_t nexp = *p.tn_exp;
   const bool live = slot < p.nblk;
   const int64_t blk = live ? p.torder[slot] : 0;
-  const int64_t last = min(((int64_t)blockIdx.x + 1) * NW, p.nblk);  // CTA's block slots end
+  const int64_t last = min(p.slot0 + ((int64_t)blockIdx.x + 1) * NW, p.nblk);  // CTA's block slots end
   const bool expanded = last <= nexp;  // uniform over the CTA
   float ctr[D];
 #pragma unroll
@@ -525,7 +526,7 @@ template <int D, int T>
 cudaError_t launch_typed(const MvpParams& p, int splits, cudaStream_t st) {
   cudaError_t e = set_attr<D, T>();
   if (e) return e;
-  dim3 grid((unsigned)((p.nblk + NW - 1) / NW), (unsigned)splits);
+  dim3 grid((unsigned)std::max<int64_t>(1, (p.nblk - p.slot0 + NW - 1) / NW), (unsigned)splits);
   mvp_f32_kernel<D, T><<<grid, NT, smem_bytes<D>(), st>>>(p); count_launch();
   return cudaGetLastError();
 }
@@ -626,6 +627,7 @@ cudaError_t dirm_typed(const MvpParams& p, const float* Q, int64_t q_stride, int
     count_launch();                                                                        \
   }                                                                                        \
   return cudaGetLastError();
+  if (m <= 1) { KRR_DIRM(1) }
   if (m <= 4) { KRR_DIRM(4) }
   if (m <= 8) { KRR_DIRM(8) }
   KRR_DIRM(16)
@@ -658,6 +660,29 @@ Plan multi_plan_dir(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
   return make_plan((Tp.nsb - Tp.h_sb_nexp) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
 }
 
+// The single-column float32 product takes the tensor-core exponent path when
+// there are enough target super-blocks to fill the GPU (one CTA of 4 warps
+// each, several per SM) and at least half of them are compact; otherwise the
+// CUDA-core kernel with its finer per-warp blocks.
+bool use_tcx(const Ctx& c, const PointsDev& Tp) {
+  return c.allow_tcx && Tp.nsb >= c.num_sms && 2 * Tp.h_sb_nexp >= Tp.nsb;
+}
+
+// Direct-form super-blocks of the single-column tensor-core path: through the
+// packed CUDA-core kernel (8 super-blocks per CTA) when its warp blocks are
+// the super-blocks, else the multi-column direct kernel with one column.
+bool tcx_dir_f32(const PointsDev& Tp) { return Tp.T * 32 == SB; }
+Plan tcx_dir_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+  if (tcx_dir_f32(Tp))
+    return make_plan(Tp.nsb - Tp.h_sb_nexp, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+  return multi_plan_dir(c, Tp, Sp);
+}
+
+Plan tcx_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+  return make_plan(Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
+                   c.plan_slots > 0 ? c.plan_slots : 4 * c.num_sms);
+}
+
 }  // namespace
 
 int mvp_targets_per_thread(int d, int64_t N) {
@@ -680,6 +705,17 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
   const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
   if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
+  if (use_tcx(c, Tp)) {
+    const Plan pt = tcx_plan(c, Tp, Sp), pd = tcx_dir_plan(c, Tp, Sp);
+    if ((e = c.ws.get("mvp.partt", sizeof(double) * pt.splits * (size_t)Tp.Npad, &v))) return e;
+    if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)Tp.Npad, &v))) return e;
+    if ((e = mvp_tcx_partials(c, Tp, Sp, nullptr, pt.splits, pt.tiles_per_split, nullptr, nullptr,
+                              nullptr, st, true)))
+      return e;
+    MvpParams p{};
+    p.nblk = Tp.nsb;
+    if ((e = dirm_dispatch(p, Tp.d, nullptr, 0, 1, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+  }
   switch (Tp.d) {
     case 1: return attrs_T<1>(Tp.T);
     case 2: return attrs_T<2>(Tp.T);
@@ -692,11 +728,112 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
   }
 }
 
+namespace {
+
+// Profiling events around the product kernels (krr_profile_*): returns the
+// stop event to record after them, or null.
+cudaEvent_t prof_begin(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaStream_t st) {
+  if (!c.profiling) return nullptr;
+  if (c.prof_used + 2 > c.prof_ev.size() && c.prof_ev.size() < 8192) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev)) return nullptr;
+      c.prof_ev.push_back(ev);
+    }
+  }
+  if (c.prof_used + 2 > c.prof_ev.size()) return nullptr;
+  cudaEventRecord(c.prof_ev[c.prof_used], st);
+  cudaEvent_t stop = c.prof_ev[c.prof_used + 1];
+  c.prof_used += 2;
+  c.prof_pairs += (double)Tp.N * (double)Sp.N;
+  return stop;
+}
+
+// Single-column float32 product with the exponent on the tensor cores:
+// expanded-form super-blocks in mvp_tcx_kernel, direct-form ones in the
+// CUDA-core kernel, then the finalize.
+cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
+                     const float* qdiag, float shift, const MvpOut& o, cudaStream_t st) {
+  cudaError_t e = mvp_reserve(c, Tp, Sp, st);
+  if (e) return e;
+  const Plan pt = tcx_plan(c, Tp, Sp), pd = tcx_dir_plan(c, Tp, Sp);
+  void *partt, *partd, *fac, *dpart, *dcnt;
+  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
+  if ((e = c.ws.get("mvp.partt", sizeof(double) * pt.splits * (size_t)Tp.Npad, &partt))) return e;
+  if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)Tp.Npad, &partd))) return e;
+  if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &fac))) return e;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
+  cudaEvent_t pev1 = prof_begin(c, Tp, Sp, st);
+  if (pev1) c.prof_tensor_exp += 1;
+  if ((e = mvp_tcx_partials(c, Tp, Sp, q, pt.splits, pt.tiles_per_split, (double*)partt, (float*)fac,
+                            o.active, st)))
+    return e;
+  if (Tp.nsb > Tp.h_sb_nexp) {
+    MvpParams p{};
+    p.xt = Tp.xs;
+    p.Nt = Tp.N;
+    p.Nt_pad = Tp.Npad;
+    p.tctr = Tp.sb_ctr;
+    p.torder = Tp.sb_order;
+    p.tn_exp = Tp.sb_nexp;
+    p.nblk = Tp.nsb;
+    p.xs = Sp.xs;
+    p.q = q;
+    p.ntiles = (int)(Sp.Npad / TS);
+    p.err = c.d_err;
+    p.s = Sp.scale;
+    p.active = o.active;
+    p.part_stride = Tp.Npad;
+    p.part = (double*)partd;
+    p.fac = (float*)fac;
+    p.slot0 = Tp.h_sb_nexp;
+    if (tcx_dir_f32(Tp)) {
+      // the warp blocks are the super-blocks: the packed CUDA-core kernel's
+      // direct form, over the direct-form slots only
+      switch (Tp.d) {
+        case 1: e = dispatch_T<1>(p, Tp.T, pd, st); break;
+        case 2: e = dispatch_T<2>(p, Tp.T, pd, st); break;
+        case 3: e = dispatch_T<3>(p, Tp.T, pd, st); break;
+        case 4: e = dispatch_T<4>(p, Tp.T, pd, st); break;
+        case 5: e = dispatch_T<5>(p, Tp.T, pd, st); break;
+        case 6: e = dispatch_T<6>(p, Tp.T, pd, st); break;
+        case 7: e = dispatch_T<7>(p, Tp.T, pd, st); break;
+        default: e = dispatch_T<8>(p, Tp.T, pd, st); break;
+      }
+      if (e) return e;
+    } else if ((e = dirm_dispatch(p, Tp.d, q, Sp.Npad, 1, SB / 32, Tp.h_sb_nexp, pd, st, true))) {
+      return e;
+    }
+  }
+  if (pev1) cudaEventRecord(pev1, st);
+  FinParams f{};
+  f.part = (const double*)partt;
+  f.splits = pt.splits;
+  f.part2 = (const double*)partd;
+  f.splits2 = pd.splits;
+  f.sb_flag = Tp.sb_flag;
+  f.part_stride = Tp.Npad;
+  f.N = Tp.N;
+  f.Npad = Tp.Npad;
+  f.fac = (const float*)fac;
+  f.qdiag = qdiag;
+  f.shift = shift;
+  f.o = o;
+  f.dot_part = (double*)dpart;
+  f.dot_count = (unsigned*)dcnt;
+  mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
                        const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                        cudaStream_t st) {
   if (prec != KRR_FP32) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
   if (Tp.N == 0) return cudaSuccess;
+  if (use_tcx(c, Tp)) return tcx_path(c, Tp, Sp, q, qdiag, shift, o, st);
   MvpParams p{};
   p.xt = Tp.xs;
   p.Nt = Tp.N;

@@ -415,6 +415,250 @@ __global__ void __launch_bounds__(256) mvp_tc_kernel(const TcParams p) {
     }
 }
 
+// ------------------------------------------------------------------------
+// Single-column float32-grade product: the exponent contraction E = A' B'^T
+// on the tensor cores (split f16 operands as above), then per pair one
+// MUFU.EX2 straight from the accumulator register and one float32 FMA with
+// the source weight, so the CUDA cores carry 1 EX2 + 1 FMA per pair and the
+// special-function unit is the only pipe near its limit (the all-CUDA-core
+// product needs d + 1 FP32 operations per pair as well, which at d = 3 loads
+// the FP32 pipe as fully as the EX2 loads MUFU).  One CTA per expanded-form
+// super-block, MT m-tiles of 16 targets per warp; a thread accumulates the
+// rows g and g+8 of each m-tile over its columns 2t, 2t+1 and the four
+// threads of a row are summed at the end.
+template <int D, int MT>
+__global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const TcParams p) {
+  using L = ExpLayout<D>;
+  using H = Half<false>;
+  constexpr int W = D + 1;
+  constexpr int RAW = (D + 1) * TS;  // coordinates, weights
+  extern __shared__ __align__(128) float smem[];
+  const int nthreads = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  __shared__ __align__(8) uint64_t bars[RS];
+  __shared__ volatile int abort_flag;
+  if (p.active && *p.active == 0) return;
+  const int64_t nexp = *p.tn_exp;
+  if ((int64_t)blockIdx.x >= nexp) return;
+
+  float* raw = smem;                                                   // RS stages
+  uint32_t* kvb = reinterpret_cast<uint32_t*>(smem + RS * RAW);          // 2 x TS x KV_STRIDE_W
+  float* qbuf = reinterpret_cast<float*>(kvb + 2 * TS * L::KV_STRIDE_W);  // 2 x TS weights
+
+  const int64_t blk = p.torder[blockIdx.x];
+  float ctr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
+
+  uint32_t afr[MT][L::KSTEPS][4];
+  const int64_t row0 = blk * p.WB + (int64_t)warp * 16 * MT;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int64_t i = row0 + mt * 16 + g + 8 * half;
+      const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+      float ah[W], al[W];
+      float r2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float x = p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
+        const float xh = p.s * (x - ctr[k]);
+        r2 = fmaf(xh, xh, r2);
+        ah[k] = H::to(H::from(xh));
+        al[k] = xh - ah[k];
+      }
+      ah[D] = 1.f;
+      al[D] = 0.f;
+      if (blockIdx.y == 0 && t == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
+#pragma unroll
+      for (int ks = 0; ks < L::KSTEPS; ++ks) {
+        const int k0 = 16 * ks + 2 * t;
+        afr[mt][ks][half] = H::pack(kv_value<D>(ah, al, k0, true), kv_value<D>(ah, al, k0 + 1, true));
+        afr[mt][ks][half + 2] =
+            H::pack(kv_value<D>(ah, al, k0 + 8, true), kv_value<D>(ah, al, k0 + 9, true));
+      }
+    }
+  }
+
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+  float acc[MT][2], acc2[MT][2], S[MT][2], C[MT][2];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) acc[mt][h] = acc2[mt][h] = S[mt][h] = C[mt][h] = 0.f;
+
+  auto issue = [&](int r) {
+    const int stage = r % RS;
+    const int64_t tile = t_begin + r;
+    float* dst = raw + stage * RAW;
+    mbar_arrive_expect_tx(&bars[stage], (uint32_t)RAW * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS, p.Q + tile * (int64_t)TS, TS * 4, &bars[stage]);
+  };
+  // CTA-wide transform of raw tile r into buffer b: the split source
+  // K-vectors, and the float32 weights (the raw stage is refilled while the
+  // tile is still being used)
+  auto transform = [&](int r, int b) {
+    const float* rs = raw + (r % RS) * RAW;
+    uint32_t* kv = kvb + b * TS * L::KV_STRIDE_W;
+    for (int j = tid; j < TS; j += nthreads) {
+      float bh[W], bl[W];
+      float bb = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float xh = p.s * (rs[k * TS + j] - ctr[k]);
+        bb = fmaf(-xh, xh, bb);
+        const float v = 2.f * xh;
+        bh[k] = H::to(H::from(v));
+        bl[k] = v - bh[k];
+      }
+      if (bb < -30000.f) {  // farther than any target can see: contributes 0
+#pragma unroll
+        for (int k = 0; k < D; ++k) bh[k] = bl[k] = 0.f;
+        bb = -30000.f;
+      }
+      bh[D] = H::to(H::from(bb));
+      bl[D] = bb - bh[D];
+      uint16_t hv[L::KV];
+#pragma unroll
+      for (int k = 0; k < L::KV; ++k) {
+        const typename H::T hk = H::from(kv_value<D>(bh, bl, k, false));
+        hv[k] = *reinterpret_cast<const uint16_t*>(&hk);
+      }
+#pragma unroll
+      for (int w = 0; w < L::KV / 2; ++w)
+        kv[j * L::KV_STRIDE_W + w] = (uint32_t)hv[2 * w] | ((uint32_t)hv[2 * w + 1] << 16);
+      qbuf[b * TS + j] = rs[D * TS + j];
+    }
+  };
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < RS; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RS, nt); ++issued) issue(issued);
+  if (nt > 0) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[0], 0));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    }
+    __syncthreads();
+    if (!abort_flag) transform(0, 0);
+    __syncthreads();
+  }
+
+  for (int r = 0; r < nt && !abort_flag; ++r) {
+    if (tid == 0 && r + RS < nt) {
+      fence_proxy_async_smem();
+      issue(r + RS);
+      ++issued;
+    }
+    if (r + 1 < nt) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[(r + 1) % RS], ((r + 1) / RS) & 1));
+      if (!ok) {
+        abort_flag = 1;
+        if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+      } else {
+        transform(r + 1, (r + 1) & 1);
+      }
+    }
+    const uint32_t* kv = kvb + (r & 1) * TS * L::KV_STRIDE_W;
+    const float* qv = qbuf + (r & 1) * TS;
+#pragma unroll 1
+    for (int kk = 0; kk < TS / 16; ++kk) {
+      uint32_t bfr[2][L::KSTEPS][2];
+#pragma unroll
+      for (int nt2 = 0; nt2 < 2; ++nt2) {
+        const int j = kk * 16 + nt2 * 8 + g;
+#pragma unroll
+        for (int ks = 0; ks < L::KSTEPS; ++ks) {
+          bfr[nt2][ks][0] = kv[j * L::KV_STRIDE_W + 8 * ks + t];
+          bfr[nt2][ks][1] = kv[j * L::KV_STRIDE_W + 8 * ks + t + 4];
+        }
+      }
+      // weights of this thread's accumulator columns: sources 2t, 2t+1 of
+      // each 8-source half
+      const float2 q0 = *reinterpret_cast<const float2*>(qv + kk * 16 + 2 * t);
+      const float2 q1 = *reinterpret_cast<const float2*>(qv + kk * 16 + 8 + 2 * t);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < L::KSTEPS; ++ks) {
+          mma16816<false>(e0, afr[mt][ks], bfr[0][ks][0], bfr[0][ks][1]);
+          mma16816<false>(e1, afr[mt][ks], bfr[1][ks][0], bfr[1][ks][1]);
+        }
+        // rows g (elements 0, 1) and g+8 (elements 2, 3); two short FMA
+        // chains per row
+        acc[mt][0] = fmaf(q0.y, ex2(e0[1]), fmaf(q0.x, ex2(e0[0]), acc[mt][0]));
+        acc2[mt][0] = fmaf(q1.y, ex2(e1[1]), fmaf(q1.x, ex2(e1[0]), acc2[mt][0]));
+        acc[mt][1] = fmaf(q0.y, ex2(e0[3]), fmaf(q0.x, ex2(e0[2]), acc[mt][1]));
+        acc2[mt][1] = fmaf(q1.y, ex2(e1[3]), fmaf(q1.x, ex2(e1[2]), acc2[mt][1]));
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        kahan_add(S[mt][h], C[mt][h], acc[mt][h] + acc2[mt][h]);
+        acc[mt][h] = acc2[mt][h] = 0.f;
+      }
+    __syncthreads();
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RS], (r / RS) & 1);
+    __syncthreads();
+    return;
+  }
+  // the four threads of a row hold its sums over columns 2t, 2t+1
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double v = (double)S[mt][h] - (double)C[mt][h];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      const int64_t i = row0 + mt * 16 + g + 8 * h;
+      if (t == 0 && i < p.Nt_pad) p.part[(int64_t)blockIdx.y * p.Nt_pad + i] = v;
+    }
+}
+
+constexpr int TCX_MT = 4;
+
+template <int D>
+constexpr size_t tcx_smem_bytes() {
+  return sizeof(float) * RS * (D + 1) * TS + sizeof(uint32_t) * 2 * TS * ExpLayout<D>::KV_STRIDE_W +
+         sizeof(float) * 2 * TS;
+}
+
+template <int D>
+cudaError_t tcx_launch_typed(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(mvp_tcx_kernel<D, TCX_MT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tcx_smem_bytes<D>());
+    if (e) return e;
+    done[dev] = true;
+  }
+  if (dry) return cudaSuccess;
+  dim3 grid((unsigned)p.nblk, (unsigned)splits);
+  mvp_tcx_kernel<D, TCX_MT><<<grid, 32 * (SB / (16 * TCX_MT)), tcx_smem_bytes<D>(), st>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int D, int MT, int NRT, bool SPLIT, bool BF>
 cudaError_t launch(const TcParams& p, int splits, int warps, cudaStream_t st, bool dry) {
   using L = ExpLayout<D>;
@@ -498,6 +742,42 @@ cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, cons
     case 6: return dispatch_prec<6>(p, splits, split, bf, st, dry);
     case 7: return dispatch_prec<7>(p, splits, split, bf, st, dry);
     case 8: return dispatch_prec<8>(p, splits, split, bf, st, dry);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* q,
+                             int splits, int tiles_per_split, double* part, float* fac,
+                             const int* active, cudaStream_t st, bool dry) {
+  TcParams p{};
+  p.xt = T.xs;
+  p.Nt = T.N;
+  p.Nt_pad = T.Npad;
+  p.tctr = T.sb_ctr;
+  p.torder = T.sb_order;
+  p.tn_exp = T.sb_nexp;
+  p.nblk = std::max<int64_t>(1, T.h_sb_nexp);
+  p.WB = SB;
+  p.xs = S.xs;
+  p.Q = q;
+  p.Ns_pad = S.Npad;
+  p.m = 1;
+  p.ntiles = (int)(S.Npad / TS);
+  p.tiles_per_split = tiles_per_split;
+  p.part = part;
+  p.fac = fac;
+  p.err = c.d_err;
+  p.s = S.scale;
+  p.active = active;
+  switch (T.d) {
+    case 1: return tcx_launch_typed<1>(p, splits, st, dry);
+    case 2: return tcx_launch_typed<2>(p, splits, st, dry);
+    case 3: return tcx_launch_typed<3>(p, splits, st, dry);
+    case 4: return tcx_launch_typed<4>(p, splits, st, dry);
+    case 5: return tcx_launch_typed<5>(p, splits, st, dry);
+    case 6: return tcx_launch_typed<6>(p, splits, st, dry);
+    case 7: return tcx_launch_typed<7>(p, splits, st, dry);
+    case 8: return tcx_launch_typed<8>(p, splits, st, dry);
     default: return cudaErrorNotSupported;
   }
 }

@@ -130,6 +130,7 @@ krr_status setup_device(int dev, DeviceScratch*& out) {
     d.base = (unsigned char*)base;
     d.ctx.device = dev;
     d.ctx.num_sms = sms;
+    d.ctx.allow_tcx = false;
     size_t off = 0;
     for (const Region& r : kRegions) {
       // recorded as larger than any request, so the workspace never regrows

@@ -60,6 +60,7 @@ def test_struct_layouts_match_header(clib):
     assert ctypes.sizeof(binding.krr_fgmres_opts) == 48
     assert ctypes.sizeof(binding.krr_solve_info) == 48
     assert ctypes.sizeof(binding.krr_problem) == 40
+    assert ctypes.sizeof(binding.krr_profile) == 40
 
 
 def test_product_path_has_no_oracle_dependency():

@@ -58,3 +58,22 @@ def test_mll_grad_host_arrays_and_no_dx(K):
                                        n_probes=2, seed=1, want_dX=False)
     assert none is None
     assert gs1 == pytest.approx(gs2, rel=1e-9) and gg1 == pytest.approx(gg2, rel=1e-9)
+
+
+def test_autograd_surrogate_carries_the_gradient(K, oracle_mod):
+    import torch
+    from paper_1408_1237_gb300.autograd import mll_surrogate
+    p = inputs.gradient_problem(seed=5, N=400, d=2, probes=8)
+    X = _dev(p["X"]).requires_grad_(True)
+    ls = torch.tensor(np.log(p["sigma"]), dtype=torch.float64, device="cuda", requires_grad=True)
+    lg = torch.tensor(np.log(p["gamma"]), dtype=torch.float64, device="cuda", requires_grad=True)
+    opts = K.default_opts(tol=1e-8, max_cycles=20)
+    loss = mll_surrogate(X, ls, lg, _dev(p["y"]), n_probes=8, seed=p["seed"], opts=opts)
+    assert loss.item() == 0.0
+    (2.0 * loss).backward()
+    gs, gg, gX, _ = K.krr_mll_grad(_dev(p["X"]), _dev(p["y"]), float(np.float32(np.exp(np.log(p["sigma"])))),
+                                   float(np.float32(np.exp(np.log(p["gamma"])))), n_probes=8,
+                                   seed=p["seed"], opts=opts)
+    assert ls.grad.item() == pytest.approx(2.0 * gs, rel=1e-6)
+    assert lg.grad.item() == pytest.approx(2.0 * gg, rel=1e-6)
+    np.testing.assert_allclose(X.grad.cpu().numpy(), 2.0 * gX.cpu().numpy(), rtol=1e-6, atol=1e-12)
