@@ -31,15 +31,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP32 form"
-# DRAM bytes (read + write) of one product-kernel launch on the 2^20-point
-# workload, from one ncu capture (profiles/mvp_f32_kernel_cube1M_d3.md); valid
-# only for the kernel source it was taken on.
+# DRAM bytes (read + write) of one product on the 2^20-point workload, from
+# one ncu capture per path (dram__bytes_read.sum + dram__bytes_write.sum of
+# every kernel of the product); valid only for the kernel sources they were
+# taken on.
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "",
-                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": ""},
-               "bytes": None}
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "52e9cee25c18425fc473ba87f707502aab864605",
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "b0014c8268cd661102f707b3228df26685dd56b0"},
+               "bytes": 22100736 + 91679488 + 17155584 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 

@@ -12,7 +12,7 @@
   the inner solve being truncated CG on M = K + delta I = K_hat + (gamma+delta) I
   (Sec. 5, Eq. for M).
 
-Readings of the paper (every one listed in the design doc):
+Readings of the paper, where it is silent or ambiguous:
 * Stopping rule (Sec. 4.3): the relative residual |b - K x|_2 / |b|_2 <= tol.
 * Alg. 1 indices are taken as the standard 1-based FGMRES(m); w is
   orthogonalised against v_1..v_j one at a time (modified Gram-Schmidt) as the
