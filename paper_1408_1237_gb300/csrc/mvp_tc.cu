@@ -123,6 +123,16 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
   }
 }
 
+// d = a b (zero accumulator input), f16 operands.
+__device__ __forceinline__ void mma16816_z(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                           uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%10,%10,%10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
+}
+
 // Value of K-vector slot k for the split vector v (hi/lo per component):
 // A' = [h, h, l, l] (operand A) or B' = [h, l, h, l] (operand B); 3-term
 // layouts drop the last block.
@@ -484,11 +494,15 @@ __global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const Tc
 
   const int t_begin = blockIdx.y * p.tiles_per_split;
   const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
-  float acc[MT][2], acc2[MT][2], S[MT][2], C[MT][2];
+  float2 acc[MT][2], acc2[MT][2];
+  float S[MT][2], C[MT][2];
 #pragma unroll
   for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) acc[mt][h] = acc2[mt][h] = S[mt][h] = C[mt][h] = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      acc[mt][h] = acc2[mt][h] = make_float2(0.f, 0.f);
+      S[mt][h] = C[mt][h] = 0.f;
+    }
 
   auto issue = [&](int r) {
     const int stage = r % RS;
@@ -590,26 +604,28 @@ __global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const Tc
       const float2 q1 = *reinterpret_cast<const float2*>(qv + kk * 16 + 8 + 2 * t);
 #pragma unroll
       for (int mt = 0; mt < MT; ++mt) {
-        float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
+        float e0[4], e1[4];
+        mma16816_z(e0, afr[mt][0], bfr[0][0][0], bfr[0][0][1]);
+        mma16816_z(e1, afr[mt][0], bfr[1][0][0], bfr[1][0][1]);
 #pragma unroll
-        for (int ks = 0; ks < L::KSTEPS; ++ks) {
+        for (int ks = 1; ks < L::KSTEPS; ++ks) {
           mma16816<false>(e0, afr[mt][ks], bfr[0][ks][0], bfr[0][ks][1]);
           mma16816<false>(e1, afr[mt][ks], bfr[1][ks][0], bfr[1][ks][1]);
         }
-        // rows g (elements 0, 1) and g+8 (elements 2, 3); two short FMA
-        // chains per row
-        acc[mt][0] = fmaf(q0.y, ex2(e0[1]), fmaf(q0.x, ex2(e0[0]), acc[mt][0]));
-        acc2[mt][0] = fmaf(q1.y, ex2(e1[1]), fmaf(q1.x, ex2(e1[0]), acc2[mt][0]));
-        acc[mt][1] = fmaf(q0.y, ex2(e0[3]), fmaf(q0.x, ex2(e0[2]), acc[mt][1]));
-        acc2[mt][1] = fmaf(q1.y, ex2(e1[3]), fmaf(q1.x, ex2(e1[2]), acc2[mt][1]));
+        // rows g (elements 0, 1) and g+8 (elements 2, 3): the two columns of
+        // a row and 8-source half share one packed FMA
+        acc[mt][0] = ffma2(q0, make_float2(ex2(e0[0]), ex2(e0[1])), acc[mt][0]);
+        acc2[mt][0] = ffma2(q1, make_float2(ex2(e1[0]), ex2(e1[1])), acc2[mt][0]);
+        acc[mt][1] = ffma2(q0, make_float2(ex2(e0[2]), ex2(e0[3])), acc[mt][1]);
+        acc2[mt][1] = ffma2(q1, make_float2(ex2(e1[2]), ex2(e1[3])), acc2[mt][1]);
       }
     }
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        kahan_add(S[mt][h], C[mt][h], acc[mt][h] + acc2[mt][h]);
-        acc[mt][h] = acc2[mt][h] = 0.f;
+        kahan_add(S[mt][h], C[mt][h], (acc[mt][h].x + acc[mt][h].y) + (acc2[mt][h].x + acc2[mt][h].y));
+        acc[mt][h] = acc2[mt][h] = make_float2(0.f, 0.f);
       }
     __syncthreads();
   }
