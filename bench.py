@@ -279,6 +279,17 @@ def run_libkrr(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     m16_ms = e0.elapsed_time(e1)
+    # the same on the tcgen05 / tensor-memory kernel (handle option)
+    h5 = K.Handle()
+    K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h5)
+    K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h5)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h5)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    m16_tc5_ms = e0.elapsed_time(e1)
+    h5.close()
 
     # ---- end to end through the C ABI with pinned host buffers
     Xh = torch.from_numpy(p["X"]).pin_memory()
@@ -341,7 +352,9 @@ def run_libkrr(args):
                     "h2d_bytes_per_step": MVP_N * (MVP_D + 1) * 4, "d2h_bytes_per_step": MVP_N * 4},
             "gpu_launches": launches,
             "clocks": clk,
-            "mvp_m16": {"ms": m16_ms, "Gpair_rhs_per_s": pairs * 16 / (m16_ms / 1e3) / 1e9},
+            "mvp_m16": {"ms": m16_ms, "Gpair_rhs_per_s": pairs * 16 / (m16_ms / 1e3) / 1e9,
+                        "kernel": "mma.sync (default)",
+                        "tcgen05_ms": m16_tc5_ms},
             "fgmres": solve,
             "mll_grad": grad,
             "cpu_baseline": cpu,

@@ -118,6 +118,20 @@ const char* krr_status_string(krr_status s);
 int krr_version(void);
 void krr_fgmres_default_opts(krr_fgmres_opts* opts);
 
+/* Handle options. */
+typedef enum {
+    /* value != 0: the multi-column tensor-core products (krr_kernel_mvp with
+     * m >= 2, block solves) use the 5th-generation tensor-core kernel
+     * (tcgen05.mma with accumulators in tensor memory: S = A B^T into tensor
+     * memory, 2^S written back over it as f16, Y += P Q with P read from
+     * tensor memory) instead of the default mma.sync kernel.  Same results to
+     * the float32 bar; on GB300 the default is faster (measured: 16 columns
+     * at 2^20 points, 450 ms vs 584 ms). */
+    KRR_OPT_TCGEN05 = 1
+} krr_option;
+/* Set option `option` of h to `value`.  Unknown options: KRR_ERR_INVALID_ARG. */
+krr_status krr_set_option(krr_handle h, int option, int value);
+
 /* ----------------------------------------------------------- kernel MVP
  * Y = (K_hat + gamma I) Q  (Eqs. 1-3; the weighted kernel sum of Sec. 3.1):
  *     Y[i,c] = sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) Q[j,c] + gamma Q[i,c]

@@ -84,6 +84,7 @@ _SIGNATURES = {
     "krr_measure_alu_peaks": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
                                _vp], _int),
     "krr_profile_enable": ([_vp, _int], _int),
+    "krr_set_option": ([_vp, _int, _int], _int),
     "krr_kernel_mvp_noalloc": ([_vp, _i64, _int, _f, _f, _vp, _int, _vp, _vp], _int),
     "krr_profile_read": ([_vp, ctypes.POINTER(krr_profile)], _int),
 }
@@ -328,6 +329,16 @@ def krr_measure_alu_peaks(handle=None, stream=None):
     h.check(lib().krr_measure_alu_peaks(h.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                         stream))
     return a.value, b.value, c.value
+
+
+KRR_OPT_TCGEN05 = 1
+
+
+def krr_set_option(option, value, handle=None):
+    """Set a handle option (KRR_OPT_TCGEN05: multi-column tensor-core
+    products on the tcgen05 / tensor-memory kernel)."""
+    h = handle or default_handle()
+    h.check(lib().krr_set_option(h.h, int(option), int(value)))
 
 
 def krr_profile_enable(enable=True, handle=None):

@@ -87,6 +87,9 @@ struct Ctx {
   // (the no-allocation entry point keeps to the CUDA-core kernel, whose
   // scratch its fixed array holds)
   bool allow_tcx = true;
+  // multi-column tensor-core products on the tcgen05 / tensor-memory kernel
+  // instead of the mma.sync kernel (krr_set_option)
+  bool use_tcgen05 = false;
   // profiling of the fast product kernel (krr_profile_enable / _read)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
@@ -186,6 +189,11 @@ cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, cons
 cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* q,
                              int splits, int tiles_per_split, double* part, float* fac,
                              const int* active, cudaStream_t st, bool dry = false);
+// ---- mvp_tc.cu: the same partial sums on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory), two CTAs per super-block.
+cudaError_t mvp_umma_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
+                              bool split, bool bf, int splits, int tiles_per_split, double* part,
+                              float* fac, const int* active, cudaStream_t st, bool dry = false);
 // Workspace and attributes of mvp_multi_launch with m columns and prec.
 cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, int m,
                               krr_precision prec, cudaStream_t st);

@@ -244,6 +244,17 @@ krr_status krr_destroy(krr_handle h) {
 
 const char* krr_last_error(krr_handle h) { return h ? h->ctx.last_error.c_str() : "NULL handle"; }
 
+krr_status krr_set_option(krr_handle h, int option, int value) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  switch (option) {
+    case KRR_OPT_TCGEN05:
+      h->ctx.use_tcgen05 = value != 0;
+      return KRR_OK;
+    default:
+      return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: unknown option %d", option);
+  }
+}
+
 krr_status krr_profile_enable(krr_handle h, int enable) {
   if (!h) return KRR_ERR_INVALID_ARG;
   h->ctx.profiling = enable != 0;

@@ -654,7 +654,11 @@ cudaError_t dirm_dispatch(const MvpParams& p, int d, const float* Q, int64_t q_s
 // tensor-core kernel over the expanded-form super-blocks, the CUDA-core
 // kernel over the direct-form ones, each planned for its own grid.
 Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
-  return make_plan(Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+  // two CTAs (of 128 targets) per super-block, at most two per SM (tensor memory)
+  // one CTA per super-block (mma.sync kernel), or two of 128 targets with at
+  // most two per SM (tcgen05 kernel: tensor memory)
+  return make_plan((c.use_tcgen05 ? 2 : 1) * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
+                   c.plan_slots);
 }
 Plan multi_plan_dir(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
   return make_plan((Tp.nsb - Tp.h_sb_nexp) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
@@ -919,6 +923,9 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   MvpParams p{};
   p.nblk = Tp.nsb;
   if ((e = dirm_dispatch(p, Tp.d, nullptr, 0, m, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+  if (c.use_tcgen05)
+    return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
+                             pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
   return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                          pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
 }
@@ -954,11 +961,16 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.fac = (float*)fac;
-  // expanded-form super-blocks: all columns on the tensor cores
-  if (Tp.h_sb_nexp > 0 &&
-      (e = mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
-                           pt.tiles_per_split, (double*)part, p.fac, o.active, st)))
-    return e;
+  // expanded-form super-blocks: all columns on the tensor cores (mma.sync
+  // kernel; the tcgen05 / tensor-memory kernel when the handle asks for it)
+  if (Tp.h_sb_nexp > 0) {
+    e = c.use_tcgen05
+            ? mvp_umma_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
+                                pt.tiles_per_split, (double*)part, p.fac, o.active, st)
+            : mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
+                              pt.tiles_per_split, (double*)part, p.fac, o.active, st);
+    if (e) return e;
+  }
   // direct-form super-blocks: all columns in one CUDA-core launch
   if (Tp.nsb > Tp.h_sb_nexp) {
     p.part = (double*)partd;

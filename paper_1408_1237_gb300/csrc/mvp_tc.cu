@@ -59,6 +59,10 @@ struct TcParams {
   int* err;
   float s;
   const int* active;
+  // tcgen05 kernel: weights pre-split into f16 hi / lo, one 16 x 256 K-major
+  // tile (8 KB) per source tile
+  const uint16_t* qh_tiles;
+  const uint16_t* ql_tiles;
 };
 
 // Terms of the split exponent: 4 (Ah Bh + Ah Bl + Al Bh + Al Bl) when 4(D+1)
@@ -648,6 +652,506 @@ __global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const Tc
     }
 }
 
+// ------------------------------------------------------------------------
+// Multi-column product on the 5th-generation tensor cores (tcgen05, TMEM
+// accumulators): the same two contractions as mvp_tc_kernel, with the
+// operands where the tcgen05 datapath wants them.
+//
+// One CTA = 128 targets (half of an expanded-form super-block) = the 128
+// TMEM lanes, 8 warps: warp w serves lanes 32 (w % 4) .. + 31 and, of every
+// chunk of 64 sources, the 32 sources of its warpgroup w / 4.  Per source
+// tile (256 sources) the CTA transforms the raw tile into f16 K-major
+// operands in shared memory (source K-vectors B and the weight columns Q, hi
+// and lo), then for each chunk of 64 sources:
+//   1. one elected thread issues S = A B^T (M = 128, N = 64, K = 16 per
+//      instruction) into one of three TMEM buffers (fp32); the next chunk's
+//      S is issued as soon as this one is complete, so the tensor cores work
+//      while the threads exponentiate;
+//   2. every thread reads its 32 values of S (tcgen05.ld), forms P = 2^S
+//      with MUFU.EX2 and writes P as f16 (hi, and lo when split) over the
+//      same 32 TMEM columns (tcgen05.st);
+//   3. the elected thread issues Y += P Q with P read from TMEM (M = 128,
+//      N = 16, K = 16 per instruction: Ph Qh + Pl Qh + Ph Ql when split).
+// Each S buffer has its own mbarrier (a commit per chunk), Y its own; every
+// barrier phase is awaited by all threads before the barrier is committed
+// again.  Y lives in TMEM for a tile and is folded into float32 Kahan sums
+// per tile.  Shared operands use the canonical no-swizzle K-major layout:
+// 8-row x 16-byte core matrices, adjacent along K 128 bytes apart (leading
+// byte offset), 8-row groups KC*128 bytes apart (stride byte offset).
+namespace umma {
+
+constexpr int ROWS = 128;       // targets per CTA (MMA M)
+constexpr int THREADS = 256;    // two warpgroups
+constexpr int NC = 64;          // sources per chunk (N of the exponent MMA)
+constexpr int NBUF = 3;         // S/P buffers of NC columns
+constexpr int YN = 16;          // Y columns (N of the P Q MMA)
+constexpr int TMEM_COLS = 256;  // S/P buffers at 0, 64, 128; Y buffers at 192, 208
+constexpr int SMEM_FLOOR = 80 * 1024;  // at most two CTAs per SM (TMEM holds two)
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo) {
+  return ((uint64_t)((saddr >> 4) & 0x3FFF)) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D f32, A/B f16 (bf = 0) or bf16 (1),
+// both K-major, N and M as given.
+__host__ __device__ constexpr uint32_t idesc(int bf, int n, int m) {
+  return (1u << 4) | ((uint32_t)bf << 7) | ((uint32_t)bf << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t id, int acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+               :: "r"(d), "r"(a_tmem), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+      :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+         "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Byte offset of element (row, k) in a K-major no-swizzle tile with kc
+// k-chunks of 8 elements per 8-row group.
+__device__ __forceinline__ uint32_t kmaj(int row, int k, int kc) {
+  return (uint32_t)((((row >> 3) * kc + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+// A stage: the tile's raw coordinates (D x 1 KB) and its weight tiles (hi,
+// and lo when split: 8 KB each, read by the MMAs straight from the stage).
+template <int D>
+constexpr uint32_t stage_bytes(bool split) {
+  return (uint32_t)(sizeof(float) * D * TS + 2 * YN * TS * (split ? 2 : 1));
+}
+
+template <int D>
+constexpr size_t smem_bytes(bool split) {
+  using L = ExpLayout<D>;
+  const size_t need = RS * (size_t)stage_bytes<D>(split) + 2 * ROWS * L::KV + 2 * (2 * TS * L::KV);
+  return need > SMEM_FLOOR ? need : SMEM_FLOOR;
+}
+
+}  // namespace umma
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(smem_addr(bar)) : "memory");
+}
+
+template <int D, bool SPLIT, bool BF>
+__global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcParams p) {
+  using namespace umma;
+  using L = ExpLayout<D>;
+  using H = Half<BF>;
+  constexpr int W = D + 1;
+  constexpr int KC = L::KV / 8;      // k-chunks of a K-vector
+  constexpr int QKC = TS / 8;        // k-chunks of a weight row (one tile)
+  constexpr int NCW = THREADS / 32;  // compute warps (warp NCW issues the MMAs)
+  constexpr int CPT = TS / NC;       // chunks per tile
+  constexpr int AHEAD = NBUF - 1;    // exponent MMAs issued ahead of the P Q in hand
+  constexpr uint32_t BBYTES = 2 * TS * L::KV;  // one B operand buffer
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[RS];        // TMA stages
+  __shared__ __align__(8) uint64_t sfull[NBUF];     // S of buffer b complete (commit)
+  __shared__ __align__(8) uint64_t pfull[NBUF];     // P of buffer b written (compute warps)
+  __shared__ __align__(8) uint64_t pdone[NBUF];     // P Q reading buffer b complete (commit)
+  __shared__ __align__(8) uint64_t bready[2];       // B operand buffer written (compute warps)
+  __shared__ __align__(8) uint64_t yfull[2];        // Y buffer complete for its tile (commit)
+  __shared__ __align__(8) uint64_t yfree[2];        // Y buffer read (compute warps)
+  __shared__ __align__(8) uint64_t dbar;            // after an abort: the MMAs issued are complete
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool mma_warp = warp == NCW;
+  const int wg = (warp >> 2) & 1;  // compute warpgroup: columns 32 wg .. of each chunk
+  if (p.active && *p.active == 0) return;
+  const int64_t nexp = *p.tn_exp;
+  const int64_t sb_slot = blockIdx.x >> 1;
+  if (sb_slot >= nexp) return;
+  constexpr uint32_t SBYTES = stage_bytes<D>(SPLIT);
+  constexpr uint32_t QTILE = 2 * YN * TS;  // bytes of one weight tile
+  unsigned char* stages = smem_raw;        // RS stages: coordinates, Qh, Ql
+  unsigned char* sA = smem_raw + RS * SBYTES;
+  unsigned char* sB = sA + 2 * ROWS * L::KV;  // two B buffers
+
+  const int64_t blk = p.torder[sb_slot];
+  float ctr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
+  const int row = 32 * (warp & 3) + lane;                                  // TMEM lane of a compute thread
+  const int64_t i = blk * SB + (int64_t)(blockIdx.x & 1) * ROWS + row;  // and its target
+
+  // ---- operand A (first compute warpgroup): the row's split K-vector [x^, 1]
+  if (warp < 4) {
+    const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+    float ah[W], al[W];
+    float r2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float x = p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
+      const float xh = p.s * (x - ctr[k]);
+      r2 = fmaf(xh, xh, r2);
+      ah[k] = H::to(H::from(xh));
+      al[k] = xh - ah[k];
+    }
+    ah[D] = 1.f;
+    al[D] = 0.f;
+    if (blockIdx.y == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
+#pragma unroll
+    for (int kc = 0; kc < KC; ++kc) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        w[e] = H::pack(kv_value<D>(ah, al, 8 * kc + 2 * e, true), kv_value<D>(ah, al, 8 * kc + 2 * e + 1, true));
+      *reinterpret_cast<uint4*>(sA + kmaj(row, 8 * kc, KC)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < RS; ++st) mbar_init(&bars[st], 1);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&sfull[b], 1);
+      mbar_init(&pfull[b], NCW);
+      mbar_init(&pdone[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bready[b], NCW);
+      mbar_init(&yfull[b], 1);
+      mbar_init(&yfree[b], NCW);
+    }
+    mbar_init(&dbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t y_col = NBUF * NC;  // Y buffers at y_col and y_col + YN
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+
+  auto issue = [&](int r) {
+    const int stage = r % RS;
+    const int64_t tile = t_begin + r;
+    unsigned char* dst = stages + stage * SBYTES;
+    mbar_arrive_expect_tx(&bars[stage], SBYTES);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS * 4, p.qh_tiles + tile * (int64_t)(YN * TS), QTILE, &bars[stage]);
+    if (SPLIT) bulk_g2s(dst + D * TS * 4 + QTILE, p.ql_tiles + tile * (int64_t)(YN * TS), QTILE, &bars[stage]);
+  };
+  // a bounded wait that also gives up once the other role has aborted
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+      if (abort_flag || clock64() - t0 > WAIT_LIMIT_CLOCKS) return false;
+    }
+    return true;
+  };
+
+  int issued = 0;
+  if (mma_warp) {
+    // ================= MMA warp: one thread issues every tcgen05.mma, as a
+    // stream of chunks: the exponent MMAs run AHEAD chunks in front of the
+    // P Q in hand, across tile boundaries
+    if (lane == 0) {
+      const uint32_t id_s = idesc(BF ? 1 : 0, NC, ROWS);
+      const uint32_t id_y = idesc(BF ? 1 : 0, YN, ROWS);
+      const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
+      uint32_t n_pd[NBUF] = {0, 0, 0}, w_pd[NBUF] = {0, 0, 0};  // pdone commits issued / awaited
+      uint32_t n_pf[NBUF] = {0, 0, 0};                            // pfull phases awaited
+      uint32_t n_br[2] = {0, 0}, n_yf[2] = {0, 0};                // bready / yfree phases awaited
+      const int total = nt * CPT;
+      int next_s = 0;
+      bool ok = true;
+      for (int c = 0; c < total && ok; ++c) {
+        while (ok && next_s < total && next_s <= c + AHEAD) {
+          const int r = next_s / CPT, q = next_s % CPT, b = next_s % NBUF, bb = r & 1;
+          if (q == 0) {  // the tile's B operand: waited for only when this S is
+                         // needed now, else the P Q in hand goes first
+            if (next_s > c && !mbar_try_wait(&bready[bb], n_br[bb] & 1)) break;
+            ok = wait(&bready[bb], n_br[bb] & 1);
+            ++n_br[bb];
+          }
+          if (ok && n_pd[b] != w_pd[b]) {  // the last P Q that read buffer b
+            ok = wait(&pdone[b], w_pd[b] & 1);
+            ++w_pd[b];
+          }
+          if (!ok) break;
+          fence_after();
+#pragma unroll
+          for (int ks = 0; ks < L::KSTEPS; ++ks)
+            mma_ss(tmem + (uint32_t)(b * NC), sdesc(a_addr + 256u * ks, KC * 128),
+                   sdesc(b_addr + (uint32_t)bb * BBYTES + (uint32_t)(8 * q * KC * 128) + 256u * ks, KC * 128),
+                   id_s, ks > 0);
+          commit(&sfull[b]);
+          ++next_s;
+        }
+        if (!ok) break;
+        const int r = c / CPT, q = c % CPT, b = c % NBUF, yb = r & 1;
+        ok = wait(&pfull[b], n_pf[b] & 1);
+        ++n_pf[b];
+        if (ok && q == 0 && r >= 2) {  // Y buffer yb was read for tile r - 2
+          ok = wait(&yfree[yb], n_yf[yb] & 1);
+          ++n_yf[yb];
+        }
+        if (!ok) break;
+        fence_after();
+        const uint32_t qh_addr = smem_addr(stages + (r % RS) * SBYTES + D * TS * 4);
+        const uint32_t ql_addr = qh_addr + QTILE;
+        const uint32_t sbuf = tmem + (uint32_t)(b * NC);
+        const uint32_t yd = tmem + y_col + (uint32_t)(YN * yb);
+#pragma unroll
+        for (int ks = 0; ks < NC / 16; ++ks) {
+          const uint32_t qoff = (uint32_t)((NC / 8) * q + 2 * ks) * 128u;
+          const uint32_t pa = sbuf + (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
+          const int acc = (q > 0 || ks > 0) ? 1 : 0;
+          mma_ts(yd, pa, sdesc(qh_addr + qoff, QKC * 128), id_y, acc);
+          if (SPLIT) {
+            mma_ts(yd, pa + 16u, sdesc(qh_addr + qoff, QKC * 128), id_y, 1);
+            mma_ts(yd, pa, sdesc(ql_addr + qoff, QKC * 128), id_y, 1);
+          }
+        }
+        commit(&pdone[b]);
+        ++n_pd[b];
+        if (q == CPT - 1) commit(&yfull[yb]);
+      }
+      if (!ok) {
+        // stop the compute warps, and let every MMA issued complete before
+        // the tensor memory is released
+        abort_flag = 1;
+        commit(&dbar);
+        mbar_wait_bounded(&dbar, 0);
+      }
+    }
+    __syncwarp();  // the idle lanes wait for the issuing lane before the block barrier
+  } else {
+    // ================= compute warps: exponentials, the B operands, Y folds
+    if (tid == 0)
+      for (; issued < min(RS, nt); ++issued) issue(issued);
+    constexpr int YW = YN / 2;  // Y columns per warpgroup
+    float Ssum[YW], Scomp[YW];
+#pragma unroll
+    for (int c = 0; c < YW; ++c) Ssum[c] = Scomp[c] = 0.f;
+    uint32_t n_sf[NBUF] = {0, 0, 0}, n_yfl[2] = {0, 0};
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+    // tile r's B operand into buffer r & 1 (its stage awaited first)
+    auto make_b = [&](int r) -> bool {
+      if (!__all_sync(0xffffffffu, wait(&bars[r % RS], (r / RS) & 1))) return false;
+      const float* rs = reinterpret_cast<const float*>(stages + (r % RS) * SBYTES);
+      unsigned char* bdst = sB + (r & 1) * BBYTES;
+      const int j = tid;  // one source per thread: its K-vector as 16-byte rows
+      float bh[W], bl[W];
+      float bb = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float xh = p.s * (rs[k * TS + j] - ctr[k]);
+        bb = fmaf(-xh, xh, bb);
+        const float v = 2.f * xh;
+        bh[k] = H::to(H::from(v));
+        bl[k] = v - bh[k];
+      }
+      if (bb < -30000.f) {  // farther than any target can see: contributes 0
+#pragma unroll
+        for (int k = 0; k < D; ++k) bh[k] = bl[k] = 0.f;
+        bb = -30000.f;
+      }
+      bh[D] = H::to(H::from(bb));
+      bl[D] = bb - bh[D];
+#pragma unroll
+      for (int kc = 0; kc < KC; ++kc) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          w[e] = H::pack(kv_value<D>(bh, bl, 8 * kc + 2 * e, false), kv_value<D>(bh, bl, 8 * kc + 2 * e + 1, false));
+        *reinterpret_cast<uint4*>(bdst + kmaj(j, 8 * kc, KC)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&bready[r & 1]);
+      return true;
+    };
+    bool ok = nt > 0 ? make_b(0) : true;
+    for (int r = 0; r < nt && ok; ++r) {
+      for (int q = 0; q < CPT && ok; ++q) {
+        const int c = r * CPT + q, b = c % NBUF;
+        ok = __all_sync(0xffffffffu, wait(&sfull[b], n_sf[b] & 1));
+        ++n_sf[b];
+        if (!ok) break;
+        fence_after();
+        // P = 2^S over this warpgroup's 32 columns: hi in the first 16, lo in
+        // the last 16 (each thread reads its values before overwriting them)
+        const uint32_t cols = tmem + (uint32_t)(b * NC) + lanes + (uint32_t)(32 * wg);
+        uint32_t v[32];
+        ld32(cols, v);
+        wait_ld();
+        uint32_t ph[16], pl[16];
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+          const float p0 = ex2(__uint_as_float(v[2 * w])), p1 = ex2(__uint_as_float(v[2 * w + 1]));
+          ph[w] = H::pack(p0, p1);
+          if (SPLIT) {
+            const float2 hv = H::unpack(ph[w]);
+            pl[w] = H::pack(p0 - hv.x, p1 - hv.y);
+          }
+        }
+        st16(cols, ph);
+        if (SPLIT) st16(cols + 16u, pl);
+        wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&pfull[b]);
+      }
+      if (!ok) break;
+      // the next tile's B (its buffer was last read by tile r - 1's exponent
+      // MMAs, complete since tile r - 1's Y was awaited)
+      if (r + 1 < nt) {
+        ok = make_b(r + 1);
+        if (!ok) break;
+      }
+      // ---- the tile's Y: fold into Kahan sums, then hand Y and the stage back
+      const int yb = r & 1;
+      ok = __all_sync(0xffffffffu, wait(&yfull[yb], n_yfl[yb] & 1));
+      ++n_yfl[yb];
+      if (!ok) break;
+      fence_after();
+      uint32_t yv[8];
+      ld8(tmem + y_col + (uint32_t)(YN * yb) + lanes + (uint32_t)(YW * wg), yv);
+      wait_ld();
+#pragma unroll
+      for (int c = 0; c < YW; ++c) kahan_add(Ssum[c], Scomp[c], __uint_as_float(yv[c]));
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&yfree[yb]);
+      if (tid == 0 && r + RS < nt) {  // every MMA of tile r is complete: its stage is free
+        fence_proxy_async_smem();
+        issue(r + RS);
+        ++issued;
+      }
+    }
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    } else if (i < p.Nt_pad) {
+#pragma unroll
+      for (int c = 0; c < YW; ++c) {
+        const int col = YW * wg + c;
+        if (col < p.m) p.part[((int64_t)blockIdx.y * p.m + col) * p.Nt_pad + i] = (double)Ssum[c] - (double)Scomp[c];
+      }
+    }
+  }
+  __syncthreads();
+  if (abort_flag) {
+    // drain (bounded): copies in flight before the shared memory is released
+    if (tid == 0)
+      for (int rr = 0; rr < issued; ++rr) mbar_wait_bounded(&bars[rr % RS], (rr / RS) & 1);
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// Weights Q (m columns, stride ld, sorted, zero padded) -> per source tile a
+// 16 x 256 K-major f16 tile (core matrices 8 rows x 16 B): hi, and lo = the
+// float32 remainder when split; rows m..15 zero.  One thread per 8 sources of
+// one row (16-byte stores).
+template <bool BF>
+__global__ void q_split_kernel(const float* __restrict__ Q, int m, int64_t ld, int64_t ntiles,
+                               uint16_t* __restrict__ qh, uint16_t* __restrict__ ql, const int* active) {
+  using H = Half<BF>;
+  if (active && *active == 0) return;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ntiles * 512) return;
+  const int64_t tile = e >> 9;
+  const int w = (int)(e & 511);
+  const int c = (w & 7) + 8 * ((w >> 3) & 1);  // row (column of Y)
+  const int seg = w >> 4;                      // 8 sources
+  uint32_t h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+  if (c < m) {
+    const float* src = Q + (int64_t)c * ld + tile * TS + 8 * seg;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float v0 = src[2 * k], v1 = src[2 * k + 1];
+      h[k] = H::pack(v0, v1);
+      const float2 hv = H::unpack(h[k]);
+      if (ql) l[k] = H::pack(v0 - hv.x, v1 - hv.y);
+    }
+  }
+  const int64_t off = tile * (int64_t)(umma::YN * TS) + (int64_t)(umma::kmaj(c, 8 * seg, TS / 8) >> 1);
+  *reinterpret_cast<uint4*>(qh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  if (ql) *reinterpret_cast<uint4*>(ql + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int D, bool SPLIT, bool BF>
+cudaError_t umma_launch_typed(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+  const size_t shm = umma::smem_bytes<D>(SPLIT);
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(mvp_umma_kernel<D, SPLIT, BF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e) return e;
+    done[dev] = true;
+  }
+  if (dry) return cudaSuccess;
+  dim3 grid((unsigned)(2 * p.nblk), (unsigned)splits);
+  mvp_umma_kernel<D, SPLIT, BF><<<grid, umma::THREADS + 32, shm, st>>>(p); count_launch();
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t umma_dispatch(const TcParams& p, int splits, bool split, bool bf, cudaStream_t st, bool dry) {
+  if (split) return umma_launch_typed<D, true, false>(p, splits, st, dry);
+  return bf ? umma_launch_typed<D, false, true>(p, splits, st, dry)
+            : umma_launch_typed<D, false, false>(p, splits, st, dry);
+}
+
 constexpr int TCX_MT = 4;
 
 template <int D>
@@ -794,6 +1298,60 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
     case 6: return tcx_launch_typed<6>(p, splits, st, dry);
     case 7: return tcx_launch_typed<7>(p, splits, st, dry);
     case 8: return tcx_launch_typed<8>(p, splits, st, dry);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t mvp_umma_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
+                              bool split, bool bf, int splits, int tiles_per_split, double* part,
+                              float* fac, const int* active, cudaStream_t st, bool dry) {
+  if (m < 1 || m > umma::YN) return cudaErrorNotSupported;
+  // the weights pre-split per source tile (workspace sized here, also in a
+  // dry run, so that a captured launch allocates nothing)
+  const int64_t ntiles = S.Npad / TS;
+  void *qh = nullptr, *ql = nullptr;
+  cudaError_t e = c.ws.get("umma.qh", sizeof(uint16_t) * umma::YN * TS * (size_t)ntiles, &qh);
+  if (!e && split) e = c.ws.get("umma.ql", sizeof(uint16_t) * umma::YN * TS * (size_t)ntiles, &ql);
+  if (e) return e;
+  if (!dry) {
+    const unsigned blocks = (unsigned)((ntiles * 512 + 255) / 256);
+    if (bf) q_split_kernel<true><<<blocks, 256, 0, st>>>(Q, m, S.Npad, ntiles, (uint16_t*)qh, nullptr, active);
+    else q_split_kernel<false><<<blocks, 256, 0, st>>>(Q, m, S.Npad, ntiles, (uint16_t*)qh,
+                                                       split ? (uint16_t*)ql : nullptr, active);
+    count_launch();
+    if ((e = cudaGetLastError())) return e;
+  }
+  TcParams p{};
+  p.qh_tiles = (const uint16_t*)qh;
+  p.ql_tiles = (const uint16_t*)ql;
+  p.xt = T.xs;
+  p.Nt = T.N;
+  p.Nt_pad = T.Npad;
+  p.tctr = T.sb_ctr;
+  p.torder = T.sb_order;
+  p.tn_exp = T.sb_nexp;
+  p.nblk = std::max<int64_t>(1, T.h_sb_nexp);
+  p.WB = SB;
+  p.xs = S.xs;
+  p.Q = Q;
+  p.Ns_pad = S.Npad;
+  p.m = m;
+  p.ntiles = (int)(S.Npad / TS);
+  p.tiles_per_split = tiles_per_split;
+  p.part = part;
+  p.fac = fac;
+  p.err = c.d_err;
+  p.s = S.scale;
+  p.active = active;
+  switch (T.d) {
+    case 1: return umma_dispatch<1>(p, splits, split, bf, st, dry);
+    case 2: return umma_dispatch<2>(p, splits, split, bf, st, dry);
+    case 3: return umma_dispatch<3>(p, splits, split, bf, st, dry);
+    case 4: return umma_dispatch<4>(p, splits, split, bf, st, dry);
+    case 5: return umma_dispatch<5>(p, splits, split, bf, st, dry);
+    case 6: return umma_dispatch<6>(p, splits, split, bf, st, dry);
+    case 7: return umma_dispatch<7>(p, splits, split, bf, st, dry);
+    case 8: return umma_dispatch<8>(p, splits, split, bf, st, dry);
     default: return cudaErrorNotSupported;
   }
 }

@@ -206,3 +206,30 @@ def test_mvp_multi_rhs_direct_form_blocks(K, oracle_mod, m, d, sigma, normal):
     Y = K.krr_kernel_mvp(_dev(X), _dev(Q), sigma, 1e-2).cpu().numpy()
     for c in range(m):
         assert scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-2) <= TOL_FP32, c
+
+
+@pytest.mark.parametrize("m,d,prec,bound", [(16, 3, "fp32", TOL_FP32), (5, 2, "fp32", TOL_FP32),
+                                            (16, 8, "fp32", TOL_FP32), (16, 3, "fp16", 2e-3),
+                                            (7, 2, "bf16", 2e-2)])
+def test_mvp_multi_rhs_tcgen05_kernel(K, oracle_mod, m, d, prec, bound):
+    # the multi-column tensor-core product on the tcgen05 / tensor-memory
+    # kernel (handle option): same bar as the default mma.sync kernel
+    rng = np.random.default_rng(300 + m + d)
+    N = 6000
+    X = rng.random((N, d)).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    sigma = 0.08 if d <= 3 else 0.5
+    h = K.Handle()
+    try:
+        K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h)
+        Y = K.krr_kernel_mvp(_dev(X), _dev(Q), sigma, 1e-3, prec=prec, handle=h).cpu().numpy()
+    finally:
+        h.close()
+    for c in range(m):
+        assert scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-3) <= bound, c
+
+
+def test_set_option_rejects_unknown(K):
+    with pytest.raises(K.KrrError) as ei:
+        K.krr_set_option(99, 1)
+    assert ei.value.status == K.KRR_ERR_INVALID_ARG
