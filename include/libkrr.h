@@ -38,6 +38,11 @@
  *             Scalar outputs (gradients of krr_mll_grad) are HOST pointers.
  * Limits:     1 <= d <= 64; N >= 1 (N = 0 returns KRR_OK with no work);
  *             sigma > 0; shifts (gamma, delta) >= 0; all finite.
+ * Dimension:  up to 8 the kernels are specialised per d and compact target
+ *             blocks use the expanded exponent form (tensor cores where it
+ *             pays); above 8 the coordinates are held padded with zeros to 16,
+ *             32, 48 or 64 and every pair takes the direct form (exact
+ *             differences on the CUDA cores).
  */
 #ifndef LIBKRR_H
 #define LIBKRR_H

@@ -33,9 +33,15 @@ struct Workspace {
 // (T targets per thread).  prep.cu computes, per warp block, the centre of its
 // bounding box and whether it is compact enough for the expanded exponent
 // form, and orders the blocks so that the expanded ones come first.
+// Coordinates per point in the prepared layout: d itself up to 8, else d
+// rounded up to 16, 32, 48 or 64 with zero coordinates (which leave every
+// distance unchanged).  Above 8 every block takes the direct form.
+inline int padded_dim(int d) { return d <= 8 ? d : (int)round_up(d, 16); }
+
 struct PointsDev {
   int64_t N = 0, Npad = 0;
-  int d = 0;
+  int d = 0;            // prepared coordinates per point (padded_dim of d_in)
+  int d_in = 0;         // the caller's dimension
   float scale = 0.f;    // s = sqrt(log2(e) / (2 sigma^2))
   double s2 = 0.0;      // s^2 = log2(e) / (2 sigma^2) in double
   float* xs = nullptr;  // tile-blocked SoA of the raw coordinates, Npad*d floats

@@ -121,7 +121,6 @@ krr_status check_points(Ctx& c, const char* fn, const float* X, int64_t N, int d
   if (!(sigma > 0.f) || !std::isfinite(sigma))
     return set_error(c, KRR_ERR_INVALID_ARG, "%s: sigma must be finite and > 0", fn);
   if (N > 0 && X == nullptr) return set_error(c, KRR_ERR_INVALID_ARG, "%s: X is NULL", fn);
-  if (d > 8) return set_error(c, KRR_ERR_UNIMPLEMENTED, "%s: d = %d > 8 not built yet", fn, d);
   return KRR_OK;
 }
 

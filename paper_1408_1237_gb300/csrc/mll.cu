@@ -86,27 +86,39 @@ __global__ void weights_kernel(const double* __restrict__ Sol, const float* __re
 
 constexpr int ADJ_NT = 256;   // threads: one target each
 constexpr int ADJ_RS = 2;     // raw stages
-constexpr int ADJ_MC = 4;     // weight columns per pass
 
-// Adjoint sums for ADJ_MC weight columns starting at c0: for target i,
-// out[(c * (D+1) + k) * Np + i] (k < D) = sum_j Phi_ij b_cj (x_ik - x_jk) and
-// out[(c * (D+1) + D) * Np + i] = sum_j Phi_ij b_cj r_ij^2, over this split's
-// source tiles; float32 per tile, Kahan-folded, FP64 partial per split.
+// Weight columns per pass and dimensions per pass: up to 8 dimensions all in
+// one pass with 4 columns; above 8, passes over 8-dimension chunks with 2
+// columns (each pass forms the full distance again).
 template <int D>
-__global__ void __launch_bounds__(ADJ_NT) adjoint_kernel(const float* __restrict__ xs, int64_t N,
-                                                          int64_t Np, const float* __restrict__ WC,
-                                                          int c0, int mcols, float s2,
-                                                          int tiles_per_split, int ntiles,
-                                                          double* __restrict__ out,
-                                                          int64_t split_stride, int* err) {
-  constexpr int NO = ADJ_MC * (D + 1);
-  constexpr int RAW = (D + ADJ_MC) * TS;
-  __shared__ __align__(128) float raw[ADJ_RS][RAW];
+constexpr int adj_mc() { return D <= 8 ? 4 : 2; }
+template <int D>
+constexpr int adj_dc() { return D <= 8 ? D : 8; }
+template <int D>
+constexpr size_t adj_smem() { return sizeof(float) * ADJ_RS * (D + adj_mc<D>()) * TS; }
+
+// Adjoint sums for adj_mc weight columns starting at c0 and the dimensions
+// k0 .. k0 + adj_dc - 1: for target i, out[(c * (D+1) + k) * Np + i] =
+// sum_j Phi_ij b_cj (x_ik - x_jk), and (pass k0 = 0) out[(c * (D+1) + D) *
+// Np + i] = sum_j Phi_ij b_cj r_ij^2, over this split's source tiles; float32
+// per tile, Kahan-folded, FP64 partial per split.
+template <int D>
+__global__ void __launch_bounds__(ADJ_NT)
+    adjoint_kernel(const float* __restrict__ xs, int64_t N, int64_t Np, const float* __restrict__ WC,
+                   int c0, int mcols, float s2, int tiles_per_split, int ntiles,
+                   double* __restrict__ out, int64_t split_stride, int* err, int k0) {
+  constexpr int MC = adj_mc<D>();
+  constexpr int DC = adj_dc<D>();
+  constexpr int NO = MC * (DC + 1);
+  constexpr int RAW = (D + MC) * TS;
+  extern __shared__ __align__(128) float raw_dyn[];
   __shared__ __align__(8) uint64_t bars[ADJ_RS];
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t i = (int64_t)blockIdx.x * ADJ_NT + tid;
   const int64_t ii = i < N ? i : N - 1;
+  const bool with_r2 = k0 == 0;
+  const int kc = k0 / DC;  // this pass's chunk of dimensions
   float xi[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) xi[k] = xs[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
@@ -118,12 +130,12 @@ __global__ void __launch_bounds__(ADJ_NT) adjoint_kernel(const float* __restrict
   auto issue = [&](int r) {
     const int stage = r % ADJ_RS;
     const int64_t tile = t_begin + r;
+    float* dst = raw_dyn + stage * RAW;
     mbar_arrive_expect_tx(&bars[stage], RAW * 4);
-    bulk_g2s(raw[stage], xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
-    for (int c = 0; c < ADJ_MC; ++c) {
+    bulk_g2s(dst, xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    for (int c = 0; c < MC; ++c) {
       const int cc = c0 + (c < mcols ? c : 0);  // unused slots reload column c0 (weights ignored)
-      bulk_g2s(raw[stage] + (D + c) * TS, WC + (int64_t)cc * Np + tile * (int64_t)TS, TS * 4,
-               &bars[stage]);
+      bulk_g2s(dst + (D + c) * TS, WC + (int64_t)cc * Np + tile * (int64_t)TS, TS * 4, &bars[stage]);
     }
   };
   if (tid == 0) {
@@ -141,22 +153,26 @@ __global__ void __launch_bounds__(ADJ_NT) adjoint_kernel(const float* __restrict
       abort_flag = 1;
       if (lane == 0) atomicExch(err, DEV_TIMEOUT);
     } else {
-      const float* rs = raw[r % ADJ_RS];
+      const float* rs = raw_dyn + (r % ADJ_RS) * RAW;
       for (int j = 0; j < TS; ++j) {
-        float dk[D];
+        // full distance, and the differences of this pass's dimensions (kept
+        // at compile-time register indices: chunk kc of 8 selected at run time)
         float r2 = 0.f;
+        float dc[DC];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          dk[k] = xi[k] - rs[k * TS + j];
-          r2 = fmaf(dk[k], dk[k], r2);
+          const float dk = xi[k] - rs[k * TS + j];
+          r2 = fmaf(dk, dk, r2);
+          if (DC == D) dc[k % DC] = dk;
+          else if (k / DC == kc) dc[k % DC] = dk;
         }
         const float phi = ex2(-s2 * r2);
 #pragma unroll
-        for (int c = 0; c < ADJ_MC; ++c) {
+        for (int c = 0; c < MC; ++c) {
           const float w = (c < mcols) ? phi * rs[(D + c) * TS + j] : 0.f;
 #pragma unroll
-          for (int k = 0; k < D; ++k) acc[c * (D + 1) + k] = fmaf(w, dk[k], acc[c * (D + 1) + k]);
-          acc[c * (D + 1) + D] = fmaf(w, r2, acc[c * (D + 1) + D]);
+          for (int k = 0; k < DC; ++k) acc[c * (DC + 1) + k] = fmaf(w, dc[k], acc[c * (DC + 1) + k]);
+          acc[c * (DC + 1) + DC] = fmaf(w, r2, acc[c * (DC + 1) + DC]);
         }
       }
 #pragma unroll
@@ -182,12 +198,16 @@ __global__ void __launch_bounds__(ADJ_NT) adjoint_kernel(const float* __restrict
   if (i < N) {
     double* o = out + (int64_t)blockIdx.y * split_stride;
 #pragma unroll
-    for (int c = 0; c < ADJ_MC; ++c) {
+    for (int c = 0; c < MC; ++c) {
       if (c >= mcols) break;
 #pragma unroll
-      for (int k = 0; k <= D; ++k)
-        o[((int64_t)(c0 + c) * (D + 1) + k) * Np + i] =
-            (double)S[c * (D + 1) + k] - (double)C[c * (D + 1) + k];
+      for (int k = 0; k < DC; ++k)
+        if (k0 + k < D)
+          o[((int64_t)(c0 + c) * (D + 1) + k0 + k) * Np + i] =
+              (double)S[c * (DC + 1) + k] - (double)C[c * (DC + 1) + k];
+      if (with_r2)
+        o[((int64_t)(c0 + c) * (D + 1) + D) * Np + i] =
+            (double)S[c * (DC + 1) + DC] - (double)C[c * (DC + 1) + DC];
     }
   }
 }
@@ -202,7 +222,7 @@ struct GradAcc {
 // copies of the (2P+1)(d+1) output columns.
 __global__ void combine_kernel(const double* __restrict__ A, int splits, int64_t split_stride,
                                const float* __restrict__ WC, const int* __restrict__ perm,
-                               int64_t N, int64_t Np, int d, int P, double inv_s2,
+                               int64_t N, int64_t Np, int d, int d_out, int P, double inv_s2,
                                float* __restrict__ dX, double* partials, GradAcc* acc) {
   __shared__ double red[8];
   __shared__ bool is_last;
@@ -228,7 +248,7 @@ __global__ void combine_kernel(const double* __restrict__ A, int splits, int64_t
       }
     }
     const int64_t oi = perm[i];
-    for (int k = 0; k < d; ++k) dX[oi * d + k] = (float)(-G[k] * inv_s2);
+    for (int k = 0; k < d_out; ++k) dX[oi * d_out + k] = (float)(-G[k] * inv_s2);
     h_loc += H;
     const double al = WC[i];
     aa_loc += al * al;
@@ -265,15 +285,27 @@ template <int D>
 cudaError_t launch_adjoint(const PointsDev& Pt, const float* WC, int ncols, int splits,
                            int tiles_per_split, double* out, int64_t split_stride, int* err,
                            cudaStream_t st) {
+  constexpr int MC = adj_mc<D>(), DC = adj_dc<D>();
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)adj_smem<D>());
+    if (e) return e;
+    done[dev] = true;
+  }
   const dim3 grid((unsigned)((Pt.N + ADJ_NT - 1) / ADJ_NT), (unsigned)splits);
   const float s2 = (float)Pt.s2;
-  for (int c0 = 0; c0 < ncols; c0 += ADJ_MC) {
-    adjoint_kernel<D><<<grid, ADJ_NT, 0, st>>>(Pt.xs, Pt.N, Pt.Npad, WC, c0,
-                                              std::min(ADJ_MC, ncols - c0), s2, tiles_per_split,
-                                              (int)(Pt.Npad / TS), out, split_stride, err); count_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e) return e;
-  }
+  for (int c0 = 0; c0 < ncols; c0 += MC)
+    for (int k0 = 0; k0 < D; k0 += DC) {
+      adjoint_kernel<D><<<grid, ADJ_NT, adj_smem<D>(), st>>>(Pt.xs, Pt.N, Pt.Npad, WC, c0,
+                                                             std::min(MC, ncols - c0), s2, tiles_per_split,
+                                                             (int)(Pt.Npad / TS), out, split_stride, err, k0);
+      count_launch();
+      cudaError_t e = cudaGetLastError();
+      if (e) return e;
+    }
   return cudaSuccess;
 }
 
@@ -331,7 +363,7 @@ extern "C" krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int 
   int splits = (int)std::min<int64_t>(ntiles, std::max<int64_t>(1, (2LL * c.num_sms + ctas - 1) / ctas));
   const int tps = (ntiles + splits - 1) / splits;
   splits = (ntiles + tps - 1) / tps;
-  const int64_t split_stride = (int64_t)ncols * (d + 1) * Pt.Npad;
+  const int64_t split_stride = (int64_t)ncols * (Pt.d + 1) * Pt.Npad;  // prepared (padded) dimension
   void *WCv, *Av, *partv, *accv;
   if ((e = c.ws.get("mll.wc", sizeof(float) * (size_t)ncols * Pt.Npad, &WCv))) return cuda_error(c, e, fn);
   if ((e = c.ws.get("mll.adj", sizeof(double) * (size_t)splits * split_stride, &Av))) return cuda_error(c, e, fn);
@@ -343,7 +375,7 @@ extern "C" krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int 
   double* A = (double*)Av;
   const unsigned pb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Pt.Npad + 255) / 256, 1024));
   weights_kernel<<<pb, 256, 0, st>>>(Sol, B, Pt.perm, N, Pt.Npad, P, WC); count_launch();
-  switch (d) {
+  switch (Pt.d) {
     case 1: e = launch_adjoint<1>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
     case 2: e = launch_adjoint<2>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
     case 3: e = launch_adjoint<3>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
@@ -351,7 +383,12 @@ extern "C" krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int 
     case 5: e = launch_adjoint<5>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
     case 6: e = launch_adjoint<6>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
     case 7: e = launch_adjoint<7>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
-    default: e = launch_adjoint<8>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
+    case 8: e = launch_adjoint<8>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
+    case 16: e = launch_adjoint<16>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
+    case 32: e = launch_adjoint<32>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
+    case 48: e = launch_adjoint<48>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
+    case 64: e = launch_adjoint<64>(Pt, WC, ncols, splits, tps, A, split_stride, c.d_err, st); break;
+    default: e = cudaErrorNotSupported; break;
   }
   if (e) return cuda_error(c, e, fn);
   const double inv_s2 = 1.0 / ((double)sigma * (double)sigma);
@@ -361,7 +398,7 @@ extern "C" krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int 
     if ((e = c.ws.get("mll.dxdummy", sizeof(float) * (size_t)N * d, &dummy))) return cuda_error(c, e, fn);
     dXout = (float*)dummy;
   }
-  combine_kernel<<<pb, 256, 0, st>>>(A, splits, split_stride, WC, Pt.perm, N, Pt.Npad, d, P,
+  combine_kernel<<<pb, 256, 0, st>>>(A, splits, split_stride, WC, Pt.perm, N, Pt.Npad, Pt.d, d, P,
                                      inv_s2, dXout, (double*)partv, (GradAcc*)accv); count_launch();
   GradAcc ha;
   if ((e = cudaMemcpyAsync(&ha, accv, sizeof(GradAcc), cudaMemcpyDeviceToHost, st))) return cuda_error(c, e, fn);

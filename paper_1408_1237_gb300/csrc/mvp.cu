@@ -302,14 +302,20 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
 // m..MC-1 of every stage are zero.  Per-tile float32 sums fold with Kahan
 // compensation into one FP64 partial per (split, column, target).
 template <int D, int MC>
-constexpr size_t dirm_smem_bytes() {
-  return sizeof(float) * 3 * (D + MC) * TS;
+constexpr int dirm_stages() {
+  return sizeof(float) * 3 * (D + MC) * TS <= 160 * 1024 ? 3 : 2;
 }
 
 template <int D, int MC>
-__global__ void __launch_bounds__(NT, 2) mvp_dirm_kernel(const MvpParams p, const float* __restrict__ Q,
-                                                         int64_t q_stride, int m, int T, int64_t slot0) {
-  constexpr int RS = 3;
+constexpr size_t dirm_smem_bytes() {
+  return sizeof(float) * dirm_stages<D, MC>() * (D + MC) * TS;
+}
+
+// (high-dimensional instances hold D coordinates per thread: one CTA per SM)
+template <int D, int MC>
+__global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_dirm_kernel(const MvpParams p, const float* __restrict__ Q,
+                                                                      int64_t q_stride, int m, int T, int64_t slot0) {
+  constexpr int RS = dirm_stages<D, MC>();
   constexpr uint32_t kStage = (D + MC) * TS;
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t bars[RS];
@@ -646,6 +652,10 @@ cudaError_t dirm_dispatch(const MvpParams& p, int d, const float* Q, int64_t q_s
     case 6: return dirm_typed<6>(p, Q, q_stride, m, T, slot0, pl, st, launch);
     case 7: return dirm_typed<7>(p, Q, q_stride, m, T, slot0, pl, st, launch);
     case 8: return dirm_typed<8>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 16: return dirm_typed<16>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 32: return dirm_typed<32>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 48: return dirm_typed<48>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 64: return dirm_typed<64>(p, Q, q_stride, m, T, slot0, pl, st, launch);
     default: return cudaErrorNotSupported;
   }
 }
@@ -687,6 +697,19 @@ Plan tcx_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
                    c.plan_slots > 0 ? c.plan_slots : 4 * c.num_sms);
 }
 
+// Buffers every product path uses: the factored scale and the dot scratch.
+cudaError_t common_reserve(Ctx& c, const PointsDev& Tp, cudaStream_t st) {
+  void* v;
+  cudaError_t e;
+  const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
+  if ((e = c.ws.get("mvp.fac", sizeof(float) * (size_t)Tp.Npad, &v))) return e;
+  if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &v))) return e;
+  const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
+  if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
+  if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 int mvp_targets_per_thread(int d, int64_t N) {
@@ -698,7 +721,8 @@ int mvp_targets_per_thread(int d, int64_t N) {
 
 cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
-  if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
+  if (Tp.d > 8) return mvp_multi_reserve(c, Tp, Sp, 1, KRR_FP32, st);  // direct form, one column
+  if (Tp.d < 1) return cudaErrorNotSupported;
   const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
   void* v;
   cudaError_t e;
@@ -835,7 +859,7 @@ cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const flo
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
                        const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                        cudaStream_t st) {
-  if (prec != KRR_FP32) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
+  if (prec != KRR_FP32 || Tp.d > 8) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
   if (Tp.N == 0) return cudaSuccess;
   if (use_tcx(c, Tp)) return tcx_path(c, Tp, Sp, q, qdiag, shift, o, st);
   MvpParams p{};
@@ -914,7 +938,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
                               krr_precision prec, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
   if (m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
-  cudaError_t e = mvp_reserve(c, Tp, Sp, st);
+  cudaError_t e = Tp.d > 8 ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
   void* v;
@@ -923,6 +947,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   MvpParams p{};
   p.nblk = Tp.nsb;
   if ((e = dirm_dispatch(p, Tp.d, nullptr, 0, m, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+  if (Tp.d > 8) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
   if (c.use_tcgen05)
     return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                              pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
@@ -934,7 +959,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
                              const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                              cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
-  if (Tp.d < 1 || Tp.d > 8 || m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
+  if (Tp.d < 1 || (Tp.d > 8 && Tp.d % 16) || Tp.d > 64 || m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
   MvpParams p{};
   p.xt = Tp.xs;
   p.Nt = Tp.N;
@@ -951,7 +976,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
   const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
-  cudaError_t e = mvp_reserve(c, Tp, Sp, st);
+  cudaError_t e = Tp.d > 8 ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   void *part, *partd, *fac, *dpart, *dcnt;
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);

@@ -176,19 +176,25 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
 #pragma unroll
     for (int c = 0; c < D; ++c) xi[u][c] = p.xs[(ii / TS) * (int64_t)D * TS + (int64_t)c * TS + ii % TS];
   }
-  float bc[D], bh[D];  // warp box: centre, half-width
+  // warp box (centre, half-width) for the near/far test; above 8
+  // dimensions every tile is treated as near (no box registers)
+  constexpr bool BOX = D <= 8;
+  constexpr int DB = BOX ? D : 1;
+  float bc[DB], bh[DB];
+  if constexpr (BOX) {
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    float lo = xi[0][c], hi = xi[0][c];
+    for (int c = 0; c < D; ++c) {
+      float lo = xi[0][c], hi = xi[0][c];
 #pragma unroll
-    for (int u = 1; u < TA; ++u) {
-      lo = fminf(lo, xi[u][c]);
-      hi = fmaxf(hi, xi[u][c]);
+      for (int u = 1; u < TA; ++u) {
+        lo = fminf(lo, xi[u][c]);
+        hi = fmaxf(hi, xi[u][c]);
+      }
+      lo = warp_min(lo);
+      hi = warp_max(hi);
+      bc[c] = 0.5f * (lo + hi);
+      bh[c] = 0.5f * (hi - lo);
     }
-    lo = warp_min(lo);
-    hi = warp_max(hi);
-    bc[c] = 0.5f * (lo + hi);
-    bh[c] = 0.5f * (hi - lo);
   }
 
   const int t_begin = blockIdx.y * p.tiles_per_split;
@@ -232,12 +238,14 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
       const float* sq = st + D * TS;
       const float* sl = st + (D + 1) * TS;
       // near/far test of this warp's box against the tile's box
-      const float* tb = p.tbox + (int64_t)(t_begin + r) * 2 * D;
       float dist2 = 0.f;
+      if constexpr (BOX) {
+        const float* tb = p.tbox + (int64_t)(t_begin + r) * 2 * D;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const float g = fmaxf(0.f, fabsf(bc[c] - tb[c]) - bh[c] - tb[D + c]);
-        dist2 = fmaf(g, g, dist2);
+        for (int c = 0; c < D; ++c) {
+          const float g = fmaxf(0.f, fabsf(bc[c] - tb[c]) - bh[c] - tb[D + c]);
+          dist2 = fmaf(g, g, dist2);
+        }
       }
       if (s2h * dist2 <= FAR_E) {
 #pragma unroll 2
@@ -296,7 +304,7 @@ constexpr size_t accm_smem_bytes() {
 }
 
 template <int D>
-__global__ void __launch_bounds__(NT, 2) mvp_accm_kernel(const AccParams p, int m) {
+__global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_accm_kernel(const AccParams p, int m) {
   constexpr uint32_t kStage = (D + 2 * AM) * TS;
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t bars[RSM];
@@ -330,12 +338,16 @@ __global__ void __launch_bounds__(NT, 2) mvp_accm_kernel(const AccParams p, int 
   float xi[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) xi[k] = p.xs[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
-  float bc[D], bh[D];  // warp box: centre, half-width
+  constexpr bool BOX = D <= 8;  // near/far test (above 8 dimensions: all near)
+  constexpr int DB = BOX ? D : 1;
+  float bc[DB], bh[DB];
+  if constexpr (BOX) {
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float lo = warp_min(xi[k]), hi = warp_max(xi[k]);
-    bc[k] = 0.5f * (lo + hi);
-    bh[k] = 0.5f * (hi - lo);
+    for (int k = 0; k < D; ++k) {
+      const float lo = warp_min(xi[k]), hi = warp_max(xi[k]);
+      bc[k] = 0.5f * (lo + hi);
+      bh[k] = 0.5f * (hi - lo);
+    }
   }
 
   const int t_begin = blockIdx.y * p.tiles_per_split;
@@ -381,12 +393,14 @@ __global__ void __launch_bounds__(NT, 2) mvp_accm_kernel(const AccParams p, int 
       const float* st = smem + (r % RSM) * kStage;
       const float* sq = st + D * TS;
       const float* sl = st + (D + AM) * TS;
-      const float* tb = p.tbox + (int64_t)(t_begin + r) * 2 * D;
       float dist2 = 0.f;
+      if constexpr (BOX) {
+        const float* tb = p.tbox + (int64_t)(t_begin + r) * 2 * D;
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float g = fmaxf(0.f, fabsf(bc[k] - tb[k]) - bh[k] - tb[D + k]);
-        dist2 = fmaf(g, g, dist2);
+        for (int k = 0; k < D; ++k) {
+          const float g = fmaxf(0.f, fabsf(bc[k] - tb[k]) - bh[k] - tb[D + k]);
+          dist2 = fmaf(g, g, dist2);
+        }
       }
       if (s2h * dist2 <= FAR_E) {
 #pragma unroll 1
@@ -550,6 +564,10 @@ cudaError_t set_accm_attr(int d) {
     case 6: return accm_attr_typed<6>();
     case 7: return accm_attr_typed<7>();
     case 8: return accm_attr_typed<8>();
+    case 16: return accm_attr_typed<16>();
+    case 32: return accm_attr_typed<32>();
+    case 48: return accm_attr_typed<48>();
+    case 64: return accm_attr_typed<64>();
     default: return cudaErrorNotSupported;
   }
 }
@@ -573,6 +591,10 @@ cudaError_t launch_accm(const AccParams& p, int d, int splits, int ncols, cudaSt
     case 6: return launch_accm_typed<6>(p, splits, ncols, st);
     case 7: return launch_accm_typed<7>(p, splits, ncols, st);
     case 8: return launch_accm_typed<8>(p, splits, ncols, st);
+    case 16: return launch_accm_typed<16>(p, splits, ncols, st);
+    case 32: return launch_accm_typed<32>(p, splits, ncols, st);
+    case 48: return launch_accm_typed<48>(p, splits, ncols, st);
+    case 64: return launch_accm_typed<64>(p, splits, ncols, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -584,7 +606,7 @@ struct AccPlan {
 AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots, int ncols) {
   const int ntiles = (int)(P.Npad / TS);
   // one target per thread in the multi-column kernel, ACC_TA otherwise
-  const int ta = ncols > 1 ? 1 : ACC_TA;
+  const int ta = (ncols > 1 || P.d > 8) ? 1 : ACC_TA;
   const int64_t ctas = (P.N + NT * ta - 1) / (NT * ta);
   const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   // fill the GPU about four times over, never below one tile per split
@@ -619,6 +641,10 @@ cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int nco
     case 6: return set_acc_attr<6, ACC_TA>();
     case 7: return set_acc_attr<7, ACC_TA>();
     case 8: return set_acc_attr<8, ACC_TA>();
+    case 16: return set_acc_attr<16, 1>();
+    case 32: return set_acc_attr<32, 1>();
+    case 48: return set_acc_attr<48, 1>();
+    case 64: return set_acc_attr<64, 1>();
     default: return cudaErrorNotSupported;
   }
 }
@@ -665,6 +691,10 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
     case 6: e = launch_acc<6, ACC_TA>(p, pl.splits, ncols, st); break;
     case 7: e = launch_acc<7, ACC_TA>(p, pl.splits, ncols, st); break;
     case 8: e = launch_acc<8, ACC_TA>(p, pl.splits, ncols, st); break;
+    case 16: e = launch_acc<16, 1>(p, pl.splits, ncols, st); break;
+    case 32: e = launch_acc<32, 1>(p, pl.splits, ncols, st); break;
+    case 48: e = launch_acc<48, 1>(p, pl.splits, ncols, st); break;
+    case 64: e = launch_acc<64, 1>(p, pl.splits, ncols, st); break;
     default: return cudaErrorNotSupported;
   }
   if (e) return e;

@@ -169,14 +169,14 @@ __global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys_in,
 // Tile-blocked pack: xs[(i/TS)*d*TS + k*TS + i%TS] = X[perm[i]*d + k]; the
 // padded points i >= N repeat the last sorted point (their weights are zero),
 // so every coordinate the product kernels meet is finite and nearby.
-__global__ void pack_kernel(const float* __restrict__ X, int64_t N, int64_t Npad, int d,
+__global__ void pack_kernel(const float* __restrict__ X, int64_t N, int64_t Npad, int d_in, int d,
                             const int* __restrict__ perm, float* __restrict__ xs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Npad) return;
   const int64_t tile = i / TS, lane = i % TS;
   float* dst = xs + tile * (int64_t)d * TS + lane;
-  const int64_t src = (int64_t)perm[i < N ? i : N - 1] * d;
-  for (int k = 0; k < d; ++k) dst[(int64_t)k * TS] = X[src + k];
+  const int64_t src = (int64_t)perm[i < N ? i : N - 1] * d_in;
+  for (int k = 0; k < d; ++k) dst[(int64_t)k * TS] = k < d_in ? X[src + k] : 0.f;  // padding: 0
 }
 
 __global__ void gather_kernel(const float* __restrict__ in, int64_t N, int m,
@@ -200,7 +200,8 @@ __global__ void scatter_kernel(const float* __restrict__ in, int64_t Npad, int64
 // coordinates); flag = 1 when every valid point lies within squared radius
 // EXPANDED_R2 of the centre in scaled units s (x - c).
 __global__ void blkinfo_kernel(const float* __restrict__ xs, int64_t N, int d, int T, float s,
-                               int64_t nblk, float* __restrict__ ctr, int* __restrict__ flag) {
+                               int64_t nblk, float* __restrict__ ctr, int* __restrict__ flag,
+                               int allow_expanded) {
   const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= nblk) return;
@@ -233,7 +234,7 @@ __global__ void blkinfo_kernel(const float* __restrict__ xs, int64_t N, int d, i
     }
   }
   r2max = warp_max(r2max);
-  if (lane == 0) flag[b] = (r2max <= EXPANDED_R2) ? 1 : 0;
+  if (lane == 0) flag[b] = (allow_expanded && r2max <= EXPANDED_R2) ? 1 : 0;
 }
 
 // Stable partition of the warp blocks: expanded-form blocks first (one block
@@ -308,14 +309,18 @@ cudaError_t scatter_orig(const float* in, int64_t Npad, int64_t N, int m, const 
 cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma,
                            const char* tag, PointsDev& P, cudaStream_t st) {
   const std::string t(tag);
+  const int d_in = d;
+  d = padded_dim(d_in);
   P.N = N;
   P.d = d;
+  P.d_in = d_in;
   P.Npad = round_up(std::max<int64_t>(N, 1), PAD);
   P.s2 = 1.0 / (std::log(2.0) * 2.0 * (double)sigma * (double)sigma);  // log2(e) / (2 sigma^2)
   P.scale = (float)std::sqrt(P.s2);
   cudaError_t e;
   void *xs, *perm, *ka, *kb, *va, *vb, *hist, *bbp, *bb;
   const int nbb = (int)std::min<int64_t>(blocks_for(N, BBOX_THREADS), 256);
+  const int allow_expanded = d <= 8 ? 1 : 0;
   const int nchunks = (int)blocks_for(N, SORT_CHUNK);
   if ((e = c.ws.get(t + ".xs", sizeof(float) * P.Npad * d, &xs))) return e;
   if ((e = c.ws.get(t + ".perm", sizeof(int) * P.Npad, &perm))) return e;
@@ -324,17 +329,17 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   if ((e = c.ws.get("sort.va", sizeof(int) * N, &va))) return e;
   if ((e = c.ws.get("sort.vb", sizeof(int) * N, &vb))) return e;
   if ((e = c.ws.get("sort.hist", sizeof(uint32_t) * 256 * (size_t)nchunks, &hist))) return e;
-  if ((e = c.ws.get("sort.bbp", sizeof(float) * 2 * d * (size_t)nbb, &bbp))) return e;
-  if ((e = c.ws.get("sort.bb", sizeof(float) * 2 * d, &bb))) return e;
+  if ((e = c.ws.get("sort.bbp", sizeof(float) * 2 * d_in * (size_t)nbb, &bbp))) return e;
+  if ((e = c.ws.get("sort.bb", sizeof(float) * 2 * d_in, &bb))) return e;
   P.xs = (float*)xs;
   P.perm = (int*)perm;
 
-  bbox_partial_kernel<<<nbb, BBOX_THREADS, sizeof(float) * 2 * d * (BBOX_THREADS / 32), st>>>(
-      X, N, d, (float*)bbp, c.d_err); count_launch();
-  bbox_final_kernel<<<1, 128, 0, st>>>((const float*)bbp, nbb, d, (float*)bb); count_launch();
-  const int dk = std::min(d, 30);
+  bbox_partial_kernel<<<nbb, BBOX_THREADS, sizeof(float) * 2 * d_in * (BBOX_THREADS / 32), st>>>(
+      X, N, d_in, (float*)bbp, c.d_err); count_launch();
+  bbox_final_kernel<<<1, 128, 0, st>>>((const float*)bbp, nbb, d_in, (float*)bb); count_launch();
+  const int dk = std::min(d_in, 30);
   const int bits = std::max(1, std::min(16, 30 / dk));
-  morton_kernel<<<blocks_for(N, 256), 256, 0, st>>>(X, N, d, dk, bits, (const float*)bb,
+  morton_kernel<<<blocks_for(N, 256), 256, 0, st>>>(X, N, d_in, dk, bits, (const float*)bb,
                                                     (uint32_t*)ka, (int*)va); count_launch();
   const int key_bits = bits * dk;
   uint32_t *kin = (uint32_t*)ka, *kout = (uint32_t*)kb;
@@ -349,7 +354,7 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
     std::swap(vin, vout);
   }
   if ((e = cudaMemcpyAsync(P.perm, vin, sizeof(int) * N, cudaMemcpyDeviceToDevice, st))) return e;
-  pack_kernel<<<blocks_for(P.Npad, 256), 256, 0, st>>>(X, N, P.Npad, d, P.perm, P.xs); count_launch();
+  pack_kernel<<<blocks_for(P.Npad, 256), 256, 0, st>>>(X, N, P.Npad, d_in, d, P.perm, P.xs); count_launch();
 
   P.T = mvp_targets_per_thread(d, N);
   P.nblk = (N + 32 * P.T - 1) / (32 * P.T);
@@ -362,7 +367,7 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.order = (int*)order;
   P.n_exp = (int*)nexp;
   blkinfo_kernel<<<blocks_for(P.nblk, 8), 256, 0, st>>>(P.xs, N, d, P.T, P.scale, P.nblk, P.ctr,
-                                                       (int*)flag); count_launch();
+                                                       (int*)flag, allow_expanded); count_launch();
   order_kernel<<<1, SCAN_THREADS, 0, st>>>((const int*)flag, P.nblk, P.order, P.n_exp); count_launch();
   // super-blocks of SB targets (nsb <= nblk: the flag scratch fits)
   P.nsb = (N + SB - 1) / SB;
@@ -375,7 +380,7 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.sb_nexp = (int*)nexp;
   P.sb_flag = (int*)flag;
   blkinfo_kernel<<<blocks_for(P.nsb, 8), 256, 0, st>>>(P.xs, N, d, SB / 32, P.scale, P.nsb, P.sb_ctr,
-                                                       P.sb_flag); count_launch();
+                                                       P.sb_flag, allow_expanded); count_launch();
   order_kernel<<<1, SCAN_THREADS, 0, st>>>(P.sb_flag, P.nsb, P.sb_order, P.sb_nexp); count_launch();
   const int64_t ntiles = P.Npad / TS;
   void* tbox;

@@ -136,3 +136,16 @@ def test_fgmres_invalid_options(K):
             K.krr_fgmres_solve(_dev(p["X"]), _dev(p["b"]), p["sigma"], p["gamma"],
                                opts=K.default_opts(**kw))
         assert ei.value.status == K.KRR_ERR_INVALID_ARG
+
+
+def test_fgmres_high_dimension(K, oracle_mod):
+    # d = 20 (a dataset-like dimension; coordinates padded to 32 internally)
+    rng = np.random.default_rng(31)
+    N, d = 1500, 20
+    X = rng.random((N, d)).astype(np.float32)
+    b = (np.sin(3 * X[:, 0]) + X[:, 1] + 0.01 * rng.standard_normal(N)).astype(np.float32)
+    sigma, gamma = 0.3 * np.sqrt(d), 1e-2
+    opts = K.default_opts(delta=0.1, inner_tol=1e-2)
+    x, info = K.krr_fgmres_solve(_dev(X), _dev(b), sigma, gamma, opts=opts)
+    rel = _oracle_relres(oracle_mod, X, b, x.cpu().numpy(), sigma, gamma)
+    assert info[0]["status"] == K.KRR_OK and rel <= 1e-6, (rel, info)

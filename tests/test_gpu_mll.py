@@ -77,3 +77,23 @@ def test_autograd_surrogate_carries_the_gradient(K, oracle_mod):
     assert ls.grad.item() == pytest.approx(2.0 * gs, rel=1e-6)
     assert lg.grad.item() == pytest.approx(2.0 * gg, rel=1e-6)
     np.testing.assert_allclose(X.grad.cpu().numpy(), 2.0 * gX.cpu().numpy(), rtol=1e-6, atol=1e-12)
+
+
+def test_mll_grad_high_dimension(K, oracle_mod):
+    # d = 12: the adjoint sums run in passes over 8-dimension chunks
+    rng = np.random.default_rng(41)
+    N, d, P = 400, 12, 4
+    X = rng.random((N, d)).astype(np.float32)
+    y = (np.cos(2 * X[:, 0]) + X[:, 3] + 0.1 * rng.standard_normal(N)).astype(np.float32)
+    sigma, gamma, seed = 0.4 * np.sqrt(d / 3.0), 0.05, 77
+    opts = K.default_opts(tol=1e-8, max_cycles=20)
+    gs, gg, gX, infos = K.krr_mll_grad(_dev(X), _dev(y), sigma, gamma, n_probes=P, seed=seed, opts=opts)
+    assert all(i["status"] == K.KRR_OK for i in infos)
+    Zp = oracle_mod.rademacher_probes(seed, N, P)
+    os_, og, oX = oracle_mod.mll_grad_hutchinson(X.astype(np.float64), y.astype(np.float64),
+                                                 f32(sigma), f32(gamma), Zp)
+    assert gs == pytest.approx(os_, rel=1e-4, abs=1e-6 * abs(os_) + 1e-8)
+    assert gg == pytest.approx(og, rel=1e-4, abs=1e-8)
+    gX = gX.cpu().numpy()
+    assert gX.shape == (N, d)
+    assert np.max(np.abs(gX - oX)) <= 1e-4 * np.max(np.abs(oX))

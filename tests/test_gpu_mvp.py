@@ -233,3 +233,30 @@ def test_set_option_rejects_unknown(K):
     with pytest.raises(K.KrrError) as ei:
         K.krr_set_option(99, 1)
     assert ei.value.status == K.KRR_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("d,m", [(9, 1), (16, 1), (17, 4), (41, 1), (64, 3), (20, 16)])
+def test_mvp_high_dimension(K, oracle_mod, d, m):
+    # above 8 dimensions the coordinates are padded with zeros to 16/32/48/64
+    # and every block takes the direct form
+    rng = np.random.default_rng(400 + d + m)
+    N = 3000
+    X = rng.random((N, d)).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    sigma = 0.25 * np.sqrt(d)
+    Y = K.krr_kernel_mvp(_dev(X), _dev(Q if m > 1 else Q[0]), sigma, 1e-2).cpu().numpy().reshape(m, N)
+    for c in range(m):
+        assert scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-2) <= TOL_FP32, (d, c)
+
+
+def test_mvp_rect_high_dimension(K, oracle_mod):
+    rng = np.random.default_rng(450)
+    Xs = rng.random((2500, 33)).astype(np.float32)
+    Xt = rng.random((700, 33)).astype(np.float32)
+    q = rng.standard_normal(2500).astype(np.float32)
+    sigma = 0.25 * np.sqrt(33)
+    y = K.krr_kernel_mvp_rect(_dev(Xt), _dev(Xs), _dev(q), sigma).cpu().numpy()
+    ref = oracle_mod.mvp_rect(Xt.astype(np.float64), Xs.astype(np.float64), q.astype(np.float64), f32(sigma))
+    scale = oracle_mod.mvp_rect(Xt.astype(np.float64), Xs.astype(np.float64),
+                                np.abs(q.astype(np.float64)), f32(sigma))
+    assert np.max(np.abs(y - ref) / np.maximum(scale, 1e-30)) <= TOL_FP32
