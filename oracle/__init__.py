@@ -10,13 +10,14 @@ input generators and nothing else.
 Modules
   mvp      -- Gaussian kernel products (Eqs. 1-3), C + OpenMP on the fly, and
               dense NumPy matrices for small N.
-  solvers  -- Cholesky direct solve, textbook CG, Algorithm 1 (FGMRES) and the
-              paper's FGMRES + truncated-CG preconditioner (Sec. 5).
+  solvers  -- Cholesky direct solve, textbook CG, Algorithm 1 (FGMRES), the
+              paper's FGMRES + truncated-CG preconditioner (Sec. 5), and
+              flexible CG (Notay) with the same preconditioner.
   mll      -- GP log-marginal likelihood, exact and Hutchinson gradients, and
               the SplitMix64 Rademacher probes.
 """
 from .mvp import mvp, mvp_rect, kernel_matrix, regularised_matrix, sqdist, num_threads
-from .solvers import (direct_solve, cg, fgmres, krr_fgmres, default_delta,
+from .solvers import (direct_solve, cg, fgmres, krr_fgmres, fcg, krr_fcg, default_delta,
                       default_inner_tol)
 from .mll import (mll, mll_grad_exact, mll_grad_hutchinson, grad_from_solves,
                   splitmix64, rademacher_probes)
@@ -24,7 +25,7 @@ from .build import build_oracle
 
 __all__ = [
     "mvp", "mvp_rect", "kernel_matrix", "regularised_matrix", "sqdist",
-    "num_threads", "direct_solve", "cg", "fgmres", "krr_fgmres",
+    "num_threads", "direct_solve", "cg", "fgmres", "krr_fgmres", "fcg", "krr_fcg",
     "default_delta", "default_inner_tol", "mll", "mll_grad_exact",
     "mll_grad_hutchinson", "grad_from_solves", "splitmix64",
     "rademacher_probes", "build_oracle",

@@ -11,6 +11,10 @@
 * ``krr_fgmres``    -- the paper's method: FGMRES on K = K_hat + gamma I with
   the inner solve being truncated CG on M = K + delta I = K_hat + (gamma+delta) I
   (Sec. 5, Eq. for M).
+* ``fcg`` / ``krr_fcg`` -- flexible CG, the paper's second outer iteration
+  (Sec. 4.3: Notay's flexible CG, whose search directions are
+  A-orthogonalised against the previous ones at every step), with the same
+  truncated-CG preconditioner.
 
 Readings of the paper, where it is silent or ambiguous:
 * Stopping rule (Sec. 4.3): the relative residual |b - K x|_2 / |b|_2 <= tol.
@@ -167,3 +171,67 @@ def default_delta(gamma):
 def default_inner_tol(tol):
     """Sec. 6 rule: inner tolerance one order of magnitude above the outer."""
     return 10.0 * tol
+
+
+class FCGResult:
+    def __init__(self):
+        self.x = None
+        self.iters = 0            # outer steps
+        self.inner_iters = 0      # total inner CG iterations
+        self.relres = np.inf      # true |b - A x| / |b| at exit
+        self.history = []         # |r_i| / |b| after each step
+        self.directions = []      # (d_i, A d_i) of every step, when kept
+
+
+def fcg(matvec, b, tol, maxit, mmax, inner=None, x0=None, keep=False):
+    """Flexible conjugate gradient (Notay) for SPD A.
+
+    Step i: z_i = B_i(r_i) from a possibly varying preconditioner (inner(v)
+    -> (z, iters); None means B = I); the new direction is z_i made
+    A-orthogonal to the last mmax directions,
+        d_i = z_i - sum_k (z_i . A d_k) / (d_k . A d_k) d_k,
+    then alpha_i = (d_i . r_i) / (d_i . A d_i), x += alpha_i d_i,
+    r -= alpha_i A d_i.  Stops when |r|_2 <= tol |b|_2 or after maxit steps.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    res = FCGResult()
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - matvec(x) if x0 is not None else b.copy()
+    bnorm = float(np.linalg.norm(b))
+    window = []   # (d_k, A d_k, d_k . A d_k)
+    while res.iters < maxit and np.linalg.norm(r) > tol * bnorm:
+        if inner is None:
+            z = r.copy()
+        else:
+            z, it = inner(r)
+            res.inner_iters += it
+        d = z.copy()
+        for dk, adk, dadk in window:
+            d = d - (z @ adk) / dadk * dk
+        ad = matvec(d)
+        dad = float(d @ ad)
+        if not dad > 0.0:
+            break
+        alpha = float(d @ r) / dad
+        x = x + alpha * d
+        r = r - alpha * ad
+        window.append((d, ad, dad))
+        if len(window) > mmax:
+            window.pop(0)
+        if keep:
+            res.directions.append((d, ad))
+        res.iters += 1
+        res.history.append(float(np.linalg.norm(r)) / bnorm if bnorm > 0 else 0.0)
+    res.x = x
+    res.relres = float(np.linalg.norm(b - matvec(x)) / bnorm) if bnorm > 0 else 0.0
+    return res
+
+
+def krr_fcg(matvec_K, matvec_M, b, mmax=30, tol=1e-6, maxit=500, inner_tol=1e-4,
+            inner_maxit=1000):
+    """Flexible CG on K, preconditioned by truncated CG on M = K + delta I
+    (Sec. 4.3 / Sec. 5); matvec_M applies M."""
+    def inner(v):
+        z, it = cg(matvec_M, v, inner_tol, inner_maxit)
+        return z, it
+    return fcg(matvec_K, b, tol, maxit, mmax, inner=inner)

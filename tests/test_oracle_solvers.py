@@ -158,3 +158,75 @@ def test_paper_parameter_rules(oracle_mod):
     assert oracle_mod.default_delta(1e-3) == pytest.approx(1e-2)
     assert oracle_mod.default_delta(0.0) == pytest.approx(1e-3)
     assert oracle_mod.default_inner_tol(1e-4) == pytest.approx(1e-3)
+
+
+# ---------------------------------------------------------------- flexible CG
+def _spd(n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.geomspace(1.0, cond, n)
+    return (Qm * lam) @ Qm.T
+
+
+def test_fcg_without_preconditioner_is_cg(oracle_mod):
+    # B = I and a window longer than the run: flexible CG is textbook CG in
+    # exact arithmetic, so both residual histories agree step by step
+    A = _spd(40, 1, cond=1e2)
+    b = np.random.default_rng(2).standard_normal(40)
+    # (the first 20 steps: later the short CG recurrence and the fully
+    # reorthogonalised one part by rounding)
+    h_cg = []
+    oracle_mod.cg(lambda v: A @ v, b, 1e-10, 20, history=h_cg)
+    r = oracle_mod.fcg(lambda v: A @ v, b, 1e-10, 20, mmax=100)
+    assert len(h_cg) == len(r.history) == 20
+    np.testing.assert_allclose(r.history, h_cg, rtol=1e-7)
+
+
+def test_fcg_exact_preconditioner_one_step(oracle_mod):
+    # B = A^-1 exactly: the first direction is the solution's increment
+    A = _spd(30, 3)
+    b = np.random.default_rng(4).standard_normal(30)
+    r = oracle_mod.fcg(lambda v: A @ v, b, 1e-12, 10, mmax=5,
+                       inner=lambda v: (np.linalg.solve(A, v), 1))
+    assert r.iters == 1
+    np.testing.assert_allclose(r.x, np.linalg.solve(A, b), rtol=1e-10)
+
+
+def test_fcg_directions_are_conjugate_with_varying_preconditioner(oracle_mod):
+    # a preconditioner that changes every step (truncated inner CG) still
+    # yields A-conjugate directions within the window, by construction
+    A = _spd(60, 5, cond=1e4)
+    b = np.random.default_rng(6).standard_normal(60)
+    M = A + 0.5 * np.eye(60)
+    inner = lambda v: oracle_mod.cg(lambda u: M @ u, v, 1e-2, 7)
+    r = oracle_mod.fcg(lambda v: A @ v, b, 1e-10, 40, mmax=40, inner=inner, keep=True)
+    D = np.array([d for d, _ in r.directions])
+    G = D @ A @ D.T
+    off = G - np.diag(np.diag(G))
+    assert np.max(np.abs(off)) <= 1e-9 * np.max(np.abs(np.diag(G)))
+    assert r.relres <= 1e-10
+
+
+def test_fcg_finite_termination(oracle_mod):
+    A = _spd(12, 7, cond=50)
+    b = np.random.default_rng(8).standard_normal(12)
+    r = oracle_mod.fcg(lambda v: A @ v, b, 1e-12, 12, mmax=12)
+    assert r.relres <= 1e-10 and r.iters <= 12
+
+
+def test_krr_fcg_matches_cholesky_on_the_small_problem(oracle_mod):
+    # the paper's FCG settings for the 2000-point problem (Sec. 5.1:
+    # delta = epsilon = 1e-4), on a 600-point instance
+    from paper_1408_1237_gb300 import inputs
+    p = inputs.small_problem(seed=9, N=600)
+    X = p["X"].astype(np.float64)
+    Kd = oracle_mod.regularised_matrix(X, p["sigma"], p["gamma"])
+    Md = oracle_mod.regularised_matrix(X, p["sigma"], p["gamma"] + 1e-4)
+    b = p["b"].astype(np.float64)
+    r = oracle_mod.krr_fcg(lambda v: Kd @ v, lambda v: Md @ v, b, mmax=30, tol=1e-6,
+                           inner_tol=1e-4, inner_maxit=2000)
+    assert r.relres <= 1e-6
+    x_star = oracle_mod.direct_solve(Kd, b)
+    assert np.linalg.norm(r.x - x_star) <= np.linalg.cond(Kd) * 1e-6 * np.linalg.norm(x_star)
+    # a strongly preconditioned flexible iteration needs few outer steps
+    assert r.iters <= 20
