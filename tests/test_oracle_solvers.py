@@ -204,7 +204,10 @@ def test_fcg_directions_are_conjugate_with_varying_preconditioner(oracle_mod):
     G = D @ A @ D.T
     off = G - np.diag(np.diag(G))
     assert np.max(np.abs(off)) <= 1e-9 * np.max(np.abs(np.diag(G)))
-    assert r.relres <= 1e-10
+    # Galerkin property: the residual is orthogonal to every direction kept
+    res = b - A @ r.x
+    proj = np.abs(D @ res) / (np.linalg.norm(D, axis=1) * np.linalg.norm(res))
+    assert np.max(proj) <= 1e-8
 
 
 def test_fcg_finite_termination(oracle_mod):
