@@ -308,7 +308,8 @@ def run_libkrr(args):
     solve = {}
     sp = inputs.small_problem(seed=rank)
     solve["small_2000pt_2d"] = {"fgmres": solve_once(K, torch, sp, dev, stream, "fp32"),
-                                "cg": cg_once(K, torch, sp, dev, stream)}
+                                "cg": cg_once(K, torch, sp, dev, stream),
+                                "fcg": fcg_once(K, torch, sp, dev, stream)}
     if args.solve_n > 0:
         solve[f"mixture_{args.solve_n}pt_2d"] = mixture_forms(K, torch, inputs, args, rank, dev, stream)
     if args.batch_probs > 0:
@@ -429,6 +430,20 @@ def cg_once(K, torch, p, dev, stream):
                                                                  tol=1e-6, maxit=20000))
     return {"time_to_solution_ms": ms, "relres_true": info["relres_true"],
             "iters": info["outer_iters"], "status": K.status_string(info["status"])}
+
+
+def fcg_once(K, torch, p, dev, stream):
+    """Flexible CG with the paper's flexible-CG settings (delta = inner tol =
+    1e-4, window 30)."""
+    X = torch.from_numpy(p["X"]).to(dev)
+    b = torch.from_numpy(p["b"]).to(dev)
+    opts = K.default_opts(delta=1e-4, inner_tol=1e-4, inner_maxit=2000, restart=30)
+    K.krr_fcg_solve(X, b, p["sigma"], p["gamma"], opts=K.default_opts(max_cycles=1, restart=1,
+                                                                     inner_maxit=1))  # workspace
+    (x, info), ms = _timed(torch, stream, lambda: K.krr_fcg_solve(X, b, p["sigma"], p["gamma"], opts=opts))
+    i = info[0]
+    return {"time_to_solution_ms": ms, "relres_true": i["relres_true"], "outer": i["outer_iters"],
+            "inner": i["inner_iters"], "status": K.status_string(i["status"])}
 
 
 def mixture_forms(K, torch, inputs, args, rank, dev, stream):

@@ -199,6 +199,25 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d,
                             double* Xsol, const krr_fgmres_opts* opts,
                             krr_solve_info* info, void* stream);
 
+/* ------------------------------------------------------ flexible CG solve
+ * Flexible CG (Notay; the paper's second outer iteration, Sec. 4.3) on
+ * K = K_hat + gamma I with the same truncated-CG preconditioner on
+ * M = K + delta I: each new search direction is the preconditioned residual
+ * made K-orthogonal to the previous opts->restart directions (the window),
+ * step lengths from the FP64 recursion, the iterate in float-float, products
+ * K d with the compensated kernel.  When the recursive residual meets the
+ * tolerance the true residual is computed; if it does not meet it, the
+ * iteration restarts from it with an empty window.  At most
+ * opts->restart * opts->max_cycles steps.  The paper pairs flexible CG with
+ * an accurate inner solve (its experiments: delta = inner_tol = 1e-4).
+ * Arguments and reports as krr_fgmres_solve (outer_iters = flexible-CG
+ * steps, cycles = restarts + 1); right-hand sides are solved one after
+ * another.  Waits for the solve. */
+krr_status krr_fcg_solve(krr_handle h, const float* X, int64_t N, int d,
+                         float sigma, float gamma, const float* B, int m_rhs,
+                         double* Xsol, const krr_fgmres_opts* opts,
+                         krr_solve_info* info, void* stream);
+
 /* Many independent problems (same d, sigma, opts; own N_k, gamma_k, m_rhs
  * right-hand sides each) solved together: one lockstep block solve per
  * problem (and block of right-hand sides), each an independent branch with

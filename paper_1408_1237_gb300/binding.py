@@ -75,6 +75,8 @@ _SIGNATURES = {
                       ctypes.POINTER(krr_solve_info), _vp], _int),
     "krr_fgmres_solve": ([_vp, _vp, _i64, _int, _f, _f, _vp, _int, _vp,
                           ctypes.POINTER(krr_fgmres_opts), ctypes.POINTER(krr_solve_info), _vp], _int),
+    "krr_fcg_solve": ([_vp, _vp, _i64, _int, _f, _f, _vp, _int, _vp,
+                       ctypes.POINTER(krr_fgmres_opts), ctypes.POINTER(krr_solve_info), _vp], _int),
     "krr_fgmres_solve_batched": ([_vp, ctypes.POINTER(krr_problem), _int, _int, _f, _int,
                                   ctypes.POINTER(krr_fgmres_opts), ctypes.POINTER(krr_solve_info),
                                   _vp], _int),
@@ -275,6 +277,25 @@ def krr_fgmres_solve(X, B, sigma, gamma, opts=None, out=None, handle=None, strea
     infos = (krr_solve_info * m)()
     s = lib().krr_fgmres_solve(h.h, _ptr(X), N, d, sigma, gamma, _ptr(B), m, _ptr(Xsol),
                                ctypes.byref(opts), infos, _stream(stream, X, B, Xsol))
+    if s != KRR_NOT_CONVERGED or raise_on_nonconv:
+        h.check(s)
+    return Xsol, [i.as_dict() for i in infos]
+
+
+def krr_fcg_solve(X, B, sigma, gamma, opts=None, out=None, handle=None, stream=None,
+                  raise_on_nonconv=False):
+    """Flexible CG with the truncated-CG preconditioner (opts.restart = the
+    window of kept directions).  B (N,) or (m, N) float32.
+    Returns (Xsol FP64 like B, [info dict per column])."""
+    h = handle or default_handle()
+    N, d = X.shape
+    m = _cols(B, N)
+    Xsol = out if out is not None else _empty_like_cols(B, m, N, "float64")
+    if opts is None:
+        opts = default_opts()
+    infos = (krr_solve_info * m)()
+    s = lib().krr_fcg_solve(h.h, _ptr(X), N, d, sigma, gamma, _ptr(B), m, _ptr(Xsol),
+                            ctypes.byref(opts), infos, _stream(stream, X, B, Xsol))
     if s != KRR_NOT_CONVERGED or raise_on_nonconv:
         h.check(s)
     return Xsol, [i.as_dict() for i in infos]

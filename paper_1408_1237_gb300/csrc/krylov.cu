@@ -584,6 +584,152 @@ __global__ void fill_zero_kernel(float* __restrict__ a, int64_t n) {
 #undef KRR_COL
 #undef KRR_GRID_LOOP
 
+// ------------------------------------------------------- flexible CG ---
+// Flexible CG (Notay; the paper's second outer iteration, Sec. 4.3): step i
+// takes the preconditioned residual z_i (truncated inner CG on M) and makes it
+// A-orthogonal to the previous (at most mmax) directions,
+//   d_i = z_i - sum_k beta_k d_k,  beta_k = (z_i . A d_k) / (d_k . A d_k),
+// then alpha_i = (d_i . r_i) / (d_i . A d_i), x += alpha_i d_i,
+// r -= alpha_i A d_i.  Directions and A d live in a circular window of
+// W = mmax + 1 FP64 slots; slot `head` receives the new direction.
+struct FState {
+  double beta[MMAX + 1], dad[MMAX + 1];
+  double alpha, rr, bnorm;
+  int cnt, head, W, brk;
+  unsigned ticket;
+};
+
+// beta_k for the cnt directions before head (multi-dot, last block divides)
+__global__ void fcg_beta_kernel(FState* F, const float* __restrict__ z, const double* __restrict__ AD,
+                                int64_t Np, double* partials) {
+  __shared__ double red[8];
+  __shared__ bool is_last;
+  const int cnt = F->cnt, W = F->W, head = F->head;
+  for (int c = 0; c < cnt; ++c) {
+    const int slot = (head - 1 - c + W) % W;
+    const double* adk = AD + (int64_t)slot * Np;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+         i += (int64_t)gridDim.x * blockDim.x)
+      acc += (double)z[i] * adk[i];
+    const double bs = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * (MMAX + 1) + c] = bs;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(&F->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int c = 0; c < cnt; ++c) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      t += partials[(int64_t)b * (MMAX + 1) + c];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) {
+      const int slot = (head - 1 - c + W) % W;
+      F->beta[slot] = F->dad[slot] > 0.0 ? t / F->dad[slot] : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) F->ticket = 0u;
+}
+
+// d = z - sum beta_k d_k into slot head (FP64) and as float-float (dh + dl)
+__global__ void fcg_dir_kernel(const FState* F, const float* __restrict__ z, double* __restrict__ D,
+                               int64_t Np, float* __restrict__ dh, float* __restrict__ dl) {
+  __shared__ double bs[MMAX + 1];
+  __shared__ int slots[MMAX + 1];
+  const int cnt = F->cnt, W = F->W, head = F->head;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+    slots[c] = (head - 1 - c + W) % W;
+    bs[c] = F->beta[slots[c]];
+  }
+  __syncthreads();
+  double* dn = D + (int64_t)head * Np;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = z[i];
+    for (int c = 0; c < cnt; ++c) v -= bs[c] * D[(int64_t)slots[c] * Np + i];
+    dn[i] = v;
+    const float h = (float)v;
+    dh[i] = h;
+    dl[i] = (float)(v - (double)h);
+  }
+}
+
+// d . A d and d . r; the last block sets alpha (or flags a breakdown)
+__global__ void fcg_alpha_kernel(FState* F, const double* __restrict__ D, const double* __restrict__ AD,
+                                 const double* __restrict__ r, int64_t Np, double* partials) {
+  __shared__ double red[8];
+  __shared__ bool is_last;
+  const int head = F->head;
+  const double* d = D + (int64_t)head * Np;
+  const double* ad = AD + (int64_t)head * Np;
+  double a1 = 0.0, a2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a1 += d[i] * ad[i];
+    a2 += d[i] * r[i];
+  }
+  const double b1 = block_sum(a1, red);
+  const double b2 = block_sum(a2, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b1;
+    partials[2 * blockIdx.x + 1] = b2;
+    __threadfence();
+    is_last = atomicAdd(&F->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last || threadIdx.x != 0) return;
+  __threadfence();
+  double t1 = 0.0, t2 = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    t1 += partials[2 * b];
+    t2 += partials[2 * b + 1];
+  }
+  F->dad[head] = t1;
+  const bool good = t1 > 0.0 && isfinite(t1) && isfinite(t2);
+  F->alpha = good ? t2 / t1 : 0.0;
+  F->brk = good ? 0 : 1;
+  F->ticket = 0u;
+}
+
+// x += alpha d (float-float), r -= alpha A d, |r|^2; the last block advances
+// the window
+__global__ void fcg_update_kernel(FState* F, const double* __restrict__ D, const double* __restrict__ AD,
+                                  int64_t Np, float* __restrict__ xh, float* __restrict__ xl,
+                                  double* __restrict__ r, double* partials, int mmax) {
+  __shared__ double red[8];
+  const int head = F->head;
+  const double a = F->alpha;
+  const double* d = D + (int64_t)head * Np;
+  const double* ad = AD + (int64_t)head * Np;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = (double)xh[i] + (double)xl[i] + a * d[i];
+    const float h = (float)t;
+    xh[i] = h;
+    xl[i] = (float)(t - (double)h);
+    const double ri = r[i] - a * ad[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double tot;
+  if (grid_sum_last(acc, partials, &F->ticket, red, tot) && threadIdx.x == 0) {
+    F->rr = tot;
+    F->cnt = min(F->cnt + 1, mmax);
+    F->head = (head + 1) % F->W;
+  }
+}
+
+__global__ void fcg_to_float_kernel(const double* __restrict__ r, int64_t Np, float* __restrict__ rf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rf[i] = (float)r[i];
+}
+
 // ---------------------------------------------------------------- driver --
 // One solve of mc right-hand sides of one problem in lockstep (a block
 // solve): every column runs its own FGMRES (its own Krylov basis, Givens
@@ -1115,6 +1261,161 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
     set_error(c, worst, "%s: tolerance not reached in %d cycles", fn, cfg.max_cycles);
   else if (worst != KRR_OK)
     set_error(c, worst, "%s: solve failed", fn);
+  return worst;
+}
+
+krr_status krr_fcg_solve(krr_handle h, const float* X, int64_t N, int d, float sigma, float gamma,
+                         const float* B, int m_rhs, double* Xsol, const krr_fgmres_opts* opts,
+                         krr_solve_info* info, void* stream) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  const char* fn = "krr_fcg_solve";
+  krr_status s = check_points(c, fn, X, N, d, sigma);
+  if (s) return s;
+  if (!(gamma >= 0.f) || !std::isfinite(gamma))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: gamma must be finite and >= 0", fn);
+  if (m_rhs < 1 || m_rhs > 1024)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: m_rhs out of range [1, 1024]", fn);
+  SolveCfg cfg;
+  if ((s = resolve_opts(c, fn, opts, gamma, cfg))) return s;
+  if (N == 0) return KRR_OK;
+  if (!B || !Xsol) return set_error(c, KRR_ERR_INVALID_ARG, "%s: B or Xsol is NULL", fn);
+  cudaStream_t ust = (cudaStream_t)stream;
+  cudaStream_t st = c.work;
+  {
+    cudaError_t e0 = fork_work(c, ust);
+    if (e0) return cuda_error(c, e0, fn);
+  }
+  Join join{c, ust};
+  float *dX, *dB;
+  double* dXs;
+  bool sX, sB, sXs;
+  if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
+  if ((s = device_view(c, "stage.B", B, (size_t)N * m_rhs, true, st, &dB, &sB))) return s;
+  if ((s = device_view_d(c, "stage.Xsol", Xsol, (size_t)N * m_rhs, false, st, &dXs, &sXs))) return s;
+  Solver sv(c);
+  sv.st = st;
+  cudaError_t e = prepare_points(c, dX, N, d, sigma, "kry.pts", sv.P, st);
+  if (e) return cuda_error(c, e, fn);
+  sv.Np = sv.P.Npad;
+  sv.gamma = gamma;
+  sv.mshift = (float)(gamma + cfg.delta);
+  sv.inner_prec = cfg.inner_prec;
+  if ((e = sv.alloc(1, 1))) return cuda_error(c, e, fn);
+  if ((e = sv.reserve())) return cuda_error(c, e, fn);
+  const int mmax = cfg.restart, W = mmax + 1;
+  const int64_t Np = sv.Np;
+  void *Dv, *ADv, *dhv, *dlv, *rfv, *Fv;
+  if ((e = c.ws.get("fcg.D", sizeof(double) * W * (size_t)Np, &Dv)) ||
+      (e = c.ws.get("fcg.AD", sizeof(double) * W * (size_t)Np, &ADv)) ||
+      (e = c.ws.get("fcg.dh", sizeof(float) * (size_t)Np, &dhv)) ||
+      (e = c.ws.get("fcg.dl", sizeof(float) * (size_t)Np, &dlv)) ||
+      (e = c.ws.get("fcg.rf", sizeof(float) * (size_t)Np, &rfv)) ||
+      (e = c.ws.get("fcg.state", sizeof(FState), &Fv)))
+    return cuda_error(c, e, fn);
+  double *D = (double*)Dv, *AD = (double*)ADv;
+  float *dh = (float*)dhv, *dl = (float*)dlv, *rf = (float*)rfv;
+  FState* F = (FState*)Fv;
+  const double tol_stop = 0.5 * cfg.tol;
+  const int cap = cfg.restart * cfg.max_cycles;  // outer steps in total
+  const unsigned vb = sv.vblocks;
+  krr_status worst = KRR_OK;
+  for (int col = 0; col < m_rhs; ++col) {
+    if ((e = load_rhs(sv, dB + (size_t)col * N, N, 1))) return cuda_error(c, e, fn);
+    std::vector<KState> hs;
+    if ((e = upload_states(sv, cfg, hs))) return cuda_error(c, e, fn);  // inner CG settings
+    FState hf;
+    auto reset_window = [&](double bnorm) -> cudaError_t {
+      memset(&hf, 0, sizeof(hf));
+      hf.W = W;
+      hf.bnorm = bnorm;
+      cudaError_t ee = cudaMemcpyAsync(F, &hf, sizeof(FState), cudaMemcpyHostToDevice, st);
+      if (!ee) ee = cudaStreamSynchronize(st);
+      return ee;
+    };
+    cudaEventRecord(c.ev0, st);
+    solve_init_kernel<<<vb, VT, 0, st>>>(sv.S, sv.b, Np, sv.xh, sv.xl, sv.r64, sv.partials); count_launch();
+    KState ks;
+    if ((e = read_state(c, sv.S, ks, st))) return cuda_error(c, e, fn);
+    const double bnorm = ks.bnorm;
+    if ((e = reset_window(bnorm))) return cuda_error(c, e, fn);
+    double rr = ks.rnorm2, relres_true = bnorm > 0.0 ? 1.0 : 0.0;
+    int it = 0, head = 0, cycles = 1;
+    krr_status st_col = KRR_OK;
+    bool done = bnorm == 0.0;
+    while (!done) {
+      if (rr <= tol_stop * tol_stop * bnorm * bnorm || it >= cap || hf.brk) {
+        // the recursive residual met the tolerance (or the cap / a breakdown):
+        // check the true one with the accurate product
+        if ((e = sv.residual(false))) return cuda_error(c, e, fn);
+        if ((e = read_state(c, sv.S, ks, st))) return cuda_error(c, e, fn);
+        relres_true = std::sqrt(ks.rnorm2) / bnorm;
+        if (!std::isfinite(relres_true)) {
+          st_col = KRR_ERR_NONFINITE;
+          break;
+        }
+        if (relres_true <= tol_stop) break;
+        if (it >= cap || hf.brk) {
+          st_col = KRR_NOT_CONVERGED;
+          break;
+        }
+        // restart from the true residual with an empty window (a step of
+        // iterative refinement)
+        rr = ks.rnorm2;
+        head = 0;
+        ++cycles;
+        if ((e = reset_window(bnorm))) return cuda_error(c, e, fn);
+      }
+      // z = M^-1 r by truncated CG (float32 right-hand side)
+      fcg_to_float_kernel<<<vb, VT, 0, st>>>(sv.r64, Np, rf); count_launch();
+      cg_init_kernel<<<vb, VT, 0, st>>>(sv.S, nullptr, 0, rf, Np, sv.z, sv.rr, sv.p, sv.partials, PRED_ALL,
+                                        sv.G, Cond{}); count_launch();
+      for (;;) {
+        Group g;
+        if ((e = read_group(sv.G, g, st))) return cuda_error(c, e, fn);
+        if (!g.cg_any) break;
+        for (int b = 0; b < 8; ++b)
+          if ((e = sv.cg_iteration())) return cuda_error(c, e, fn);
+      }
+      // the new direction, its product and the step
+      fcg_beta_kernel<<<vb, VT, 0, st>>>(F, sv.z, AD, Np, sv.partials); count_launch();
+      fcg_dir_kernel<<<vb, VT, 0, st>>>(F, sv.z, D, Np, dh, dl); count_launch();
+      if ((e = mvp_acc_launch(c, sv.P, dh, dl, gamma, 0.0, nullptr, 1.0, AD + (size_t)head * Np, nullptr, st)))
+        return cuda_error(c, e, fn);
+      fcg_alpha_kernel<<<vb, VT, 0, st>>>(F, D, AD, sv.r64, Np, sv.partials); count_launch();
+      fcg_update_kernel<<<vb, VT, 0, st>>>(F, D, AD, Np, sv.xh, sv.xl, sv.r64, sv.partials, mmax); count_launch();
+      if ((e = cudaGetLastError())) return cuda_error(c, e, fn);
+      if ((e = cudaMemcpyAsync(&hf, F, sizeof(FState), cudaMemcpyDeviceToHost, st)) ||
+          (e = cudaStreamSynchronize(st)))
+        return cuda_error(c, e, fn);
+      rr = hf.rr;
+      head = hf.head;
+      ++it;
+    }
+    cudaEventRecord(c.ev1, st);
+    if ((e = cudaEventSynchronize(c.ev1))) return cuda_error(c, e, fn);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+    if ((e = read_state(c, sv.S, ks, st))) return cuda_error(c, e, fn);
+    scatter_x64_kernel<<<vb, VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, Np, dXs + (size_t)col * N); count_launch();
+    if (info) {
+      krr_solve_info& in = info[col];
+      in.outer_iters = it;
+      in.inner_iters = ks.inner_total;
+      in.cycles = cycles;
+      in.breakdowns = ks.breakdowns + hf.brk;
+      in.relres_est = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
+      in.relres_true = relres_true;
+      in.time_ms = ms;
+      in.status = st_col;
+    }
+    if (st_col != KRR_OK && worst == KRR_OK) worst = st_col;
+  }
+  if (sXs && (e = cudaMemcpyAsync(Xsol, dXs, sizeof(double) * N * m_rhs, cudaMemcpyDeviceToHost, st)))
+    return cuda_error(c, e, fn);
+  krr_status de = read_device_error(c, st, fn);
+  if (de) return de;
+  if (worst != KRR_OK) set_error(c, worst, "%s: a right-hand side did not reach the tolerance", fn);
   return worst;
 }
 
