@@ -16,7 +16,10 @@
  * The loop over rows is split across OpenMP threads; the order of the sum over
  * sources inside one row is the plain j = 0..N-1 order.
  *
- * Parity: pinned by the closed forms and invariants in tests/test_oracle_mvp.py.
+ * The Matern kernel of Sec. 6.1 has its own two functions below.
+ *
+ * Parity: pinned by the closed forms and invariants in tests/test_oracle_mvp.py
+ * (Gaussian) and tests/test_oracle_matern.py (Matern).
  */
 #include <math.h>
 #include <stdint.h>
@@ -74,6 +77,56 @@ void oracle_mvp_rect(const double* Xt, int64_t Nt, const double* Xs, int64_t Ns,
             }
             acc += exp(-dist2 / two_sigma2) * q[j];
         }
+        y[t] = acc;
+    }
+}
+
+/*
+ * Matern kernel of Sec. 6.1 (Eq. MaternKernel, smoothness 3/2), with the
+ * length scale h in the role sigma has for the Gaussian:
+ *
+ *     k(x_i, x_j) = (1 + sqrt(3) d_ij) exp(-sqrt(3) d_ij),
+ *     d_ij = ||x_i - x_j|| / h,
+ *
+ * and the same weighted sums as above:
+ *     y_r = sum_j k(x_r, x_j) q_j + gamma q_r           (square, Eq. 3)
+ *     y_t = sum_j k(xt_t, xs_j) q_j                      (rectangular)
+ */
+static double matern32(const double* a, const double* b, int d, double h)
+{
+    double dist2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double diff = a[k] - b[k];
+        dist2 += diff * diff;
+    }
+    const double t = sqrt(3.0) * sqrt(dist2) / h;
+    return (1.0 + t) * exp(-t);
+}
+
+void oracle_mvp_matern(const double* X, int64_t N, int d, double h, double gamma,
+                       const double* Q, int m, const int64_t* rows, int64_t nrows,
+                       double* Y)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows ? rows[r] : r;
+        const double* xi = X + i * d;
+        for (int c = 0; c < m; ++c) {
+            const double* q = Q + (int64_t)c * N;
+            double acc = 0.0;
+            for (int64_t j = 0; j < N; ++j) acc += matern32(xi, X + j * d, d, h) * q[j];
+            Y[(int64_t)c * nrows + r] = acc + gamma * q[i];
+        }
+    }
+}
+
+void oracle_mvp_rect_matern(const double* Xt, int64_t Nt, const double* Xs, int64_t Ns,
+                            int d, double h, const double* q, double* y)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < Nt; ++t) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < Ns; ++j) acc += matern32(Xt + t * d, Xs + j * d, d, h) * q[j];
         y[t] = acc;
     }
 }
