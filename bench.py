@@ -38,9 +38,9 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "52e9cee25c18425fc473ba87f707502aab864605",
-                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "b0014c8268cd661102f707b3228df26685dd56b0"},
-               "bytes": 22100736 + 91679488 + 17155584 + 0}
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "e02f3d4c7aaab6ccb47d0d0f72e0ba0e70a65cb7",
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "1ea52efd48eed195348b75518e71a1d329f13585"},
+               "bytes": 22164224 + 91434240 + 17156096 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 
