@@ -38,9 +38,9 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "e02f3d4c7aaab6ccb47d0d0f72e0ba0e70a65cb7",
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "7929ff54debf9b5286ac1632d89154af72a7df60",
                            "paper_1408_1237_gb300/csrc/mvp_tc.cu": "1ea52efd48eed195348b75518e71a1d329f13585"},
-               "bytes": 22164224 + 91434240 + 17156096 + 0}
+               "bytes": 22316544 + 91850240 + 17240320 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 
@@ -60,6 +60,8 @@ def parse_args(argv=None):
                     help="largest problem of the batching-form subset")
     ap.add_argument("--grad-n", type=int, default=1 << 16,
                     help="points of the log-marginal-likelihood gradient (0 skips it)")
+    ap.add_argument("--no-matern", dest="matern", action="store_false",
+                    help="skip the Matern-kernel product and solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -317,6 +319,9 @@ def run_libkrr(args):
     grad = None
     if args.grad_n > 0:
         grad = gradient_form(K, torch, inputs, args, rank, dev, stream)
+    matern = None
+    if args.matern:
+        matern = matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
 
     # ---- FP64 oracle on the host cores (rank 0, one GPU only)
     cpu = None
@@ -358,6 +363,7 @@ def run_libkrr(args):
                         "tcgen05_ms": m16_tc5_ms},
             "fgmres": solve,
             "mll_grad": grad,
+            "matern": matern,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -382,7 +388,7 @@ def traffic_bytes(tensor_exp):
     return t["bytes"]
 
 
-def solve_once(K, torch, p, dev, stream, inner_prec):
+def solve_once(K, torch, p, dev, stream, inner_prec, handle=None):
     """Time one FGMRES solve (prep included) with CUDA events; FP64-recheck
     is left to the tests.  Returns a report dict."""
     X = torch.from_numpy(p["X"]).to(dev)
@@ -391,11 +397,11 @@ def solve_once(K, torch, p, dev, stream, inner_prec):
                           tol=p["tol"], inner_prec=inner_prec)
     warm = K.default_opts(restart=p["restart"], max_cycles=1, inner_maxit=1,
                           inner_prec=inner_prec)
-    K.krr_fgmres_solve(X, b, p["sigma"], p["gamma"], opts=warm)  # allocates the workspace
+    K.krr_fgmres_solve(X, b, p["sigma"], p["gamma"], opts=warm, handle=handle)  # allocates the workspace
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    x, info = K.krr_fgmres_solve(X, b, p["sigma"], p["gamma"], opts=opts)
+    x, info = K.krr_fgmres_solve(X, b, p["sigma"], p["gamma"], opts=opts, handle=handle)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     i = info[0]
@@ -422,12 +428,13 @@ def _report(K, infos):
             "all_ok": all(i["status"] == K.KRR_OK for i in infos)}
 
 
-def cg_once(K, torch, p, dev, stream):
+def cg_once(K, torch, p, dev, stream, handle=None):
     X = torch.from_numpy(p["X"]).to(dev)
     b = torch.from_numpy(p["b"]).to(dev)
-    K.krr_cg_solve(X, b, p["sigma"], p["gamma"], tol=1e-6, maxit=1)  # workspace
+    K.krr_cg_solve(X, b, p["sigma"], p["gamma"], tol=1e-6, maxit=1, handle=handle)  # workspace
     (x, info), ms = _timed(torch, stream, lambda: K.krr_cg_solve(X, b, p["sigma"], p["gamma"],
-                                                                 tol=1e-6, maxit=20000))
+                                                                 tol=1e-6, maxit=20000,
+                                                                 handle=handle))
     return {"time_to_solution_ms": ms, "relres_true": info["relres_true"],
             "iters": info["outer_iters"], "status": K.status_string(info["status"])}
 
@@ -526,6 +533,55 @@ def gradient_form(K, torch, inputs, args, rank, dev, stream):
     (gs, gg, gX, infos), ms = _timed(torch, stream, lambda: K.krr_mll_grad(
         X, y, gp["sigma"], gp["gamma"], n_probes=32, seed=gp["seed"]))
     return dict(N=args.grad_n, d=4, probes=32, time_ms=ms, dlogsigma=gs, dloggamma=gg, **_report(K, infos))
+
+
+def matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes):
+    """The Matern kernel (Sec. 6.1, smoothness 3/2) on its own handle: the
+    single-column product on the 2^20-point cube (h = 0.1) against its ALU
+    roofline, and time to a 1e-6 residual on the 2000-point problem and on
+    two-class clouds shaped like the paper's Matern table (N = 1000)."""
+    h = K.Handle()
+    K.krr_set_option(K.KRR_OPT_KERNEL, K.KRR_KERNEL_MATERN32, handle=h)
+    hl, gamma = 0.1, 1e-3
+    y = torch.empty_like(q)
+    K.krr_kernel_mvp(X, q, hl, gamma, out=y, handle=h)
+    rsqrt_rate = K.krr_measure_rsqrt_rate(handle=h)
+    torch.cuda.synchronize(dev)
+    K.krr_profile_enable(True, handle=h)
+    reps = 3
+    (_, ms) = _timed(torch, stream, lambda: [K.krr_kernel_mvp(X, q, hl, gamma, out=y, handle=h)
+                                             for _ in range(reps)])
+    prof = K.krr_profile_read(handle=h)
+    K.krr_profile_enable(False, handle=h)
+    n = X.shape[0]
+    pairs = float(n) * n
+    kern_ms = prof["product_ms"] / max(prof["product_launches"], 1)
+    # direct form per pair: d differences, d multiply-adds, three multiplies
+    # (r = r^2 rsqrt(r^2), a = s r, the exponent), the (1 + a) e FMA and the
+    # weighted accumulate on the FP32 lanes; one rsqrt and one EX2 on MUFU
+    d = X.shape[1]
+    fp32_ops = 2 * d + 5
+    peak = min(fp32_lanes / fp32_ops, 1.0 / (1.0 / ex2_rate + 1.0 / rsqrt_rate))
+    product = {"N": n, "d": d, "h": hl, "step_ms": ms / reps, "kernel_ms": kern_ms,
+               "Gpairs_per_s": pairs / (kern_ms / 1e3) / 1e9,
+               "roofline": {"bound": "alu", "peak_Gpairs_per_s": peak / 1e9,
+                            "frac": pairs / (kern_ms / 1e3) / peak,
+                            "peak_source": f"min(FP32 lanes {fp32_lanes / 1e12:.2f}e12 / {fp32_ops}, "
+                                           f"1 / (1/EX2 {ex2_rate / 1e12:.2f}e12 + 1/rsqrt "
+                                           f"{rsqrt_rate / 1e12:.2f}e12))",
+                            "kernel": "mvp_dirm_kernel<3, 1, Matern>"}}
+    solves = {}
+    sp = inputs.small_problem(seed=rank)
+    sp = dict(sp, sigma=0.1)  # h = 0.1 on the 2000-point problem
+    solves["small_2000pt_2d"] = {"fgmres": solve_once(K, torch, sp, dev, stream, "fp32", handle=h),
+                                 "cg": cg_once(K, torch, sp, dev, stream, handle=h)}
+    for dd in (3, 14, 25, 61):
+        mp = inputs.matern_problem(seed=rank + dd, N=1000, d=dd)
+        solves[f"classification_1000pt_d{dd}"] = {
+            "fgmres": solve_once(K, torch, mp, dev, stream, "fp32", handle=h),
+            "cg": cg_once(K, torch, mp, dev, stream, handle=h)}
+    h.close()
+    return {"product": product, "solves": solves}
 
 
 def main(argv=None):

@@ -132,9 +132,28 @@ typedef enum {
      * tensor memory) instead of the default mma.sync kernel.  Same results to
      * the float32 bar; on GB300 the default is faster (measured: 16 columns
      * at 2^20 points, 450 ms vs 584 ms). */
-    KRR_OPT_TCGEN05 = 1
+    KRR_OPT_TCGEN05 = 1,
+    /* value: a krr_kernel_family.  The kernel function every product and
+     * solver of this handle uses (default KRR_KERNEL_GAUSSIAN).  Under
+     * KRR_KERNEL_MATERN32 the `sigma` argument of every call is the Matern
+     * length scale h.  krr_mll_grad supports the Gaussian only and returns
+     * KRR_ERR_UNIMPLEMENTED otherwise. */
+    KRR_OPT_KERNEL = 2
 } krr_option;
-/* Set option `option` of h to `value`.  Unknown options: KRR_ERR_INVALID_ARG. */
+
+/* Kernel functions (KRR_OPT_KERNEL). */
+typedef enum {
+    /* exp(-|x_i - x_j|^2 / (2 sigma^2))  (Eq. 2) */
+    KRR_KERNEL_GAUSSIAN = 0,
+    /* Matern, smoothness 3/2 (Sec. 6.1, Eq. MaternKernel):
+     * (1 + sqrt(3) r / h) exp(-sqrt(3) r / h), r = |x_i - x_j|, h = sigma.
+     * Every pair takes the direct form (differences, sqrt, one exponential),
+     * on the CUDA cores at float32 whatever `prec` asks; the accurate
+     * products of the solvers evaluate it in float-float. */
+    KRR_KERNEL_MATERN32 = 1
+} krr_kernel_family;
+/* Set option `option` of h to `value`.  Unknown options or values:
+ * KRR_ERR_INVALID_ARG. */
 krr_status krr_set_option(krr_handle h, int option, int value);
 
 /* ----------------------------------------------------------- kernel MVP
@@ -200,7 +219,7 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d,
                             krr_solve_info* info, void* stream);
 
 /* ------------------------------------------------------ flexible CG solve
- * Flexible CG (Notay; the paper's second outer iteration, Sec. 4.3) on
+ * Flexible CG (Notay; the paper's second outer iteration, Sec. 4.2) on
  * K = K_hat + gamma I with the same truncated-CG preconditioner on
  * M = K + delta I: each new search direction is the preconditioned residual
  * made K-orthogonal to the previous opts->restart directions (the window),
@@ -255,13 +274,18 @@ krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int d,
  * the result).  Outputs are HOST doubles; any may be NULL. */
 krr_status krr_measure_alu_peaks(krr_handle h, double* ex2_per_s, double* ffma_per_s,
                                  double* ffma2_lanes_per_s, void* stream);
+/* Reciprocal square roots (rsqrtf, the one the Matern kernel takes per pair)
+ * per second on the handle's device at its current clocks, measured the same
+ * way (a few ms of GPU time; waits).  rsqrt_per_s: HOST double, not NULL. */
+krr_status krr_measure_rsqrt_rate(krr_handle h, double* rsqrt_per_s, void* stream);
 
 /* Launch and timing counters for measurement (not part of the method). */
 typedef struct {
     long long launches;     /* kernels the library launched since it was loaded
                                (a launch captured into a CUDA graph counts once) */
-    int product_launches;   /* fast-product kernel launches timed since the
-                               last read                                        */
+    int product_launches;   /* fast-product launches (single- or multi-column
+                               float32 / reduced-precision products, not the
+                               accurate product) timed since the last read      */
     double product_ms;      /* their summed device time (CUDA events recorded
                                on the stream each launch ran on)                */
     double product_pairs;   /* target x source pairs they evaluated, per column */
@@ -269,7 +293,7 @@ typedef struct {
                                tensor-core exponent path (the exponent
                                contraction on the tensor cores, one MUFU.EX2
                                and one FMA per pair on the CUDA cores); the
-                               rest ran the all-CUDA-core kernel              */
+                               rest ran the CUDA-core kernels                  */
 } krr_profile;
 /* Start (enable != 0) or stop timing the fast-product kernel on h; resets the
  * timed list.  Timing adds two event records per product launch. */

@@ -1,7 +1,7 @@
 """FP64 reference solvers for K x = b (test infrastructure only).
 
 * ``direct_solve``  -- Cholesky factorisation and two triangular solves, the
-  "Direct" column of Tables I-II (Sec. 5.1).  K is SPD (Sec. 3), so x is unique.
+  "Direct" column of Tables I-II (Sec. 6.1).  K is SPD (Sec. 3), so x is unique.
 * ``cg``            -- textbook conjugate gradient for SPD K (Sec. 3; Saad's
   CG).  Used unpreconditioned as the baseline and, truncated, as the inner
   preconditioner solve of Sec. 4.3 / Sec. 5.
@@ -12,12 +12,12 @@
   the inner solve being truncated CG on M = K + delta I = K_hat + (gamma+delta) I
   (Sec. 5, Eq. for M).
 * ``fcg`` / ``krr_fcg`` -- flexible CG, the paper's second outer iteration
-  (Sec. 4.3: Notay's flexible CG, whose search directions are
+  (Sec. 4.2: Notay's flexible CG, whose search directions are
   A-orthogonalised against the previous ones at every step), with the same
   truncated-CG preconditioner.
 
 Readings of the paper, where it is silent or ambiguous:
-* Stopping rule (Sec. 4.3): the relative residual |b - K x|_2 / |b|_2 <= tol.
+* Stopping rule (Sec. 4.2): the relative residual |b - K x|_2 / |b|_2 <= tol.
 * Alg. 1 indices are taken as the standard 1-based FGMRES(m); w is
   orthogonalised against v_1..v_j one at a time (modified Gram-Schmidt) as the
   inner loop of Alg. 1 states; h_{ij} = (K z_j, v_i).
@@ -102,7 +102,7 @@ def fgmres(matvec, b, restart, tol, max_cycles, inner=None, x0=None):
         return res
     m = restart
     for _cycle in range(max_cycles):
-        # line 1: r0 = b - K x0, beta = |r0|, v1 = r0 / beta
+        # cycle start: r0 = b - K x0, beta = |r0|, v1 = r0 / beta
         r0 = b - matvec(x)
         beta = float(np.linalg.norm(r0))
         if beta <= tol * bnorm:
@@ -115,23 +115,23 @@ def fgmres(matvec, b, restart, tol, max_cycles, inner=None, x0=None):
         k = 0
         y = None
         for j in range(m):
-            # line 4: inner preconditioner solve M_j z_j = v_j
+            # preconditioning: inner solve M_j z_j = v_j
             if inner is None:
                 Z[j] = V[j]
             else:
                 Z[j], it = inner(V[j])
                 res.inner_iters += it
-            # line 5: w = K z_j
+            # product: w = K z_j
             w = matvec(Z[j])
-            # lines 6-8: modified Gram-Schmidt
+            # orthogonalisation: modified Gram-Schmidt
             for i in range(j + 1):
                 H[i, j] = w @ V[i]
                 w = w - H[i, j] * V[i]
-            # line 9: h_{j+1,j} = |w|, v_{j+1} = w / h_{j+1,j}
+            # new basis vector: h_{j+1,j} = |w|, v_{j+1} = w / h_{j+1,j}
             H[j + 1, j] = np.linalg.norm(w)
             k = j + 1
             res.outer_iters += 1
-            # line 12 (per step): y = argmin |beta e1 - Hbar y|
+            # least squares (each step): y = argmin |beta e1 - Hbar y|
             e1 = np.zeros(k + 1)
             e1[0] = beta
             y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
@@ -142,10 +142,10 @@ def fgmres(matvec, b, restart, tol, max_cycles, inner=None, x0=None):
             V[j + 1] = w / H[j + 1, j]
             if est <= tol * bnorm:
                 break
-        # line 12: x = x0 + Z y
+        # update: x = x0 + Z y
         x = x + Z[:k].T @ y
         res.last_cycle = (V[:k + 1].copy(), Z[:k].copy(), H[:k + 1, :k].copy(), beta)
-        # line 13: stop if satisfied, else restart from x
+        # test: stop if satisfied, else restart from x
         if np.linalg.norm(b - matvec(x)) <= tol * bnorm:
             break
     res.x = x
@@ -229,8 +229,8 @@ def fcg(matvec, b, tol, maxit, mmax, inner=None, x0=None, keep=False):
 
 def krr_fcg(matvec_K, matvec_M, b, mmax=30, tol=1e-6, maxit=500, inner_tol=1e-4,
             inner_maxit=1000):
-    """Flexible CG on K, preconditioned by truncated CG on M = K + delta I
-    (Sec. 4.3 / Sec. 5); matvec_M applies M."""
+    """Flexible CG (Sec. 4.2) on K, preconditioned by truncated CG on
+    M = K + delta I (Sec. 4.3 / Sec. 5); matvec_M applies M."""
     def inner(v):
         z, it = cg(matvec_M, v, inner_tol, inner_maxit)
         return z, it

@@ -85,6 +85,7 @@ _SIGNATURES = {
                       _vp, ctypes.POINTER(krr_solve_info), _vp], _int),
     "krr_measure_alu_peaks": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
                                _vp], _int),
+    "krr_measure_rsqrt_rate": ([_vp, ctypes.POINTER(_d), _vp], _int),
     "krr_profile_enable": ([_vp, _int], _int),
     "krr_set_option": ([_vp, _int, _int], _int),
     "krr_kernel_mvp_noalloc": ([_vp, _i64, _int, _f, _f, _vp, _int, _vp, _vp], _int),
@@ -352,12 +353,24 @@ def krr_measure_alu_peaks(handle=None, stream=None):
     return a.value, b.value, c.value
 
 
+def krr_measure_rsqrt_rate(handle=None, stream=None):
+    """rsqrtf results per second on the current device."""
+    h = handle or default_handle()
+    a = _d()
+    h.check(lib().krr_measure_rsqrt_rate(h.h, ctypes.byref(a), stream))
+    return a.value
+
+
 KRR_OPT_TCGEN05 = 1
+KRR_OPT_KERNEL = 2
+KRR_KERNEL_GAUSSIAN, KRR_KERNEL_MATERN32 = 0, 1
 
 
 def krr_set_option(option, value, handle=None):
     """Set a handle option (KRR_OPT_TCGEN05: multi-column tensor-core
-    products on the tcgen05 / tensor-memory kernel)."""
+    products on the tcgen05 / tensor-memory kernel; KRR_OPT_KERNEL: the
+    kernel function, KRR_KERNEL_GAUSSIAN or KRR_KERNEL_MATERN32, whose length
+    scale h is then passed as sigma)."""
     h = handle or default_handle()
     h.check(lib().krr_set_option(h.h, int(option), int(value)))
 

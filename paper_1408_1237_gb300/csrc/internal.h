@@ -42,8 +42,13 @@ struct PointsDev {
   int64_t N = 0, Npad = 0;
   int d = 0;            // prepared coordinates per point (padded_dim of d_in)
   int d_in = 0;         // the caller's dimension
-  float scale = 0.f;    // s = sqrt(log2(e) / (2 sigma^2))
-  double s2 = 0.0;      // s^2 = log2(e) / (2 sigma^2) in double
+  // kernel family (KRR_KERNEL_*) and its scale s, with x^ = s x:
+  //   Gaussian:   s = sqrt(log2(e) / (2 sigma^2)), value 2^(-|x^_i - x^_j|^2)
+  //   Matern 3/2: s = sqrt(3) / h,                 value (1 + a) 2^(-a log2(e)),
+  //               a = |x^_i - x^_j|
+  int kfam = 0;
+  float scale = 0.f;
+  double s2 = 0.0;      // s^2 in double
   float* xs = nullptr;  // tile-blocked SoA of the raw coordinates, Npad*d floats
   int* perm = nullptr;  // sorted position -> original index
   int T = 1;            // targets per thread of the product kernels
@@ -96,6 +101,8 @@ struct Ctx {
   // multi-column tensor-core products on the tcgen05 / tensor-memory kernel
   // instead of the mma.sync kernel (krr_set_option)
   bool use_tcgen05 = false;
+  // kernel function of every product and solve (KRR_KERNEL_*, krr_set_option)
+  int kernel_family = 0;
   // profiling of the fast product kernel (krr_profile_enable / _read)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop

@@ -249,6 +249,11 @@ krr_status krr_set_option(krr_handle h, int option, int value) {
     case KRR_OPT_TCGEN05:
       h->ctx.use_tcgen05 = value != 0;
       return KRR_OK;
+    case KRR_OPT_KERNEL:
+      if (value != KRR_KERNEL_GAUSSIAN && value != KRR_KERNEL_MATERN32)
+        return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: unknown kernel family %d", value);
+      h->ctx.kernel_family = value;
+      return KRR_OK;
     default:
       return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: unknown option %d", option);
   }

@@ -26,7 +26,7 @@
 //     working precision while needing two grid reductions instead of j+1),
 //     Hessenberg matrix, Givens rotations and least squares in FP64;
 //   * the iterate x in float-float (two float32 arrays, returned as FP64) and the restart
-//     residual r = b - K x (Alg. 1 line 1) from the accurate product of
+//     residual r = b - K x (each cycle start of Alg. 1) from the accurate product of
 //     mvp_acc.cu, so a restart acts as a step of iterative refinement and the
 //     true residual reaches tolerances the float32 products alone cannot.
 #include <algorithm>
@@ -440,7 +440,7 @@ __global__ void x_update_kernel(KState* S0, const float* __restrict__ Z, int64_t
 }
 
 // One thread per column, after the accurate residual: convergence test and
-// the next cycle's start (Alg. 1 lines 1 and 13).  tol_stop < tol leaves
+// the next cycle's start (the restart test and cycle start of Alg. 1).  tol_stop < tol leaves
 // room for rounding.  A column that has stopped keeps its verdict (its
 // residual is not recomputed, so the test repeats it).
 __global__ void restart_check_kernel(KState* S0, int ncols, Group* G, Cond rc, double tol_stop) {
@@ -585,7 +585,7 @@ __global__ void fill_zero_kernel(float* __restrict__ a, int64_t n) {
 #undef KRR_GRID_LOOP
 
 // ------------------------------------------------------- flexible CG ---
-// Flexible CG (Notay; the paper's second outer iteration, Sec. 4.3): step i
+// Flexible CG (Notay; the paper's second outer iteration, Sec. 4.2): step i
 // takes the preconditioned residual z_i (truncated inner CG on M) and makes it
 // A-orthogonal to the previous (at most mmax) directions,
 //   d_i = z_i - sum_k beta_k d_k,  beta_k = (z_i . A d_k) / (d_k . A d_k),
@@ -1571,6 +1571,7 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
       if ((e = sub_context(c, br.size(), &bc))) return cuda_error(c, e, fn);
       bc->plan_slots = slots;
       bc->use_tcgen05 = c.use_tcgen05;
+      bc->kernel_family = c.kernel_family;
       if (col0 == 0 && (e = prepare_points(*bc, pr.X, pr.N, d, sigma, "bat.pts", pts[k], st)))
         return cuda_error(c, e, fn);
       auto so = std::make_unique<Solver>(*bc);

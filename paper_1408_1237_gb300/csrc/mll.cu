@@ -322,6 +322,8 @@ extern "C" krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int 
   if (!h) return KRR_ERR_INVALID_ARG;
   Ctx& c = h->ctx;
   const char* fn = "krr_mll_grad";
+  if (c.kernel_family != KRR_KERNEL_GAUSSIAN)
+    return set_error(c, KRR_ERR_UNIMPLEMENTED, "%s: the gradient is built for the Gaussian kernel only", fn);
   krr_status s = check_points(c, fn, X, N, d, sigma);
   if (s) return s;
   if (!(gamma > 0.f) || !std::isfinite(gamma))

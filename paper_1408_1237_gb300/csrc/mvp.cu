@@ -33,6 +33,11 @@
 //    source split writes one FP64 partial per target, and a finalize kernel
 //    adds the splits in fixed order (deterministic), applies 2^(-|x^_i|^2), the
 //    shift term and the fused epilogue (axpy, dot, scatter).
+//  * Other kernel functions (the Matern kernel of Sec. 6.1) take the direct
+//    form in the multi-column CUDA-core kernel, templated on the pair
+//    function (KF): a = s |x_i - x_j| with s = sqrt(3) / h by one reciprocal
+//    square root and one multiply, then (1 + a) 2^(-a log2(e)) by one
+//    MUFU.EX2 and one FMA.
 #include <algorithm>
 #include <cmath>
 
@@ -293,6 +298,17 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   }
 }
 
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e) = 1 / ln 2
+
+// Matern 3/2 value from the squared raw distance: a = s r, (1 + a) 2^(-a log2 e).
+// r = r2 / sqrt(r2) through the reciprocal square root (a 2-ulp routine); the
+// clamp keeps r2 = 0 (a point against itself) at a = 0 instead of 0 * inf.
+__device__ __forceinline__ float matern32_value(float r2, float s) {
+  const float a = s * (r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+  const float e = ex2(a * -kLog2e);
+  return fmaf(a, e, e);
+}
+
 // Direct-form warp blocks for several columns at once: one exponential per
 // pair, shared by the m <= MC weight columns (a pair costs d subtractions, d
 // multiply-adds, a multiply by -s^2, one MUFU.EX2 and m FMAs).  One target
@@ -312,7 +328,8 @@ constexpr size_t dirm_smem_bytes() {
 }
 
 // (high-dimensional instances hold D coordinates per thread: one CTA per SM)
-template <int D, int MC>
+// KF: pair function, 0 = Gaussian 2^(-s^2 r^2), 1 = Matern 3/2.
+template <int D, int MC, int KF>
 __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_dirm_kernel(const MvpParams p, const float* __restrict__ Q,
                                                                       int64_t q_stride, int m, int T, int64_t slot0) {
   constexpr int RS = dirm_stages<D, MC>();
@@ -339,6 +356,7 @@ __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_dirm_kernel(const Mvp
   }
   if (blockIdx.y == 0 && valid) p.fac[i] = 1.f;
   const float ns2 = -(p.s * p.s);
+  const float s = p.s;
 
   const int t_begin = blockIdx.y * p.tiles_per_split;
   const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
@@ -403,7 +421,12 @@ __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_dirm_kernel(const Mvp
           e[3] = fmaf(d3, d3, e[3]);
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) e[v] = ex2(e[v] * ns2);
+        for (int v = 0; v < 4; ++v) {
+          if constexpr (KF == 0)
+            e[v] = ex2(e[v] * ns2);
+          else
+            e[v] = matern32_value(e[v], s);
+        }
 #pragma unroll
         for (int c = 0; c < MC; ++c) {
           const float4 qq = *reinterpret_cast<const float4*>(cq + c * TS + j);
@@ -603,13 +626,13 @@ cudaError_t dispatch_T(MvpParams p, int T, const Plan& pl, cudaStream_t st) {
   return cudaErrorNotSupported;
 }
 
-template <int D, int MC>
+template <int D, int MC, int KF>
 cudaError_t set_dirm_attr() {
   static bool done[128] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 128 && done[dev]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mvp_dirm_kernel<D, MC>,
+  cudaError_t e = cudaFuncSetAttribute(mvp_dirm_kernel<D, MC, KF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)dirm_smem_bytes<D, MC>());
   if (!e && dev < 128) done[dev] = true;
@@ -618,7 +641,7 @@ cudaError_t set_dirm_attr() {
 
 // Multi-column direct-form launch (or, with launch = false, only its
 // attribute), MC the smallest of 4, 8, 16 that holds m columns.
-template <int D>
+template <int D, int KF>
 cudaError_t dirm_typed(const MvpParams& p, const float* Q, int64_t q_stride, int m, int T,
                        int64_t slot0, const Plan& pl, cudaStream_t st, bool launch) {
   const int bpc = NW / T;
@@ -627,9 +650,9 @@ cudaError_t dirm_typed(const MvpParams& p, const float* Q, int64_t q_stride, int
   pp.tiles_per_split = pl.tiles_per_split;
   cudaError_t e;
 #define KRR_DIRM(MCV)                                                                       \
-  if ((e = set_dirm_attr<D, MCV>())) return e;                                             \
+  if ((e = set_dirm_attr<D, MCV, KF>())) return e;                                         \
   if (launch) {                                                                            \
-    mvp_dirm_kernel<D, MCV><<<grid, NT, dirm_smem_bytes<D, MCV>(), st>>>(pp, Q, q_stride, m, T, slot0); \
+    mvp_dirm_kernel<D, MCV, KF><<<grid, NT, dirm_smem_bytes<D, MCV>(), st>>>(pp, Q, q_stride, m, T, slot0); \
     count_launch();                                                                        \
   }                                                                                        \
   return cudaGetLastError();
@@ -640,24 +663,33 @@ cudaError_t dirm_typed(const MvpParams& p, const float* Q, int64_t q_stride, int
 #undef KRR_DIRM
 }
 
-cudaError_t dirm_dispatch(const MvpParams& p, int d, const float* Q, int64_t q_stride, int m, int T,
-                          int64_t slot0, const Plan& pl, cudaStream_t st, bool launch) {
-  if (T < 1 || T > NW || NW % T) return cudaErrorNotSupported;
+template <int KF>
+cudaError_t dirm_dispatch_k(const MvpParams& p, int d, const float* Q, int64_t q_stride, int m, int T,
+                            int64_t slot0, const Plan& pl, cudaStream_t st, bool launch) {
   switch (d) {
-    case 1: return dirm_typed<1>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 2: return dirm_typed<2>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 3: return dirm_typed<3>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 4: return dirm_typed<4>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 5: return dirm_typed<5>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 6: return dirm_typed<6>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 7: return dirm_typed<7>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 8: return dirm_typed<8>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 16: return dirm_typed<16>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 32: return dirm_typed<32>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 48: return dirm_typed<48>(p, Q, q_stride, m, T, slot0, pl, st, launch);
-    case 64: return dirm_typed<64>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 1: return dirm_typed<1, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 2: return dirm_typed<2, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 3: return dirm_typed<3, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 4: return dirm_typed<4, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 5: return dirm_typed<5, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 6: return dirm_typed<6, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 7: return dirm_typed<7, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 8: return dirm_typed<8, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 16: return dirm_typed<16, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 32: return dirm_typed<32, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 48: return dirm_typed<48, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
+    case 64: return dirm_typed<64, KF>(p, Q, q_stride, m, T, slot0, pl, st, launch);
     default: return cudaErrorNotSupported;
   }
+}
+
+// kf: the kernel family of the points (KRR_KERNEL_*)
+cudaError_t dirm_dispatch(const MvpParams& p, int d, int kf, const float* Q, int64_t q_stride, int m,
+                          int T, int64_t slot0, const Plan& pl, cudaStream_t st, bool launch) {
+  if (T < 1 || T > NW || NW % T) return cudaErrorNotSupported;
+  if (kf == KRR_KERNEL_MATERN32) return dirm_dispatch_k<1>(p, d, Q, q_stride, m, T, slot0, pl, st, launch);
+  if (kf != KRR_KERNEL_GAUSSIAN) return cudaErrorNotSupported;
+  return dirm_dispatch_k<0>(p, d, Q, q_stride, m, T, slot0, pl, st, launch);
 }
 
 // Source splits of the multi-column kernels (one CTA per super-block): the
@@ -721,7 +753,9 @@ int mvp_targets_per_thread(int d, int64_t N) {
 
 cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
-  if (Tp.d > 8) return mvp_multi_reserve(c, Tp, Sp, 1, KRR_FP32, st);  // direct form, one column
+  // direct form only (above 8 dimensions, or a kernel other than the
+  // Gaussian): the multi-column kernel with one column
+  if (Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN) return mvp_multi_reserve(c, Tp, Sp, 1, KRR_FP32, st);
   if (Tp.d < 1) return cudaErrorNotSupported;
   const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
   void* v;
@@ -742,7 +776,7 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
       return e;
     MvpParams p{};
     p.nblk = Tp.nsb;
-    if ((e = dirm_dispatch(p, Tp.d, nullptr, 0, 1, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+    if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, 1, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
   }
   switch (Tp.d) {
     case 1: return attrs_T<1>(Tp.T);
@@ -830,7 +864,7 @@ cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const flo
         default: e = dispatch_T<8>(p, Tp.T, pd, st); break;
       }
       if (e) return e;
-    } else if ((e = dirm_dispatch(p, Tp.d, q, Sp.Npad, 1, SB / 32, Tp.h_sb_nexp, pd, st, true))) {
+    } else if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, q, Sp.Npad, 1, SB / 32, Tp.h_sb_nexp, pd, st, true))) {
       return e;
     }
   }
@@ -859,7 +893,8 @@ cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const flo
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
                        const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                        cudaStream_t st) {
-  if (prec != KRR_FP32 || Tp.d > 8) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
+  if (prec != KRR_FP32 || Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN)
+    return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
   if (Tp.N == 0) return cudaSuccess;
   if (use_tcx(c, Tp)) return tcx_path(c, Tp, Sp, q, qdiag, shift, o, st);
   MvpParams p{};
@@ -938,7 +973,8 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
                               krr_precision prec, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
   if (m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
-  cudaError_t e = Tp.d > 8 ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
+  const bool direct_only = Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN;
+  cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
   void* v;
@@ -946,8 +982,8 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)m * Tp.Npad, &v))) return e;
   MvpParams p{};
   p.nblk = Tp.nsb;
-  if ((e = dirm_dispatch(p, Tp.d, nullptr, 0, m, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
-  if (Tp.d > 8) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
+  if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, m, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+  if (direct_only) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
   if (c.use_tcgen05)
     return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                              pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
@@ -976,7 +1012,8 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
   const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
-  cudaError_t e = Tp.d > 8 ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
+  const bool direct_only = Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN;
+  cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   void *part, *partd, *fac, *dpart, *dcnt;
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
@@ -986,6 +1023,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   if ((e = c.ws.get("mvp.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.fac = (float*)fac;
+  cudaEvent_t pev1 = prof_begin(c, Tp, Sp, st);
   // expanded-form super-blocks: all columns on the tensor cores (mma.sync
   // kernel; the tcgen05 / tensor-memory kernel when the handle asks for it)
   if (Tp.h_sb_nexp > 0) {
@@ -999,8 +1037,9 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   // direct-form super-blocks: all columns in one CUDA-core launch
   if (Tp.nsb > Tp.h_sb_nexp) {
     p.part = (double*)partd;
-    if ((e = dirm_dispatch(p, Tp.d, Q, Sp.Npad, m, SB / 32, Tp.h_sb_nexp, pd, st, true))) return e;
+    if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, Q, Sp.Npad, m, SB / 32, Tp.h_sb_nexp, pd, st, true))) return e;
   }
+  if (pev1) cudaEventRecord(pev1, st);
   FinParams f{};
   f.part = (const double*)part;
   f.splits = pt.splits;

@@ -1,5 +1,6 @@
 // Accurate kernel product for the true residual of the outer solver
-// (hot-path step A9, Alg. 1 lines 1 and 13: r = b - K x):
+// (hot-path step A9: the cycle-start residual and the convergence test of
+// Algorithm 1, r = b - K x):
 //
 //   out_i = cu u_i + cy (sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) q_j + shift q_i)
 //
@@ -17,9 +18,15 @@
 //     float-float; the result is within about 3e-12 (relative);
 //   * q_j (the FP64 iterate) arrives as float hi + lo; each product q_j Phi_ij
 //     is split exactly (FMA error term) and summed with TwoSum.
+// The Matern kernel of Sec. 6.1 (KF = 1) follows the same scheme: r^2 as
+// above; r = sqrt(r^2) in float-float (the correctly rounded square root of
+// the high part plus one Newton correction for the remainder); a = s r with
+// s = sqrt(3)/h split hi + lo; 2^(-a log2 e) by the same table and series
+// (log2 e split hi + lo); then (1 + a) times it in float-float.
 // A (warp, source tile) pair whose bounding boxes are farther apart than
-// s^2 d^2 > 30 contributes less than 2^-30 per term; it takes a plain float32
-// path into the low-order accumulator.  Each source split writes an FP64
+// s^2 d^2 > 30 (Gaussian; 625 for the Matern kernel, a > 25) contributes less
+// than 2^-30 per term; it takes a plain float32 path into the low-order
+// accumulator.  Each source split writes an FP64
 // partial per target; the finalize kernel sums splits in fixed order and
 // applies the epilogue in FP64 (deterministic).
 #include <algorithm>
@@ -34,10 +41,14 @@ namespace {
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
 constexpr int RS = 3;
-constexpr float FAR_E = 30.f;  // s^2 dist^2 beyond which a tile is far
+// s^2 dist^2 beyond which a tile is far: Gaussian 2^-30, Matern (1 + a) e^-a < 2^-30
+template <int KF>
+constexpr float far_e() { return KF == 0 ? 30.f : 625.f; }
 
 struct AccConst {
   float s2h, s2l;  // s^2 = s2h + s2l
+  float sh, sl;    // s = sh + sl (Matern: sqrt(3) / h)
+  float l2eh, l2el;  // log2(e) = l2eh + l2el
   float c1h, c1l;  // ln 2 = c1h + c1l
   float c2, c3, c4;  // (ln 2)^k / k!, k = 2..4
   float th[64], tl[64];  // 2^(k/64) = th[k] + tl[k]
@@ -73,17 +84,15 @@ __device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) - (b + bb);
 }
 
-// exp2(-s^2 |xi - xj|^2) as the float-float H + L2 (xj: source coordinates,
-// TS apart).
+// r^2 = sum_k (xi_k - xj_k)^2 as the float-float rh + rl, the differences
+// exact (xj: source coordinates, TS apart).
 template <int D>
-__device__ __forceinline__ void acc_exp(const float (&xi)[D], const float* __restrict__ xj,
-                                        const AccConst& k, const float* __restrict__ tab_h,
-                                        const float* __restrict__ tab_l, float& Hout, float& Lout) {
-  // r^2 = sum_k (dh + dl)^2 in float-float, the differences exact
+__device__ __forceinline__ void acc_r2(const float (&xi)[D], const float* __restrict__ xj,
+                                       float& rh, float& rl) {
   float dh, dl;
   two_diff(xi[0], xj[0], dh, dl);
-  float rh = dh * dh;
-  float rl = fmaf(dh, dh, -rh) + 2.f * dh * dl;
+  rh = dh * dh;
+  rl = fmaf(dh, dh, -rh) + 2.f * dh * dl;
 #pragma unroll
   for (int c = 1; c < D; ++c) {
     two_diff(xi[c], xj[c * TS], dh, dl);
@@ -94,9 +103,12 @@ __device__ __forceinline__ void acc_exp(const float (&xi)[D], const float* __res
     rh = s;
     rl += e + pe;
   }
-  // e = -(s2h + s2l)(rh + rl)
-  const float eh = -k.s2h * rh;
-  const float el = fmaf(-k.s2h, rh, -eh) - fmaf(k.s2h, rl, k.s2l * rh);
+}
+
+// 2^(eh + el) (eh <= 0, |el| small) as the float-float Hout + Lout.
+__device__ __forceinline__ void acc_exp2(float eh, float el, const AccConst& k,
+                                         const float* __restrict__ tab_h,
+                                         const float* __restrict__ tab_l, float& Hout, float& Lout) {
   // e = n + j/64 + (r + el), m = 64 n + j = rint(64 eh); below -200 the value
   // flushes to zero anyway
   const float y = 64.f * fmaxf(eh, -200.f);  // exact scaling
@@ -125,6 +137,55 @@ __device__ __forceinline__ void acc_exp(const float (&xi)[D], const float* __res
   Lout = L2 * sc;
 }
 
+// Kernel value of the pair (xi, xj) as the float-float Hout + Lout:
+//   KF = 0: exp2(-s^2 r^2) (the Gaussian);
+//   KF = 1: (1 + a) exp2(-a log2 e), a = s r (the Matern kernel, smoothness 3/2).
+template <int D, int KF>
+__device__ __forceinline__ void acc_kval(const float (&xi)[D], const float* __restrict__ xj,
+                                         const AccConst& k, const float* __restrict__ tab_h,
+                                         const float* __restrict__ tab_l, float& Hout, float& Lout) {
+  float rh, rl;
+  acc_r2<D>(xi, xj, rh, rl);
+  if constexpr (KF == 0) {
+    // e = -(s2h + s2l)(rh + rl)
+    const float eh = -k.s2h * rh;
+    const float el = fmaf(-k.s2h, rh, -eh) - fmaf(k.s2h, rl, k.s2l * rh);
+    acc_exp2(eh, el, k, tab_h, tab_l, Hout, Lout);
+  } else {
+    // r = sqrt(rh + rl): uh the correctly rounded sqrt(rh), whose remainder
+    // rh - uh^2 is exact by FMA; one Newton step gives the low part
+    const float uh = __fsqrt_rn(rh);
+    const float ul = uh > 0.f ? __fdividef(fmaf(-uh, uh, rh) + rl, 2.f * uh) : 0.f;
+    // a = (sh + sl)(uh + ul)
+    const float ah = k.sh * uh;
+    const float al = fmaf(k.sh, uh, -ah) + fmaf(k.sh, ul, k.sl * uh);
+    // e = -(l2eh + l2el)(ah + al)
+    const float p = k.l2eh * ah;
+    const float eh = -p;
+    const float el = -(fmaf(k.l2eh, ah, -p) + fmaf(k.l2eh, al, k.l2el * ah));
+    float Eh, El;
+    acc_exp2(eh, el, k, tab_h, tab_l, Eh, El);
+    // (1 + ah + al)(Eh + El)
+    float oh, ol;
+    two_sum(1.f, ah, oh, ol);
+    ol += al;
+    Hout = oh * Eh;
+    Lout = fmaf(oh, Eh, -Hout) + fmaf(oh, El, ol * Eh);
+  }
+}
+
+// Float32 kernel value of a far pair from its squared distance.
+template <int KF>
+__device__ __forceinline__ float far_value(float r2, const AccConst& k) {
+  if constexpr (KF == 0) {
+    return ex2(-k.s2h * r2);
+  } else {
+    const float a = k.sh * (r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+    const float e = ex2(-k.l2eh * a);
+    return fmaf(a, e, e);
+  }
+}
+
 // (qh + ql)(H + L2) added into (S, L): the product's high part exactly split
 // (FMA error term) and added with TwoSum.
 __device__ __forceinline__ void acc_fma(float qh, float ql, float H, float L2, float& S, float& L) {
@@ -136,18 +197,18 @@ __device__ __forceinline__ void acc_fma(float qh, float ql, float H, float L2, f
   L += e + ae + fmaf(qh, L2, ql * H);
 }
 
-// Accurate q * exp2(-s^2 |xi - xj|^2) added into (S, L).
-template <int D>
+// Accurate q * k(xi, xj) added into (S, L).
+template <int D, int KF>
 __device__ __forceinline__ void acc_pair(const float (&xi)[D], const float* __restrict__ xj,
                                          float qh, float ql, float& S, float& L,
                                          const AccConst& k, const float* __restrict__ tab_h,
                                          const float* __restrict__ tab_l) {
   float H, L2;
-  acc_exp<D>(xi, xj, k, tab_h, tab_l, H, L2);
+  acc_kval<D, KF>(xi, xj, k, tab_h, tab_l, H, L2);
   acc_fma(qh, ql, H, L2, S, L);
 }
 
-template <int D, int TA>
+template <int D, int TA, int KF>
 __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
   constexpr uint32_t kStageFloats = (D + 2) * TS;  // coordinates, qh, ql
   extern __shared__ __align__(128) float smem[];
@@ -247,13 +308,13 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
           dist2 = fmaf(g, g, dist2);
         }
       }
-      if (s2h * dist2 <= FAR_E) {
+      if (s2h * dist2 <= far_e<KF>()) {
 #pragma unroll 2
         for (int j = 0; j < TS; ++j) {
           const float qh = sq[j], ql = sl[j];
 #pragma unroll
           for (int u = 0; u < TA; ++u)
-            acc_pair<D>(xi[u], st + j, qh, ql, S[u], L[u], p.k, tab_h, tab_l);
+            acc_pair<D, KF>(xi[u], st + j, qh, ql, S[u], L[u], p.k, tab_h, tab_l);
         }
       } else {
         for (int j = 0; j < TS; ++j) {
@@ -266,7 +327,7 @@ __global__ void __launch_bounds__(NT) mvp_acc_kernel(const AccParams p) {
               const float dd = xi[u][c] - st[c * TS + j];
               r2 = fmaf(dd, dd, r2);
             }
-            L[u] = fmaf(qh, ex2(-s2h * r2), L[u]);
+            L[u] = fmaf(qh, far_value<KF>(r2, p.k), L[u]);
           }
         }
       }
@@ -303,7 +364,7 @@ constexpr size_t accm_smem_bytes() {
   return sizeof(float) * RSM * (D + 2 * AM) * TS;
 }
 
-template <int D>
+template <int D, int KF>
 __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_accm_kernel(const AccParams p, int m) {
   constexpr uint32_t kStage = (D + 2 * AM) * TS;
   extern __shared__ __align__(128) float smem[];
@@ -402,11 +463,11 @@ __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_accm_kernel(const Acc
           dist2 = fmaf(g, g, dist2);
         }
       }
-      if (s2h * dist2 <= FAR_E) {
+      if (s2h * dist2 <= far_e<KF>()) {
 #pragma unroll 1
         for (int j = 0; j < TS; ++j) {
           float H, L2;
-          acc_exp<D>(xi, st + j, p.k, tab_h, tab_l, H, L2);
+          acc_kval<D, KF>(xi, st + j, p.k, tab_h, tab_l, H, L2);
 #pragma unroll
           for (int a = 0; a < AM; ++a)
             if (a < na) acc_fma(sq[a * TS + j], sl[a * TS + j], H, L2, S[a], L[a]);
@@ -420,7 +481,7 @@ __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_accm_kernel(const Acc
             const float dd = xi[k] - st[k * TS + j];
             r2 = fmaf(dd, dd, r2);
           }
-          const float E = ex2(-s2h * r2);
+          const float E = far_value<KF>(r2, p.k);
 #pragma unroll
           for (int a = 0; a < AM; ++a)
             if (a < na) L[a] = fmaf(sq[a * TS + j], E, L[a]);
@@ -499,11 +560,13 @@ __global__ void __launch_bounds__(256) acc_finalize_kernel(const AccFin f) {
   }
 }
 
-// ln 2 in float-float, the Taylor coefficients (ln 2)^k / k! (k = 2..4) and
+// log2(e) and ln 2 in float-float, the Taylor coefficients (ln 2)^k / k! (k = 2..4) and
 // the table 2^(j/64), j = 0..63, in float-float.
 AccConst make_consts() {
   AccConst k;
   const double ln2 = std::log(2.0);
+  k.l2eh = (float)(1.0 / ln2);
+  k.l2el = (float)(1.0 / ln2 - (double)k.l2eh);
   k.c1h = (float)ln2;
   k.c1l = (float)(ln2 - (double)k.c1h);
   k.c2 = (float)(ln2 * ln2 / 2.0);
@@ -517,86 +580,104 @@ AccConst make_consts() {
   return k;
 }
 
-template <int D, int TA>
+template <int D, int TA, int KF>
 cudaError_t set_acc_attr() {
   static bool done[128] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 128 && done[dev]) return cudaSuccess;
   const size_t shm = sizeof(float) * RS * (D + 2) * TS;
-  cudaError_t e = cudaFuncSetAttribute(mvp_acc_kernel<D, TA>,
+  cudaError_t e = cudaFuncSetAttribute(mvp_acc_kernel<D, TA, KF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (!e && dev < 128) done[dev] = true;
   return e;
 }
 
-template <int D, int TA>
-cudaError_t launch_acc(const AccParams& p, int splits, int ncols, cudaStream_t st) {
+// Single-column accurate product (launch = false: only its attribute).
+template <int D, int TA, int KF>
+cudaError_t launch_acc(const AccParams& p, int splits, int ncols, cudaStream_t st, bool launch) {
   const size_t shm = sizeof(float) * RS * (D + 2) * TS;
-  cudaError_t e = set_acc_attr<D, TA>();
-  if (e) return e;
+  cudaError_t e = set_acc_attr<D, TA, KF>();
+  if (e || !launch) return e;
   dim3 grid((unsigned)((p.N + NT * TA - 1) / (NT * TA)), (unsigned)splits, (unsigned)ncols);
-  mvp_acc_kernel<D, TA><<<grid, NT, shm, st>>>(p); count_launch();
+  mvp_acc_kernel<D, TA, KF><<<grid, NT, shm, st>>>(p); count_launch();
   return cudaGetLastError();
 }
 
 constexpr int ACC_TA = 2;
 
-template <int D>
+template <int KF>
+cudaError_t launch_acc_d(const AccParams& p, int d, int splits, int ncols, cudaStream_t st,
+                         bool launch) {
+  switch (d) {
+    case 1: return launch_acc<1, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 2: return launch_acc<2, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 3: return launch_acc<3, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 4: return launch_acc<4, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 5: return launch_acc<5, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 6: return launch_acc<6, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 7: return launch_acc<7, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 8: return launch_acc<8, ACC_TA, KF>(p, splits, ncols, st, launch);
+    case 16: return launch_acc<16, 1, KF>(p, splits, ncols, st, launch);
+    case 32: return launch_acc<32, 1, KF>(p, splits, ncols, st, launch);
+    case 48: return launch_acc<48, 1, KF>(p, splits, ncols, st, launch);
+    case 64: return launch_acc<64, 1, KF>(p, splits, ncols, st, launch);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <int D, int KF>
 cudaError_t accm_attr_typed() {
   static bool done[128] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 128 && done[dev]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mvp_accm_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(mvp_accm_kernel<D, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)accm_smem_bytes<D>());
   if (!e && dev < 128) done[dev] = true;
   return e;
 }
 
-cudaError_t set_accm_attr(int d) {
-  switch (d) {
-    case 1: return accm_attr_typed<1>();
-    case 2: return accm_attr_typed<2>();
-    case 3: return accm_attr_typed<3>();
-    case 4: return accm_attr_typed<4>();
-    case 5: return accm_attr_typed<5>();
-    case 6: return accm_attr_typed<6>();
-    case 7: return accm_attr_typed<7>();
-    case 8: return accm_attr_typed<8>();
-    case 16: return accm_attr_typed<16>();
-    case 32: return accm_attr_typed<32>();
-    case 48: return accm_attr_typed<48>();
-    case 64: return accm_attr_typed<64>();
-    default: return cudaErrorNotSupported;
-  }
-}
-
-template <int D>
-cudaError_t launch_accm_typed(const AccParams& p, int splits, int ncols, cudaStream_t st) {
-  cudaError_t e = accm_attr_typed<D>();
-  if (e) return e;
+// Multi-column accurate product (launch = false: only its attribute).
+template <int D, int KF>
+cudaError_t launch_accm_typed(const AccParams& p, int splits, int ncols, cudaStream_t st, bool launch) {
+  cudaError_t e = accm_attr_typed<D, KF>();
+  if (e || !launch) return e;
   dim3 grid((unsigned)((p.N + NT - 1) / NT), (unsigned)splits);
-  mvp_accm_kernel<D><<<grid, NT, accm_smem_bytes<D>(), st>>>(p, ncols); count_launch();
+  mvp_accm_kernel<D, KF><<<grid, NT, accm_smem_bytes<D>(), st>>>(p, ncols); count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_accm(const AccParams& p, int d, int splits, int ncols, cudaStream_t st) {
+template <int KF>
+cudaError_t launch_accm_d(const AccParams& p, int d, int splits, int ncols, cudaStream_t st,
+                          bool launch) {
   switch (d) {
-    case 1: return launch_accm_typed<1>(p, splits, ncols, st);
-    case 2: return launch_accm_typed<2>(p, splits, ncols, st);
-    case 3: return launch_accm_typed<3>(p, splits, ncols, st);
-    case 4: return launch_accm_typed<4>(p, splits, ncols, st);
-    case 5: return launch_accm_typed<5>(p, splits, ncols, st);
-    case 6: return launch_accm_typed<6>(p, splits, ncols, st);
-    case 7: return launch_accm_typed<7>(p, splits, ncols, st);
-    case 8: return launch_accm_typed<8>(p, splits, ncols, st);
-    case 16: return launch_accm_typed<16>(p, splits, ncols, st);
-    case 32: return launch_accm_typed<32>(p, splits, ncols, st);
-    case 48: return launch_accm_typed<48>(p, splits, ncols, st);
-    case 64: return launch_accm_typed<64>(p, splits, ncols, st);
+    case 1: return launch_accm_typed<1, KF>(p, splits, ncols, st, launch);
+    case 2: return launch_accm_typed<2, KF>(p, splits, ncols, st, launch);
+    case 3: return launch_accm_typed<3, KF>(p, splits, ncols, st, launch);
+    case 4: return launch_accm_typed<4, KF>(p, splits, ncols, st, launch);
+    case 5: return launch_accm_typed<5, KF>(p, splits, ncols, st, launch);
+    case 6: return launch_accm_typed<6, KF>(p, splits, ncols, st, launch);
+    case 7: return launch_accm_typed<7, KF>(p, splits, ncols, st, launch);
+    case 8: return launch_accm_typed<8, KF>(p, splits, ncols, st, launch);
+    case 16: return launch_accm_typed<16, KF>(p, splits, ncols, st, launch);
+    case 32: return launch_accm_typed<32, KF>(p, splits, ncols, st, launch);
+    case 48: return launch_accm_typed<48, KF>(p, splits, ncols, st, launch);
+    case 64: return launch_accm_typed<64, KF>(p, splits, ncols, st, launch);
     default: return cudaErrorNotSupported;
   }
+}
+
+// The accurate product's kernel for the points' kernel family and column
+// count (launch = false: only the shared-memory attribute).
+cudaError_t launch_any(const AccParams& p, int d, int kf, int splits, int ncols, cudaStream_t st,
+                       bool launch) {
+  if (kf == KRR_KERNEL_MATERN32)
+    return ncols > 1 ? launch_accm_d<1>(p, d, splits, ncols, st, launch)
+                     : launch_acc_d<1>(p, d, splits, ncols, st, launch);
+  if (kf != KRR_KERNEL_GAUSSIAN) return cudaErrorNotSupported;
+  return ncols > 1 ? launch_accm_d<0>(p, d, splits, ncols, st, launch)
+                   : launch_acc_d<0>(p, d, splits, ncols, st, launch);
 }
 
 struct AccPlan {
@@ -631,22 +712,8 @@ cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int nco
   const bool fresh = c.ws.slots.find("acc.dotcnt") == c.ws.slots.end();
   if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
   if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
-  if (ncols > 1) return set_accm_attr(P.d);
-  switch (P.d) {
-    case 1: return set_acc_attr<1, ACC_TA>();
-    case 2: return set_acc_attr<2, ACC_TA>();
-    case 3: return set_acc_attr<3, ACC_TA>();
-    case 4: return set_acc_attr<4, ACC_TA>();
-    case 5: return set_acc_attr<5, ACC_TA>();
-    case 6: return set_acc_attr<6, ACC_TA>();
-    case 7: return set_acc_attr<7, ACC_TA>();
-    case 8: return set_acc_attr<8, ACC_TA>();
-    case 16: return set_acc_attr<16, 1>();
-    case 32: return set_acc_attr<32, 1>();
-    case 48: return set_acc_attr<48, 1>();
-    case 64: return set_acc_attr<64, 1>();
-    default: return cudaErrorNotSupported;
-  }
+  AccParams p{};
+  return launch_any(p, P.d, P.kfam, pl.splits, ncols, st, false);
 }
 
 cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const float* ql,
@@ -666,9 +733,13 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   p.ntiles = (int)(P.Npad / TS);
   p.err = c.d_err;
   p.k = make_consts();
-  // s^2 = log2(e) / (2 sigma^2) in float-float from the double value
+  // s^2 (Gaussian: log2(e) / (2 sigma^2); Matern: 3 / h^2) and s in
+  // float-float from the double values
   p.k.s2h = (float)P.s2;
   p.k.s2l = (float)(P.s2 - (double)p.k.s2h);
+  const double sd = std::sqrt(P.s2);
+  p.k.sh = (float)sd;
+  p.k.sl = (float)(sd - (double)p.k.sh);
   const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols);
   p.tiles_per_split = pl.tiles_per_split;
   p.splits = pl.splits;
@@ -680,23 +751,7 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   if ((e = c.ws.get("acc.dotpart", sizeof(double) * MAX_COLS * fin_blocks, &dpart))) return e;
   if ((e = c.ws.get("acc.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.part = (double*)part;
-  if (ncols > 1) {
-    e = launch_accm(p, P.d, pl.splits, ncols, st);
-  } else switch (P.d) {
-    case 1: e = launch_acc<1, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 2: e = launch_acc<2, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 3: e = launch_acc<3, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 4: e = launch_acc<4, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 5: e = launch_acc<5, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 6: e = launch_acc<6, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 7: e = launch_acc<7, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 8: e = launch_acc<8, ACC_TA>(p, pl.splits, ncols, st); break;
-    case 16: e = launch_acc<16, 1>(p, pl.splits, ncols, st); break;
-    case 32: e = launch_acc<32, 1>(p, pl.splits, ncols, st); break;
-    case 48: e = launch_acc<48, 1>(p, pl.splits, ncols, st); break;
-    case 64: e = launch_acc<64, 1>(p, pl.splits, ncols, st); break;
-    default: return cudaErrorNotSupported;
-  }
+  e = launch_any(p, P.d, P.kfam, pl.splits, ncols, st, true);
   if (e) return e;
   AccFin f{};
   f.part = p.part;

@@ -4,7 +4,9 @@
 // The Gaussian of Eq. 2 becomes a base-2 exponential of scaled points:
 //   exp(-|x_i - x_j|^2 / (2 sigma^2)) = 2^(-s^2 |x_i - x_j|^2),
 //   s = sqrt(log2(e) / (2 sigma^2)),
-// so the product kernels evaluate it with one MUFU.EX2 per pair.  The packed
+// so the product kernels evaluate it with one MUFU.EX2 per pair.  (Under the
+// Matern kernel of Sec. 6.1 the scale is s = sqrt(3) / h and the kernels form
+// a = s |x_i - x_j|; every block takes the direct form.)  The packed
 // copy keeps the caller's float32 coordinates unscaled: the kernels scale
 // only after recentring or differencing, where no significant digits are
 // lost (scaling first would round s*x at the magnitude of s*x).  Sorting the
@@ -315,12 +317,17 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.d = d;
   P.d_in = d_in;
   P.Npad = round_up(std::max<int64_t>(N, 1), PAD);
-  P.s2 = 1.0 / (std::log(2.0) * 2.0 * (double)sigma * (double)sigma);  // log2(e) / (2 sigma^2)
+  P.kfam = c.kernel_family;
+  if (P.kfam == KRR_KERNEL_MATERN32)
+    P.s2 = 3.0 / ((double)sigma * (double)sigma);  // (sqrt(3) / h)^2
+  else
+    P.s2 = 1.0 / (std::log(2.0) * 2.0 * (double)sigma * (double)sigma);  // log2(e) / (2 sigma^2)
   P.scale = (float)std::sqrt(P.s2);
   cudaError_t e;
   void *xs, *perm, *ka, *kb, *va, *vb, *hist, *bbp, *bb;
   const int nbb = (int)std::min<int64_t>(blocks_for(N, BBOX_THREADS), 256);
-  const int allow_expanded = d <= 8 ? 1 : 0;
+  // the expanded form factors the Gaussian; other kernels take the direct form
+  const int allow_expanded = (d <= 8 && P.kfam == KRR_KERNEL_GAUSSIAN) ? 1 : 0;
   const int nchunks = (int)blocks_for(N, SORT_CHUNK);
   if ((e = c.ws.get(t + ".xs", sizeof(float) * P.Npad * d, &xs))) return e;
   if ((e = c.ws.get(t + ".perm", sizeof(int) * P.Npad, &perm))) return e;

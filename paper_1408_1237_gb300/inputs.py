@@ -17,12 +17,17 @@ them with the shapes of Sec. 5.3 and Sec. 6):
   mixture     N = 262,144 in d = 2 from a 16-component Gaussian mixture
               (component std 0.02, means uniform in [0,1]^2), sigma 0.03,
               gamma 1e-3, b smooth field plus noise (kriging-like low-d cloud,
-              Sec. 6.3).
+              Sec. 6.2).
   batch       64 problems, N_k log-uniform in [1024, 65536], d = 8, points
               N(0, I), sigma 1, gamma_k log-uniform in [1e-4, 1e-1], 16
               right-hand sides N(0, 1) each.
   gradient    N = 65,536 uniform in [0,1]^4, sigma 0.2, gamma 1e-2, y a GP
               sample (random Fourier features, 4096 features) plus N(0, gamma).
+  matern      binary classification for the Matern kernel (the Sec. 6.1
+              table: d from 3 to 61, N up to 1,000): two classes N(+-mu, I_d),
+              |mu| = 1 along a random direction, labels b = +-1 (class 1 with
+              probability 1/2); length scale h = sqrt(d), gamma 1e-2,
+              delta 10 gamma, inner tolerance 1e-2.
 """
 import numpy as np
 
@@ -110,6 +115,17 @@ def gradient_problem(seed=0, N=65536, d=4, probes=32):
     y = gp_sample_rff(X, sigma, rng) + rng.normal(0.0, np.sqrt(gamma), N)
     return dict(X=X.astype(np.float32), y=y.astype(np.float32), sigma=sigma,
                 gamma=gamma, probes=probes, seed=seed + 1000)
+
+
+def matern_problem(seed=0, N=1000, d=25):
+    """Two-class cloud with +-1 labels for the Matern kernel (h passed as sigma)."""
+    rng = np.random.default_rng(seed)
+    mu = rng.standard_normal(d)
+    mu /= np.linalg.norm(mu)
+    b = np.where(rng.random(N) < 0.5, 1.0, -1.0)
+    X = b[:, None] * mu[None, :] + rng.standard_normal((N, d))
+    return dict(X=X.astype(np.float32), b=b.astype(np.float32), sigma=float(np.sqrt(d)),
+                gamma=1e-2, delta=1e-1, inner_tol=1e-2, restart=30, tol=1e-6)
 
 
 def sample_rows(N, count, seed):

@@ -1,4 +1,4 @@
-"""GPU flexible CG (the paper's second outer iteration, Sec. 4.3) against the
+"""GPU flexible CG (the paper's second outer iteration, Sec. 4.2) against the
 FP64 oracle: the true residual recomputed in FP64 meets the tolerance, the
 library's own true residual agrees with it, and the step counts are those of
 the oracle's flexible CG with the same preconditioner settings."""
