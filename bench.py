@@ -62,6 +62,8 @@ def parse_args(argv=None):
                     help="points of the log-marginal-likelihood gradient (0 skips it)")
     ap.add_argument("--no-matern", dest="matern", action="store_false",
                     help="skip the Matern-kernel product and solves")
+    ap.add_argument("--no-highd", dest="highd", action="store_false",
+                    help="skip the high-dimensional product comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -322,6 +324,8 @@ def run_libkrr(args):
     matern = None
     if args.matern:
         matern = matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
+    tuned = autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream, kern_ms, m16_ms)
+    highd = highd_form(K, torch, rank, dev) if args.highd else None
 
     # ---- FP64 oracle on the host cores (rank 0, one GPU only)
     cpu = None
@@ -364,6 +368,8 @@ def run_libkrr(args):
             "fgmres": solve,
             "mll_grad": grad,
             "matern": matern,
+            "autotune": tuned,
+            "highd": highd,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -490,7 +496,7 @@ def mixture_forms(K, torch, inputs, args, rank, dev, stream):
     return out
 
 
-def batching_form(K, torch, inputs, args, rank, dev, stream):
+def batching_form(K, torch, inputs, args, rank, dev, stream, handle=None, plain=True):
     """A subset of the batching workload (d = 8, N(0, I) points, sigma 1,
     gamma log-uniform in [1e-4, 1e-1], 16 N(0,1) right-hand sides each, N
     log-uniform in [1024, batch-nmax]): all problems in one batched call vs
@@ -506,10 +512,18 @@ def batching_form(K, torch, inputs, args, rank, dev, stream):
                           B=torch.from_numpy(np.ascontiguousarray(pr["B"].T)).to(dev),
                           gamma=pr["gamma"],
                           Xsol=torch.empty((16, N), dtype=torch.float64, device=dev)))
+    first_ms = None
+    if handle is not None:  # the first call tunes every product shape of the batch
+        _, first_ms = _timed(torch, stream, lambda: K.krr_fgmres_solve_batched(
+            probs, d=8, sigma=bp["sigma"], m_rhs=16, handle=handle))
     infos, ms = _timed(torch, stream, lambda: K.krr_fgmres_solve_batched(probs, d=8, sigma=bp["sigma"],
-                                                                         m_rhs=16))
+                                                                         m_rhs=16, handle=handle))
     out = {"N": [int(p["X"].shape[0]) for p in probs], "rhs_per_problem": 16,
            "batched": dict(total_ms=ms, per_rhs_ms=ms / (16 * len(probs)), **_report(K, infos))}
+    if first_ms is not None:
+        out["batched"]["first_call_ms"] = first_ms
+    if not plain:
+        return out
     tot, n, pinfos = 0.0, 0, []
     for pr in probs:
         for c in range(2):
@@ -569,7 +583,7 @@ def matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
                             "peak_source": f"min(FP32 lanes {fp32_lanes / 1e12:.2f}e12 / {fp32_ops}, "
                                            f"1 / (1/EX2 {ex2_rate / 1e12:.2f}e12 + 1/rsqrt "
                                            f"{rsqrt_rate / 1e12:.2f}e12))",
-                            "kernel": "mvp_dirm_kernel<3, 1, Matern>"}}
+                            "kernel": "mvp_f32_kernel<3, 8, Matern> (direct form, 8 targets per thread)"}}
     solves = {}
     sp = inputs.small_problem(seed=rank)
     sp = dict(sp, sigma=0.1)  # h = 0.1 on the 2000-point problem
@@ -582,6 +596,80 @@ def matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
             "cg": cg_once(K, torch, mp, dev, stream, handle=h)}
     h.close()
     return {"product": product, "solves": solves}
+
+
+def autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream, kern_ms, m16_ms):
+    """Products and the batching subset on a handle with KRR_OPT_AUTOTUNE: the
+    first call of each shape tunes its source splits (timed separately), the
+    next ones run the tuned plan."""
+    h = K.Handle()
+    K.krr_set_option(K.KRR_OPT_AUTOTUNE, 1, handle=h)
+    y = torch.empty_like(q)
+    Y16 = torch.empty_like(Q16)
+    (_, tune1_ms) = _timed(torch, stream, lambda: K.krr_kernel_mvp(X, q, sigma, gamma, out=y, handle=h))
+    (_, tune16_ms) = _timed(torch, stream, lambda: K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h))
+    K.krr_profile_enable(True, handle=h)
+    reps = 3
+    for _ in range(reps):
+        K.krr_kernel_mvp(X, q, sigma, gamma, out=y, handle=h)
+    prof = K.krr_profile_read(handle=h)
+    K.krr_profile_enable(False, handle=h)
+    t1 = prof["product_ms"] / max(prof["product_launches"], 1)
+    (_, t16) = _timed(torch, stream, lambda: K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h))
+    out = {"product_m1": {"model_kernel_ms": kern_ms, "tuned_kernel_ms": t1, "first_call_ms": tune1_ms},
+           "product_m16": {"model_ms": m16_ms, "tuned_ms": t16, "first_call_ms": tune16_ms}}
+    if args.batch_probs > 0:
+        out["batching_d8"] = batching_form(K, torch, inputs, args, rank, dev, stream, handle=h,
+                                           plain=False)
+    h.close()
+    return out
+
+
+def tensor_peak_tflops():
+    """Measured dense bf16 tensor peak of this machine (burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def highd_form(K, torch, rank, dev):
+    """High-dimensional single-column products (N = 65536 uniform in [0,1]^d):
+    the cross term on the tensor cores (kernel width 0.3 sqrt(d): compact
+    super-blocks) against the direct form on the CUDA cores (the same points
+    at width 0.02 sqrt(d): no compact block).  The tensor path's contraction
+    is 3 (d + 1) split-f16 products per pair, 2 flops each."""
+    import numpy as np
+    peak, src = tensor_peak_tflops()
+    out = {}
+    for d in (16, 32, 64):
+        rng = np.random.default_rng(1000 + 17 * rank + d)
+        n = 65536
+        X = torch.from_numpy(rng.random((n, d)).astype(np.float32)).to(dev)
+        q = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+        y = torch.empty_like(q)
+        row = {}
+        for name, width in (("tensor", 0.3), ("direct", 0.02)):
+            sig = width * float(np.sqrt(d))
+            h = K.Handle()
+            K.krr_kernel_mvp(X, q, sig, 1e-3, out=y, handle=h)
+            torch.cuda.synchronize(dev)
+            K.krr_profile_enable(True, handle=h)
+            for _ in range(3):
+                K.krr_kernel_mvp(X, q, sig, 1e-3, out=y, handle=h)
+            prof = K.krr_profile_read(handle=h)
+            h.close()
+            ms = prof["product_ms"] / max(prof["product_launches"], 1)
+            row[name] = {"kernel_ms": ms, "Gpairs_per_s": float(n) * n / ms / 1e6,
+                         "tensor_path": prof["tensor_exponent_launches"] == prof["product_launches"]}
+        tflops = float(n) * n * 2 * 3 * (d + 1) / (row["tensor"]["kernel_ms"] / 1e3) / 1e12
+        row["tensor"]["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": tflops / peak, "peak_source": f"bf16 dense, {src}",
+                                     "kernel": f"mvp_tch_kernel<{((d + 15) // 16) * 16}> (mma.sync m16n8k16)"}
+        row["speedup"] = row["direct"]["kernel_ms"] / row["tensor"]["kernel_ms"]
+        out[f"d{d}"] = row
+    return out
 
 
 def main(argv=None):

@@ -138,7 +138,16 @@ typedef enum {
      * KRR_KERNEL_MATERN32 the `sigma` argument of every call is the Matern
      * length scale h.  krr_mll_grad supports the Gaussian only and returns
      * KRR_ERR_UNIMPLEMENTED otherwise. */
-    KRR_OPT_KERNEL = 2
+    KRR_OPT_KERNEL = 2,
+    /* value != 0: autotune the source split of every product (the range of
+     * source tiles one CTA sums, i.e. how finely a product is spread over
+     * the SMs).  The first product of each shape (sizes, columns, precision,
+     * kernel family) on this handle, outside a CUDA-graph capture, times
+     * the real launch at 1/4 to 4 times the modelled split count on scratch
+     * weights (a few launches; waits for them) and keeps the fastest for
+     * later products of that shape.  Results stay within the same error
+     * bars; the summation grouping, hence the last bits, may differ. */
+    KRR_OPT_AUTOTUNE = 3
 } krr_option;
 
 /* Kernel functions (KRR_OPT_KERNEL). */

@@ -363,6 +363,7 @@ def krr_measure_rsqrt_rate(handle=None, stream=None):
 
 KRR_OPT_TCGEN05 = 1
 KRR_OPT_KERNEL = 2
+KRR_OPT_AUTOTUNE = 3
 KRR_KERNEL_GAUSSIAN, KRR_KERNEL_MATERN32 = 0, 1
 
 
@@ -370,7 +371,8 @@ def krr_set_option(option, value, handle=None):
     """Set a handle option (KRR_OPT_TCGEN05: multi-column tensor-core
     products on the tcgen05 / tensor-memory kernel; KRR_OPT_KERNEL: the
     kernel function, KRR_KERNEL_GAUSSIAN or KRR_KERNEL_MATERN32, whose length
-    scale h is then passed as sigma)."""
+    scale h is then passed as sigma; KRR_OPT_AUTOTUNE: time the products'
+    source splits on first use of each shape and keep the fastest)."""
     h = handle or default_handle()
     h.check(lib().krr_set_option(h.h, int(option), int(value)))
 

@@ -103,6 +103,15 @@ struct Ctx {
   bool use_tcgen05 = false;
   // kernel function of every product and solve (KRR_KERNEL_*, krr_set_option)
   int kernel_family = 0;
+  // autotuning of the products' source splits (KRR_OPT_AUTOTUNE): the first
+  // reserve or launch of a product shape outside a graph capture times the
+  // real launch at several scales of the modelled split count and keeps the
+  // fastest; split_scale is the scale in force for the product being planned
+  bool autotune = false;
+  bool tuning = false;
+  int prod_depth = 0;
+  double split_scale = 1.0;
+  std::unordered_map<std::string, double> tune_cache;
   // profiling of the fast product kernel (krr_profile_enable / _read)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
@@ -110,6 +119,37 @@ struct Ctx {
   double prof_pairs = 0.0;
   int prof_tensor_exp = 0;           // timed launches on the tensor-core exponent path
 };
+
+// Product shape key of the autotuner: kind ("mvp" or "acc"), sizes, columns,
+// precision, kernel family and the planning context.
+std::string tune_key(const Ctx& c, const char* kind, const PointsDev& Tp, const PointsDev& Sp, int m,
+                     int prec);
+// The tuned split scale of a shape (1 when untuned).
+inline double tuned_scale(const Ctx& c, const std::string& key) {
+  const auto it = c.tune_cache.find(key);
+  return it == c.tune_cache.end() ? 1.0 : it->second;
+}
+// Whether a product entry point may run the tuner now: enabled, not already
+// tuning, not nested in another product entry point, and the stream is not
+// being captured into a graph.
+bool can_tune(const Ctx& c, cudaStream_t st);
+// Sets c.split_scale for one product entry point and counts the nesting.
+struct TuneScope {
+  Ctx& c;
+  double old;
+  TuneScope(Ctx& cc, double s) : c(cc), old(cc.split_scale) {
+    c.split_scale = s;
+    ++c.prod_depth;
+  }
+  ~TuneScope() {
+    c.split_scale = old;
+    --c.prod_depth;
+  }
+};
+// Split scales the tuner tries, the modelled one first.
+constexpr double TUNE_SCALES[] = {1.0, 0.5, 2.0, 0.25, 4.0};
+// Largest partial-sum buffer a tuning candidate may ask for.
+constexpr double TUNE_MAX_BYTES = 1073741824.0;
 
 // Sub-context k of c (created on first use; freed with the handle).
 cudaError_t sub_context(Ctx& c, size_t k, Ctx** out);

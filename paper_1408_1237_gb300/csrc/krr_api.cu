@@ -43,6 +43,22 @@ void Workspace::release_all() {
   slots.clear();
 }
 
+std::string tune_key(const Ctx& c, const char* kind, const PointsDev& Tp, const PointsDev& Sp, int m,
+                     int prec) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|%lld|%lld|%d|%d|%d|%d|%d|%d|%lld|%lld", kind, (long long)Tp.N,
+           (long long)Sp.N, Tp.d, Tp.kfam, m, prec, c.plan_slots, c.use_tcgen05 ? 1 : 0,
+           (long long)Tp.h_nexp, (long long)Tp.h_sb_nexp);
+  return buf;
+}
+
+bool can_tune(const Ctx& c, cudaStream_t st) {
+  if (!c.autotune || c.tuning || c.prod_depth > 0) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs == cudaStreamCaptureStatusNone;
+}
+
 cudaError_t sub_context(Ctx& c, size_t k, Ctx** out) {
   while (c.subs.size() <= k) {
     Ctx* s = new (std::nothrow) Ctx();
@@ -248,6 +264,9 @@ krr_status krr_set_option(krr_handle h, int option, int value) {
   switch (option) {
     case KRR_OPT_TCGEN05:
       h->ctx.use_tcgen05 = value != 0;
+      return KRR_OK;
+    case KRR_OPT_AUTOTUNE:
+      h->ctx.autotune = value != 0;
       return KRR_OK;
     case KRR_OPT_KERNEL:
       if (value != KRR_KERNEL_GAUSSIAN && value != KRR_KERNEL_MATERN32)

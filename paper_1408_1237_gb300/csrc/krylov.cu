@@ -1572,6 +1572,7 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
       bc->plan_slots = slots;
       bc->use_tcgen05 = c.use_tcgen05;
       bc->kernel_family = c.kernel_family;
+      bc->autotune = c.autotune;
       if (col0 == 0 && (e = prepare_points(*bc, pr.X, pr.N, d, sigma, "bat.pts", pts[k], st)))
         return cuda_error(c, e, fn);
       auto so = std::make_unique<Solver>(*bc);

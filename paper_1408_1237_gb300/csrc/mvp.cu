@@ -132,13 +132,26 @@ __device__ __forceinline__ void compute_expanded(const float* __restrict__ cb,
   }
 }
 
-template <int D, int T>
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e) = 1 / ln 2
+
+// Matern 3/2 value from the squared raw distance: a = s r, (1 + a) 2^(-a log2 e).
+// r = r2 / sqrt(r2) through the reciprocal square root (a 2-ulp routine); the
+// clamp keeps r2 = 0 (a point against itself) at a = 0 instead of 0 * inf.
+__device__ __forceinline__ float matern32_value(float r2, float s) {
+  const float a = s * (r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+  const float e = ex2(a * -kLog2e);
+  return fmaf(a, e, e);
+}
+
+// KF: pair function, 0 = Gaussian 2^(-s^2 r^2), 1 = Matern 3/2 (s = sqrt(3)/h).
+template <int D, int T, int KF>
 __device__ __forceinline__ void compute_direct(const float* __restrict__ cb,
                                                const float2 (&tx)[T][D], float2 (&acc)[T],
-                                               float s2) {
+                                               float s2, float s) {
   const float* cX = cb;  // holds -x_j (raw)
   const float* cQ = cb + (D + 1) * TS;
   const float2 ns2 = make_float2(-s2, -s2);
+  const float2 sv = make_float2(s, s), nl2e = make_float2(-kLog2e, -kLog2e);
 #pragma unroll 2
   for (int j = 0; j < TS; j += 4) {
     float4 xk[D];
@@ -157,20 +170,33 @@ __device__ __forceinline__ void compute_direct(const float* __restrict__ cb,
         r0 = ffma2(d0, d0, r0);
         r1 = ffma2(d1, d1, r1);
       }
-      r0 = fmul2(r0, ns2);
-      r1 = fmul2(r1, ns2);
       float2 e0, e1;
-      e0.x = ex2(r0.x);
-      e0.y = ex2(r0.y);
-      e1.x = ex2(r1.x);
-      e1.y = ex2(r1.y);
+      if constexpr (KF == 0) {
+        r0 = fmul2(r0, ns2);
+        r1 = fmul2(r1, ns2);
+        e0.x = ex2(r0.x);
+        e0.y = ex2(r0.y);
+        e1.x = ex2(r1.x);
+        e1.y = ex2(r1.y);
+      } else {
+        // a = s r (r = r^2 rsqrt(r^2), clamped at r^2 = 0), then (1 + a) 2^(-a log2 e)
+        const float2 a0 = fmul2(sv, fmul2(r0, make_float2(rsqrtf(fmaxf(r0.x, 1e-30f)),
+                                                          rsqrtf(fmaxf(r0.y, 1e-30f)))));
+        const float2 a1 = fmul2(sv, fmul2(r1, make_float2(rsqrtf(fmaxf(r1.x, 1e-30f)),
+                                                          rsqrtf(fmaxf(r1.y, 1e-30f)))));
+        const float2 t0 = fmul2(a0, nl2e), t1 = fmul2(a1, nl2e);
+        e0 = make_float2(ex2(t0.x), ex2(t0.y));
+        e1 = make_float2(ex2(t1.x), ex2(t1.y));
+        e0 = ffma2(a0, e0, e0);
+        e1 = ffma2(a1, e1, e1);
+      }
       acc[u] = ffma2(make_float2(qq.x, qq.y), e0, acc[u]);
       acc[u] = ffma2(make_float2(qq.z, qq.w), e1, acc[u]);
     }
   }
 }
 
-template <int D, int T>
+template <int D, int T, int KF>
 __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   constexpr int RS = raw_stages<D>();
   constexpr uint32_t kRawFloats = (D + 1) * TS;
@@ -270,7 +296,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
       if (expanded)
         compute_expanded<D, T>(wbuf, tx, acc);
       else
-        compute_direct<D, T>(wbuf, tx, acc, s2);
+        compute_direct<D, T, KF>(wbuf, tx, acc, s2, p.s);
 #pragma unroll
       for (int u = 0; u < T; ++u) {
         kahan_add(sum[u], comp[u], acc[u].x + acc[u].y);
@@ -296,17 +322,6 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
       if (i < p.Nt_pad) part[i] = (double)sum[u] - (double)comp[u];
     }
   }
-}
-
-constexpr float kLog2e = 1.4426950408889634f;  // log2(e) = 1 / ln 2
-
-// Matern 3/2 value from the squared raw distance: a = s r, (1 + a) 2^(-a log2 e).
-// r = r2 / sqrt(r2) through the reciprocal square root (a 2-ulp routine); the
-// clamp keeps r2 = 0 (a point against itself) at a = 0 instead of 0 * inf.
-__device__ __forceinline__ float matern32_value(float r2, float s) {
-  const float a = s * (r2 * rsqrtf(fmaxf(r2, 1e-30f)));
-  const float e = ex2(a * -kLog2e);
-  return fmaf(a, e, e);
 }
 
 // Direct-form warp blocks for several columns at once: one exponential per
@@ -538,25 +553,25 @@ constexpr size_t smem_bytes() {
 }
 
 // Dynamic shared-memory opt-in, once per kernel instance and device.
-template <int D, int T>
+template <int D, int T, int KF>
 cudaError_t set_attr() {
   static bool done[128] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 128 && done[dev]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mvp_f32_kernel<D, T>,
+  cudaError_t e = cudaFuncSetAttribute(mvp_f32_kernel<D, T, KF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes<D>());
   if (!e && dev < 128) done[dev] = true;
   return e;
 }
 
-template <int D, int T>
+template <int D, int T, int KF>
 cudaError_t launch_typed(const MvpParams& p, int splits, cudaStream_t st) {
-  cudaError_t e = set_attr<D, T>();
+  cudaError_t e = set_attr<D, T, KF>();
   if (e) return e;
   dim3 grid((unsigned)std::max<int64_t>(1, (p.nblk - p.slot0 + NW - 1) / NW), (unsigned)splits);
-  mvp_f32_kernel<D, T><<<grid, NT, smem_bytes<D>(), st>>>(p); count_launch();
+  mvp_f32_kernel<D, T, KF><<<grid, NT, smem_bytes<D>(), st>>>(p); count_launch();
   return cudaGetLastError();
 }
 
@@ -599,31 +614,53 @@ struct Plan {
   int tiles_per_split = 1;
 };
 
-Plan make_plan(int64_t nblk, int ntiles, int num_sms, int plan_slots = 0) {
+// scale: the autotuner's factor on the modelled split count (1: the model).
+Plan make_plan(int64_t nblk, int ntiles, int num_sms, int plan_slots, double scale) {
   const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   const int64_t ctas = (nblk + NW - 1) / NW;
   Plan pl;
-  const int splits = choose_splits(ctas, ntiles, slots);
+  int splits = choose_splits(ctas, ntiles, slots);
+  if (scale != 1.0)
+    splits = std::max(1, std::min({(int)std::lround(splits * scale), ntiles, 256}));
   pl.tiles_per_split = (ntiles + splits - 1) / splits;
   pl.splits = (ntiles + pl.tiles_per_split - 1) / pl.tiles_per_split;
   return pl;
 }
 
-template <int D>
+template <int D, int KF = 0>
 cudaError_t attrs_T(int T) {
   constexpr int TL = large_T<D>();
-  if (T == TL) return set_attr<D, TL>();
-  if (T == 1) return set_attr<D, 1>();
+  if (T == TL) return set_attr<D, TL, KF>();
+  if (T == 1) return set_attr<D, 1, KF>();
   return cudaErrorNotSupported;
 }
 
-template <int D>
+template <int D, int KF = 0>
 cudaError_t dispatch_T(MvpParams p, int T, const Plan& pl, cudaStream_t st) {
   constexpr int TL = large_T<D>();
   p.tiles_per_split = pl.tiles_per_split;
-  if (T == TL) return launch_typed<D, TL>(p, pl.splits, st);
-  if (T == 1) return launch_typed<D, 1>(p, pl.splits, st);
+  if (T == TL) return launch_typed<D, TL, KF>(p, pl.splits, st);
+  if (T == 1) return launch_typed<D, 1, KF>(p, pl.splits, st);
   return cudaErrorNotSupported;
+}
+
+// The packed CUDA-core kernel for d <= 8 and kernel family kf (KRR_KERNEL_*):
+// launch (launch = true) or only its shared-memory attribute.
+template <int KF>
+cudaError_t f32_any_k(const MvpParams& p, int d, int T, const Plan& pl, cudaStream_t st, bool launch) {
+  switch (d) {
+#define KRR_F32_CASE(DV) \
+    case DV: return launch ? dispatch_T<DV, KF>(p, T, pl, st) : attrs_T<DV, KF>(T);
+    KRR_F32_CASE(1) KRR_F32_CASE(2) KRR_F32_CASE(3) KRR_F32_CASE(4)
+    KRR_F32_CASE(5) KRR_F32_CASE(6) KRR_F32_CASE(7) KRR_F32_CASE(8)
+#undef KRR_F32_CASE
+    default: return cudaErrorNotSupported;
+  }
+}
+cudaError_t f32_any(const MvpParams& p, int d, int kf, int T, const Plan& pl, cudaStream_t st, bool launch) {
+  if (kf == KRR_KERNEL_MATERN32) return f32_any_k<1>(p, d, T, pl, st, launch);
+  if (kf != KRR_KERNEL_GAUSSIAN) return cudaErrorNotSupported;
+  return f32_any_k<0>(p, d, T, pl, st, launch);
 }
 
 template <int D, int MC, int KF>
@@ -700,17 +737,25 @@ Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
   // one CTA per super-block (mma.sync kernel), or two of 128 targets with at
   // most two per SM (tcgen05 kernel: tensor memory)
   return make_plan((c.use_tcgen05 ? 2 : 1) * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
-                   c.plan_slots);
+                   c.plan_slots, c.split_scale);
 }
+// Multi-column products keep the tensor cores to d <= 8 (Gaussian); elsewhere
+// every super-block takes the direct form, whatever its compactness flag.
+bool multi_direct_only(const PointsDev& Tp) { return Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN; }
+int64_t multi_nexp(const PointsDev& Tp) { return multi_direct_only(Tp) ? 0 : Tp.h_sb_nexp; }
 Plan multi_plan_dir(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
-  return make_plan((Tp.nsb - Tp.h_sb_nexp) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+  return make_plan((Tp.nsb - multi_nexp(Tp)) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots,
+                   c.split_scale);
 }
 
 // The single-column float32 product takes the tensor-core exponent path when
 // there are enough target super-blocks to fill the GPU (one CTA of 4 warps
 // each, several per SM) and at least half of them are compact; otherwise the
 // CUDA-core kernel with its finer per-warp blocks.
+// Above 8 dimensions the direct form costs 2d + 2 FP32 operations per pair,
+// so any compact super-block is worth the tensor-core kernel (mvp_tch_kernel).
 bool use_tcx(const Ctx& c, const PointsDev& Tp) {
+  if (Tp.d > 8) return c.allow_tcx && Tp.kfam == KRR_KERNEL_GAUSSIAN && Tp.h_sb_nexp > 0;
   return c.allow_tcx && Tp.nsb >= c.num_sms && 2 * Tp.h_sb_nexp >= Tp.nsb;
 }
 
@@ -720,13 +765,15 @@ bool use_tcx(const Ctx& c, const PointsDev& Tp) {
 bool tcx_dir_f32(const PointsDev& Tp) { return Tp.T * 32 == SB; }
 Plan tcx_dir_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
   if (tcx_dir_f32(Tp))
-    return make_plan(Tp.nsb - Tp.h_sb_nexp, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
-  return multi_plan_dir(c, Tp, Sp);
+    return make_plan(Tp.nsb - Tp.h_sb_nexp, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots,
+                     c.split_scale);
+  return make_plan((Tp.nsb - Tp.h_sb_nexp) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots,
+                   c.split_scale);
 }
 
 Plan tcx_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
   return make_plan(Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
-                   c.plan_slots > 0 ? c.plan_slots : 4 * c.num_sms);
+                   c.plan_slots > 0 ? c.plan_slots : 4 * c.num_sms, c.split_scale);
 }
 
 // Buffers every product path uses: the factored scale and the dot scratch.
@@ -739,7 +786,92 @@ cudaError_t common_reserve(Ctx& c, const PointsDev& Tp, cudaStream_t st) {
   const bool fresh = c.ws.slots.find("mvp.dotcnt") == c.ws.slots.end();
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &v))) return e;
   if (fresh && (e = cudaMemsetAsync(v, 0, sizeof(unsigned) * MAX_COLS, st))) return e;
+  // a device zero: the expanded-form block count of products that take the
+  // direct form everywhere
+  const bool fresh0 = c.ws.slots.find("mvp.zero") == c.ws.slots.end();
+  if ((e = c.ws.get("mvp.zero", sizeof(int), &v))) return e;
+  if (fresh0 && (e = cudaMemsetAsync(v, 0, sizeof(int), st))) return e;
   return cudaSuccess;
+}
+
+// Largest source-split count among the kernels of a product route at the
+// split scale in force (sizes the partial-sum buffers of a tuning candidate).
+int route_splits(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, krr_precision prec) {
+  if (m == 1 && prec == KRR_FP32) {
+    if (use_tcx(c, Tp)) return std::max(tcx_plan(c, Tp, Sp).splits, tcx_dir_plan(c, Tp, Sp).splits);
+    if (Tp.d <= 8) return make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots, c.split_scale).splits;
+  }
+  int s = multi_plan_dir(c, Tp, Sp).splits;
+  if (!multi_direct_only(Tp)) s = std::max(s, multi_plan_tc(c, Tp, Sp).splits);
+  return s;
+}
+
+// The autotuner of the fast products: times the real launch of this route
+// (scratch zero weights; the instruction stream does not depend on them) at
+// each split scale of TUNE_SCALES, best of two after a warm-up, and keeps
+// the fastest in c.tune_cache (the modelled split unless another is 2%
+// faster).  Candidates whose partial sums would exceed TUNE_MAX_BYTES are
+// skipped.
+cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, krr_precision prec,
+                         cudaStream_t st, const std::string& key) {
+  struct Restore {
+    Ctx& c;
+    bool prof;
+    ~Restore() {
+      c.tuning = false;
+      c.profiling = prof;
+    }
+  } restore{c, c.profiling};
+  c.tuning = true;
+  c.profiling = false;
+  void *qv, *yv;
+  cudaError_t e;
+  if ((e = c.ws.get("tune.q", sizeof(float) * (size_t)m * Sp.Npad, &qv))) return e;
+  if ((e = c.ws.get("tune.y", sizeof(float) * (size_t)m * Tp.Npad, &yv))) return e;
+  if ((e = cudaMemsetAsync(qv, 0, sizeof(float) * (size_t)m * Sp.Npad, st))) return e;
+  cudaEvent_t ev[2];
+  if ((e = cudaEventCreate(&ev[0]))) return e;
+  if ((e = cudaEventCreate(&ev[1]))) {
+    cudaEventDestroy(ev[0]);
+    return e;
+  }
+  double best = 1.0;
+  float best_ms = -1.f;
+  for (double s : TUNE_SCALES) {
+    c.tune_cache[key] = s;
+    {
+      TuneScope ts(c, s);
+      if (s > 1.0 && 8.0 * route_splits(c, Tp, Sp, m, prec) * m * (double)Tp.Npad > TUNE_MAX_BYTES)
+        continue;
+    }
+    MvpOut o;
+    o.out_f = (float*)yv;
+    auto run = [&]() {
+      return (m == 1 && prec == KRR_FP32)
+                 ? mvp_launch(c, Tp, Sp, (const float*)qv, nullptr, 0.f, prec, o, st)
+                 : mvp_multi_launch(c, Tp, Sp, (const float*)qv, m, nullptr, 0.f, prec, o, st);
+    };
+    if ((e = run())) break;  // warm-up: workspace and attributes of this split
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && !e; ++rep) {
+      cudaEventRecord(ev[0], st);
+      e = run();
+      cudaEventRecord(ev[1], st);
+      if (!e) e = cudaEventSynchronize(ev[1]);
+      float t = 0.f;
+      if (!e) cudaEventElapsedTime(&t, ev[0], ev[1]);
+      ms = std::min(ms, t);
+    }
+    if (e) break;
+    if (best_ms < 0.f || ms < 0.98f * best_ms) {
+      best_ms = ms;
+      best = s;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  c.tune_cache[key] = e ? 1.0 : best;
+  return e;
 }
 
 }  // namespace
@@ -753,11 +885,32 @@ int mvp_targets_per_thread(int d, int64_t N) {
 
 cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
-  // direct form only (above 8 dimensions, or a kernel other than the
-  // Gaussian): the multi-column kernel with one column
-  if (Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN) return mvp_multi_reserve(c, Tp, Sp, 1, KRR_FP32, st);
+  const std::string key = tune_key(c, "mvp", Tp, Sp, 1, KRR_FP32);
+  if (can_tune(c, st) && !c.tune_cache.count(key)) {
+    cudaError_t te = autotune_mvp(c, Tp, Sp, 1, KRR_FP32, st, key);
+    if (te) return te;
+  }
+  TuneScope scope(c, tuned_scale(c, key));
+  // above 8 dimensions: the high-dimensional tensor-core kernel on compact
+  // super-blocks with the multi-column direct-form kernel on the rest, or
+  // that direct-form kernel alone
+  if (Tp.d > 8) {
+    if (!use_tcx(c, Tp)) return mvp_multi_reserve(c, Tp, Sp, 1, KRR_FP32, st);
+    cudaError_t e = common_reserve(c, Tp, st);
+    if (e) return e;
+    const Plan pt = tcx_plan(c, Tp, Sp), pd = tcx_dir_plan(c, Tp, Sp);
+    void* v;
+    if ((e = c.ws.get("mvp.partt", sizeof(double) * pt.splits * (size_t)Tp.Npad, &v))) return e;
+    if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)Tp.Npad, &v))) return e;
+    if ((e = mvp_tcx_partials(c, Tp, Sp, nullptr, pt.splits, pt.tiles_per_split, nullptr, nullptr,
+                              nullptr, st, true)))
+      return e;
+    MvpParams p{};
+    p.nblk = Tp.nsb;
+    return dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, 1, SB / 32, Tp.h_sb_nexp, pd, st, false);
+  }
   if (Tp.d < 1) return cudaErrorNotSupported;
-  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots);
+  const Plan pl = make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots, c.split_scale);
   void* v;
   cudaError_t e;
   const unsigned fin_blocks = (unsigned)((Tp.Npad + 255) / 256);
@@ -778,16 +931,8 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
     p.nblk = Tp.nsb;
     if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, 1, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
   }
-  switch (Tp.d) {
-    case 1: return attrs_T<1>(Tp.T);
-    case 2: return attrs_T<2>(Tp.T);
-    case 3: return attrs_T<3>(Tp.T);
-    case 4: return attrs_T<4>(Tp.T);
-    case 5: return attrs_T<5>(Tp.T);
-    case 6: return attrs_T<6>(Tp.T);
-    case 7: return attrs_T<7>(Tp.T);
-    default: return attrs_T<8>(Tp.T);
-  }
+  MvpParams p0{};
+  return f32_any(p0, Tp.d, Tp.kfam, Tp.T, pl, st, false);
 }
 
 namespace {
@@ -893,9 +1038,15 @@ cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const flo
 cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const float* q,
                        const float* qdiag, float shift, krr_precision prec, const MvpOut& o,
                        cudaStream_t st) {
-  if (prec != KRR_FP32 || Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN)
-    return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
+  if (prec != KRR_FP32) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
   if (Tp.N == 0) return cudaSuccess;
+  if (Tp.d > 8 && !use_tcx(c, Tp)) return mvp_multi_launch(c, Tp, Sp, q, 1, qdiag, shift, prec, o, st);
+  const std::string key = tune_key(c, "mvp", Tp, Sp, 1, KRR_FP32);
+  if (can_tune(c, st) && !c.tune_cache.count(key)) {
+    cudaError_t te = autotune_mvp(c, Tp, Sp, 1, KRR_FP32, st, key);
+    if (te) return te;
+  }
+  TuneScope scope(c, tuned_scale(c, key));
   if (use_tcx(c, Tp)) return tcx_path(c, Tp, Sp, q, qdiag, shift, o, st);
   MvpParams p{};
   p.xt = Tp.xs;
@@ -913,7 +1064,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   p.part_stride = Tp.Npad;
   p.err = c.d_err;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
-  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots);
+  const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots, c.split_scale);
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   void *part, *fac, *dpart, *dcnt;
@@ -940,17 +1091,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
       c.prof_pairs += (double)Tp.N * (double)Sp.N;
     }
   }
-  switch (Tp.d) {
-    case 1: e = dispatch_T<1>(p, Tp.T, pl, st); break;
-    case 2: e = dispatch_T<2>(p, Tp.T, pl, st); break;
-    case 3: e = dispatch_T<3>(p, Tp.T, pl, st); break;
-    case 4: e = dispatch_T<4>(p, Tp.T, pl, st); break;
-    case 5: e = dispatch_T<5>(p, Tp.T, pl, st); break;
-    case 6: e = dispatch_T<6>(p, Tp.T, pl, st); break;
-    case 7: e = dispatch_T<7>(p, Tp.T, pl, st); break;
-    case 8: e = dispatch_T<8>(p, Tp.T, pl, st); break;
-    default: return cudaErrorNotSupported;
-  }
+  e = f32_any(p, Tp.d, Tp.kfam, Tp.T, pl, st, true);
   if (e) return e;
   if (pev1) cudaEventRecord(pev1, st);
   FinParams f{};
@@ -973,7 +1114,13 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
                               krr_precision prec, cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
   if (m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
-  const bool direct_only = Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN;
+  const std::string key = tune_key(c, "mvp", Tp, Sp, m, prec);
+  if (can_tune(c, st) && !c.tune_cache.count(key)) {
+    cudaError_t te = autotune_mvp(c, Tp, Sp, m, prec, st, key);
+    if (te) return te;
+  }
+  TuneScope scope(c, tuned_scale(c, key));
+  const bool direct_only = multi_direct_only(Tp);
   cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
@@ -982,7 +1129,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)m * Tp.Npad, &v))) return e;
   MvpParams p{};
   p.nblk = Tp.nsb;
-  if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, m, SB / 32, Tp.h_sb_nexp, pd, st, false))) return e;
+  if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, m, SB / 32, multi_nexp(Tp), pd, st, false))) return e;
   if (direct_only) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
   if (c.use_tcgen05)
     return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
@@ -996,6 +1143,12 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
                              cudaStream_t st) {
   if (Tp.N == 0) return cudaSuccess;
   if (Tp.d < 1 || (Tp.d > 8 && Tp.d % 16) || Tp.d > 64 || m < 1 || m > MAX_COLS) return cudaErrorNotSupported;
+  const std::string key = tune_key(c, "mvp", Tp, Sp, m, prec);
+  if (can_tune(c, st) && !c.tune_cache.count(key)) {
+    cudaError_t te = autotune_mvp(c, Tp, Sp, m, prec, st, key);
+    if (te) return te;
+  }
+  TuneScope scope(c, tuned_scale(c, key));
   MvpParams p{};
   p.xt = Tp.xs;
   p.Nt = Tp.N;
@@ -1012,7 +1165,8 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
   const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
-  const bool direct_only = Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN;
+  const bool direct_only = multi_direct_only(Tp);
+  const int64_t nexp = multi_nexp(Tp);
   cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
   void *part, *partd, *fac, *dpart, *dcnt;
@@ -1026,7 +1180,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   cudaEvent_t pev1 = prof_begin(c, Tp, Sp, st);
   // expanded-form super-blocks: all columns on the tensor cores (mma.sync
   // kernel; the tcgen05 / tensor-memory kernel when the handle asks for it)
-  if (Tp.h_sb_nexp > 0) {
+  if (nexp > 0) {
     e = c.use_tcgen05
             ? mvp_umma_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                                 pt.tiles_per_split, (double*)part, p.fac, o.active, st)
@@ -1035,17 +1189,23 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
     if (e) return e;
   }
   // direct-form super-blocks: all columns in one CUDA-core launch
-  if (Tp.nsb > Tp.h_sb_nexp) {
+  if (Tp.nsb > nexp) {
     p.part = (double*)partd;
-    if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, Q, Sp.Npad, m, SB / 32, Tp.h_sb_nexp, pd, st, true))) return e;
+    if (direct_only) {
+      // every super-block direct: the kernel reads an expanded-form count of 0
+      void* zero;
+      if ((e = c.ws.get("mvp.zero", sizeof(int), &zero))) return e;
+      p.tn_exp = (const int*)zero;
+    }
+    if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, Q, Sp.Npad, m, SB / 32, nexp, pd, st, true))) return e;
   }
   if (pev1) cudaEventRecord(pev1, st);
   FinParams f{};
-  f.part = (const double*)part;
-  f.splits = pt.splits;
+  f.part = (const double*)(direct_only ? partd : part);
+  f.splits = direct_only ? pd.splits : pt.splits;
   f.part2 = (const double*)partd;
   f.splits2 = pd.splits;
-  f.sb_flag = Tp.sb_flag;
+  f.sb_flag = direct_only ? nullptr : Tp.sb_flag;
   f.part_stride = (int64_t)m * Tp.Npad;
   f.N = Tp.N;
   f.Npad = Tp.Npad;

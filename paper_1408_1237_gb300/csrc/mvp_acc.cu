@@ -684,7 +684,8 @@ struct AccPlan {
   int splits, tiles_per_split;
 };
 
-AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots, int ncols) {
+// scale: the autotuner's factor on the modelled split count (1: the model).
+AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots, int ncols, double scale) {
   const int ntiles = (int)(P.Npad / TS);
   // one target per thread in the multi-column kernel, ACC_TA otherwise
   const int ta = (ncols > 1 || P.d > 8) ? 1 : ACC_TA;
@@ -692,10 +693,66 @@ AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots, int ncols) {
   const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   // fill the GPU about four times over, never below one tile per split
   int splits = (int)std::min<int64_t>(ntiles, std::max<int64_t>(1, (4LL * slots + ctas - 1) / ctas));
+  if (scale != 1.0) splits = std::max(1, std::min({(int)std::lround(splits * scale), ntiles, 256}));
   AccPlan pl;
   pl.tiles_per_split = (ntiles + splits - 1) / splits;
   pl.splits = (ntiles + pl.tiles_per_split - 1) / pl.tiles_per_split;
   return pl;
+}
+
+// The autotuner of the accurate product (see autotune_mvp in mvp.cu): the
+// real launch on scratch zero weights at each split scale, fastest kept.
+cudaError_t autotune_acc(Ctx& c, const PointsDev& P, int ncols, cudaStream_t st, const std::string& key) {
+  struct Restore {
+    Ctx& c;
+    ~Restore() { c.tuning = false; }
+  } restore{c};
+  c.tuning = true;
+  void *qv, *yv;
+  cudaError_t e;
+  if ((e = c.ws.get("tune.aq", sizeof(float) * (size_t)ncols * P.Npad, &qv))) return e;
+  if ((e = c.ws.get("tune.ay", sizeof(double) * (size_t)ncols * P.Npad, &yv))) return e;
+  if ((e = cudaMemsetAsync(qv, 0, sizeof(float) * (size_t)ncols * P.Npad, st))) return e;
+  cudaEvent_t ev[2];
+  if ((e = cudaEventCreate(&ev[0]))) return e;
+  if ((e = cudaEventCreate(&ev[1]))) {
+    cudaEventDestroy(ev[0]);
+    return e;
+  }
+  AccCols cols;
+  cols.n = ncols;
+  double best = 1.0;
+  float best_ms = -1.f;
+  for (double s : TUNE_SCALES) {
+    c.tune_cache[key] = s;
+    if (s > 1.0 &&
+        8.0 * acc_plan(P, c.num_sms, c.plan_slots, ncols, s).splits * ncols * (double)P.Npad > TUNE_MAX_BYTES)
+      continue;
+    auto run = [&]() {
+      return mvp_acc_launch(c, P, (const float*)qv, (const float*)qv, 0.f, 0.0, nullptr, 1.0, (double*)yv,
+                            nullptr, st, cols);
+    };
+    if ((e = run())) break;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && !e; ++rep) {
+      cudaEventRecord(ev[0], st);
+      e = run();
+      cudaEventRecord(ev[1], st);
+      if (!e) e = cudaEventSynchronize(ev[1]);
+      float t = 0.f;
+      if (!e) cudaEventElapsedTime(&t, ev[0], ev[1]);
+      ms = std::min(ms, t);
+    }
+    if (e) break;
+    if (best_ms < 0.f || ms < 0.98f * best_ms) {
+      best_ms = ms;
+      best = s;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  c.tune_cache[key] = e ? 1.0 : best;
+  return e;
 }
 
 }  // namespace
@@ -703,7 +760,13 @@ AccPlan acc_plan(const PointsDev& P, int num_sms, int plan_slots, int ncols) {
 cudaError_t mvp_acc_reserve(Ctx& c, const PointsDev& P, cudaStream_t st, int ncols) {
   if (P.N == 0) return cudaSuccess;
   if (ncols < 1 || ncols > MAX_COLS) return cudaErrorNotSupported;
-  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols);
+  const std::string key = tune_key(c, "acc", P, P, ncols, KRR_FP32);
+  if (can_tune(c, st) && !c.tune_cache.count(key)) {
+    cudaError_t te = autotune_acc(c, P, ncols, st, key);
+    if (te) return te;
+  }
+  TuneScope scope(c, tuned_scale(c, key));
+  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols, c.split_scale);
   void* v;
   cudaError_t e;
   if ((e = c.ws.get("acc.part", sizeof(double) * ncols * pl.splits * (size_t)P.Npad, &v))) return e;
@@ -721,6 +784,12 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
                            double* dot, cudaStream_t st, const AccCols& cols) {
   if (P.N == 0) return cudaSuccess;
   const int ncols = cols.n;
+  const std::string key = tune_key(c, "acc", P, P, ncols, KRR_FP32);
+  if (can_tune(c, st) && !c.tune_cache.count(key)) {
+    cudaError_t te = autotune_acc(c, P, ncols, st, key);
+    if (te) return te;
+  }
+  TuneScope scope(c, tuned_scale(c, key));
   cudaError_t e = mvp_acc_reserve(c, P, st, ncols);
   if (e) return e;
   AccParams p{};
@@ -740,7 +809,7 @@ cudaError_t mvp_acc_launch(Ctx& c, const PointsDev& P, const float* qh, const fl
   const double sd = std::sqrt(P.s2);
   p.k.sh = (float)sd;
   p.k.sl = (float)(sd - (double)p.k.sh);
-  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols);
+  const AccPlan pl = acc_plan(P, c.num_sms, c.plan_slots, ncols, c.split_scale);
   p.tiles_per_split = pl.tiles_per_split;
   p.splits = pl.splits;
   p.active = cols.active;

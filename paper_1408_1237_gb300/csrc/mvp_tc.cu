@@ -653,6 +653,229 @@ __global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const Tc
 }
 
 // ------------------------------------------------------------------------
+// High-dimensional single-column product (d = 16, 32, 48, 64: coordinates
+// zero-padded), where the cross term -2 x^_i . x^_j is a real contraction:
+// per pair 3 (d + 1) split-f16 products on the tensor cores instead of 2d + 2
+// float32 operations on the CUDA cores.  Same factored form as
+// mvp_tcx_kernel (compact super-blocks only: |x^_i - c|^2 <= 8 in scaled
+// units bounds the cancellation error of the expanded form, whatever d):
+//   E_ij = A_i . B_j, A_i = [u_i, 1], B_j = [2 v_j, -|v_j|^2], u, v = x^ - c,
+// split three ways (A' = [Ah, Ah, Al], B' = [Bh, Bl, Bh]).
+// Differences from the low-d kernel:
+//  * the K-vectors are long (4 to 13 contraction steps), so the A fragments
+//    of a warp cover MT = 2 m-tiles (d <= 32) or 1 (d >= 48), and the CTA has
+//    SB / (16 MT) warps;
+//  * targets and sources are written to shared memory as K-vector rows one
+//    component at a time (three 16-bit stores each), without per-slot
+//    selects; the target rows are read back once into the A fragments;
+//  * one K-vector buffer (the d = 64 tile is 108 KB): a tile is transformed
+//    from its raw stage between two barriers, and the raw stages (TMA bulk
+//    copies) keep loading while the tensor cores work.
+template <int D>
+struct HighD {
+  static constexpr int W = D + 1;
+  static constexpr int KSTEPS = (3 * W + 15) / 16;
+  static constexpr int STRIDE = 8 * KSTEPS + 4;    // words per K-vector row (fragment loads conflict-free)
+  static constexpr int MT = KSTEPS <= 7 ? 2 : 1;   // m-tiles per warp
+  static constexpr int WARPS = SB / (16 * MT);
+  static constexpr int RSD = D <= 32 ? 2 : 1;      // raw source stages
+};
+
+template <int D>
+constexpr size_t tch_smem_bytes() {
+  using L = HighD<D>;
+  return sizeof(float) * (L::RSD * (D + 1) * TS + TS) + sizeof(uint32_t) * TS * L::STRIDE;
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcParams p) {
+  using L = HighD<D>;
+  using H = Half<false>;
+  constexpr int W = D + 1, MT = L::MT, RSD = L::RSD, KS = L::KSTEPS, ST = L::STRIDE;
+  constexpr int RAW = (D + 1) * TS;  // coordinates, weights
+  extern __shared__ __align__(128) float smem[];
+  float* raw = smem;                                       // RSD stages
+  float* qbuf = smem + RSD * RAW;                          // TS weights
+  uint32_t* kv = reinterpret_cast<uint32_t*>(qbuf + TS);   // TS rows x ST words
+  const int nthreads = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  __shared__ __align__(8) uint64_t bars[RSD];
+  __shared__ volatile int abort_flag;
+  __shared__ float ctr[D];
+  if (p.active && *p.active == 0) return;
+  const int64_t nexp = *p.tn_exp;
+  if ((int64_t)blockIdx.x >= nexp) return;
+  const int64_t blk = p.torder[blockIdx.x];
+  const int64_t row0 = blk * p.WB;
+  for (int k = tid; k < D; k += nthreads) ctr[k] = p.tctr[blk * D + k];
+  for (int w = tid; w < TS * ST; w += nthreads) kv[w] = 0u;  // padding slots stay zero
+  __syncthreads();
+
+  // ---- target K-vectors A' = [uh, uh, ul] over [u, 1], then the A fragments
+  for (int r = tid; r < SB; r += nthreads) {
+    const int64_t i = row0 + r;
+    const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+    uint16_t* row = reinterpret_cast<uint16_t*>(kv + r * ST);
+    float r2 = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < D; ++k) {
+      const float u = p.s * (p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS] - ctr[k]);
+      r2 = fmaf(u, u, r2);
+      const typename H::T uh = H::from(u);
+      const typename H::T ul = H::from(u - H::to(uh));
+      row[k] = *reinterpret_cast<const uint16_t*>(&uh);
+      row[W + k] = *reinterpret_cast<const uint16_t*>(&uh);
+      row[2 * W + k] = *reinterpret_cast<const uint16_t*>(&ul);
+    }
+    const typename H::T one = H::from(1.f), zero = H::from(0.f);
+    row[D] = *reinterpret_cast<const uint16_t*>(&one);
+    row[W + D] = *reinterpret_cast<const uint16_t*>(&one);
+    row[2 * W + D] = *reinterpret_cast<const uint16_t*>(&zero);
+    if (blockIdx.y == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
+  }
+  __syncthreads();
+  uint32_t afr[MT][KS][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
+    const int ra = (warp * MT + mt) * 16 + g, rb = ra + 8;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      afr[mt][ks][0] = kv[ra * ST + 8 * ks + t];
+      afr[mt][ks][1] = kv[rb * ST + 8 * ks + t];
+      afr[mt][ks][2] = kv[ra * ST + 8 * ks + t + 4];
+      afr[mt][ks][3] = kv[rb * ST + 8 * ks + t + 4];
+    }
+  }
+
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+  float2 acc[MT][2], acc2[MT][2];
+  float S[MT][2], C[MT][2];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      acc[mt][h] = acc2[mt][h] = make_float2(0.f, 0.f);
+      S[mt][h] = C[mt][h] = 0.f;
+    }
+
+  auto issue = [&](int r) {
+    const int stage = r % RSD;
+    const int64_t tile = t_begin + r;
+    float* dst = raw + stage * RAW;
+    mbar_arrive_expect_tx(&bars[stage], (uint32_t)RAW * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS, p.Q + tile * (int64_t)TS, TS * 4, &bars[stage]);
+  };
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < RSD; ++st) mbar_init(&bars[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();  // also: every warp holds its A fragments before kv is reused
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RSD, nt); ++issued) issue(issued);
+
+  for (int r = 0; r < nt; ++r) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[r % RSD], (r / RSD) & 1));
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    }
+    __syncthreads();  // the previous tile's products are done with kv
+    if (abort_flag) break;
+    // ---- source K-vectors B' = [Bh, Bl, Bh] over [2 v, -|v|^2] and weights
+    const float* rs = raw + (r % RSD) * RAW;
+    for (int j = tid; j < TS; j += nthreads) {
+      float bb = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < D; ++k) {
+        const float v = p.s * (rs[k * TS + j] - ctr[k]);
+        bb = fmaf(-v, v, bb);
+      }
+      const bool far = bb < -30000.f;  // farther than any target can see: contributes 0
+      uint16_t* row = reinterpret_cast<uint16_t*>(kv + j * ST);
+#pragma unroll 4
+      for (int k = 0; k < D; ++k) {
+        const float v = far ? 0.f : 2.f * p.s * (rs[k * TS + j] - ctr[k]);
+        const typename H::T vh = H::from(v);
+        const typename H::T vl = H::from(v - H::to(vh));
+        row[k] = *reinterpret_cast<const uint16_t*>(&vh);
+        row[W + k] = *reinterpret_cast<const uint16_t*>(&vl);
+        row[2 * W + k] = *reinterpret_cast<const uint16_t*>(&vh);
+      }
+      const float b = far ? -30000.f : bb;
+      const typename H::T bh = H::from(b);
+      const typename H::T bl = H::from(b - H::to(bh));
+      row[D] = *reinterpret_cast<const uint16_t*>(&bh);
+      row[W + D] = *reinterpret_cast<const uint16_t*>(&bl);
+      row[2 * W + D] = *reinterpret_cast<const uint16_t*>(&bh);
+      qbuf[j] = rs[D * TS + j];
+    }
+    __syncthreads();  // kv ready; the raw stage may be refilled
+    if (tid == 0 && r + RSD < nt) {
+      fence_proxy_async_smem();
+      issue(r + RSD);
+      ++issued;
+    }
+#pragma unroll 1
+    for (int kk = 0; kk < TS / 16; ++kk) {
+      const int j0 = kk * 16 + g, j1 = j0 + 8;
+      float e0[MT][4], e1[MT][4];
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const uint32_t b00 = kv[j0 * ST + 8 * ks + t], b01 = kv[j0 * ST + 8 * ks + t + 4];
+        const uint32_t b10 = kv[j1 * ST + 8 * ks + t], b11 = kv[j1 * ST + 8 * ks + t + 4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          if (ks == 0) {
+            mma16816_z(e0[mt], afr[mt][0], b00, b01);
+            mma16816_z(e1[mt], afr[mt][0], b10, b11);
+          } else {
+            mma16816<false>(e0[mt], afr[mt][ks], b00, b01);
+            mma16816<false>(e1[mt], afr[mt][ks], b10, b11);
+          }
+        }
+      }
+      const float2 q0 = *reinterpret_cast<const float2*>(qbuf + kk * 16 + 2 * t);
+      const float2 q1 = *reinterpret_cast<const float2*>(qbuf + kk * 16 + 8 + 2 * t);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        acc[mt][0] = ffma2(q0, make_float2(ex2(e0[mt][0]), ex2(e0[mt][1])), acc[mt][0]);
+        acc2[mt][0] = ffma2(q1, make_float2(ex2(e1[mt][0]), ex2(e1[mt][1])), acc2[mt][0]);
+        acc[mt][1] = ffma2(q0, make_float2(ex2(e0[mt][2]), ex2(e0[mt][3])), acc[mt][1]);
+        acc2[mt][1] = ffma2(q1, make_float2(ex2(e1[mt][2]), ex2(e1[mt][3])), acc2[mt][1]);
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        kahan_add(S[mt][h], C[mt][h], (acc[mt][h].x + acc[mt][h].y) + (acc2[mt][h].x + acc2[mt][h].y));
+        acc[mt][h] = acc2[mt][h] = make_float2(0.f, 0.f);
+      }
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int r = 0; r < issued; ++r) mbar_wait_bounded(&bars[r % RSD], (r / RSD) & 1);
+    __syncthreads();
+    return;
+  }
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double v = (double)S[mt][h] - (double)C[mt][h];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      const int64_t i = row0 + (warp * MT + mt) * 16 + g + 8 * h;
+      if (t == 0 && i < p.Nt_pad) p.part[(int64_t)blockIdx.y * p.Nt_pad + i] = v;
+    }
+}
+
+// ------------------------------------------------------------------------
 // Multi-column product on the 5th-generation tensor cores (tcgen05, TMEM
 // accumulators): the same two contractions as mvp_tc_kernel, with the
 // operands where the tcgen05 datapath wants them.
@@ -1179,6 +1402,24 @@ cudaError_t tcx_launch_typed(const TcParams& p, int splits, cudaStream_t st, boo
   return cudaGetLastError();
 }
 
+template <int D>
+cudaError_t tch_launch_typed(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(mvp_tch_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tch_smem_bytes<D>());
+    if (e) return e;
+    done[dev] = true;
+  }
+  if (dry) return cudaSuccess;
+  dim3 grid((unsigned)p.nblk, (unsigned)splits);
+  mvp_tch_kernel<D><<<grid, 32 * HighD<D>::WARPS, tch_smem_bytes<D>(), st>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int D, int MT, int NRT, bool SPLIT, bool BF>
 cudaError_t launch(const TcParams& p, int splits, int warps, cudaStream_t st, bool dry) {
   using L = ExpLayout<D>;
@@ -1298,6 +1539,10 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
     case 6: return tcx_launch_typed<6>(p, splits, st, dry);
     case 7: return tcx_launch_typed<7>(p, splits, st, dry);
     case 8: return tcx_launch_typed<8>(p, splits, st, dry);
+    case 16: return tch_launch_typed<16>(p, splits, st, dry);
+    case 32: return tch_launch_typed<32>(p, splits, st, dry);
+    case 48: return tch_launch_typed<48>(p, splits, st, dry);
+    case 64: return tch_launch_typed<64>(p, splits, st, dry);
     default: return cudaErrorNotSupported;
   }
 }

@@ -326,8 +326,12 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   cudaError_t e;
   void *xs, *perm, *ka, *kb, *va, *vb, *hist, *bbp, *bb;
   const int nbb = (int)std::min<int64_t>(blocks_for(N, BBOX_THREADS), 256);
-  // the expanded form factors the Gaussian; other kernels take the direct form
-  const int allow_expanded = (d <= 8 && P.kfam == KRR_KERNEL_GAUSSIAN) ? 1 : 0;
+  // the expanded form factors the Gaussian; other kernels take the direct
+  // form.  Warp blocks (the packed CUDA-core kernel, d <= 8) and super-blocks
+  // (the tensor-core kernels, d <= 64) are classified separately.
+  const bool gauss = P.kfam == KRR_KERNEL_GAUSSIAN;
+  const int allow_expanded = (d <= 8 && gauss) ? 1 : 0;
+  const int allow_expanded_sb = gauss ? 1 : 0;
   const int nchunks = (int)blocks_for(N, SORT_CHUNK);
   if ((e = c.ws.get(t + ".xs", sizeof(float) * P.Npad * d, &xs))) return e;
   if ((e = c.ws.get(t + ".perm", sizeof(int) * P.Npad, &perm))) return e;
@@ -387,7 +391,7 @@ cudaError_t prepare_points(Ctx& c, const float* X, int64_t N, int d, float sigma
   P.sb_nexp = (int*)nexp;
   P.sb_flag = (int*)flag;
   blkinfo_kernel<<<blocks_for(P.nsb, 8), 256, 0, st>>>(P.xs, N, d, SB / 32, P.scale, P.nsb, P.sb_ctr,
-                                                       P.sb_flag, allow_expanded); count_launch();
+                                                       P.sb_flag, allow_expanded_sb); count_launch();
   order_kernel<<<1, SCAN_THREADS, 0, st>>>(P.sb_flag, P.nsb, P.sb_order, P.sb_nexp); count_launch();
   const int64_t ntiles = P.Npad / TS;
   void* tbox;
