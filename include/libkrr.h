@@ -147,7 +147,19 @@ typedef enum {
      * weights (a few launches; waits for them) and keeps the fastest for
      * later products of that shape.  Results stay within the same error
      * bars; the summation grouping, hence the last bits, may differ. */
-    KRR_OPT_AUTOTUNE = 3
+    KRR_OPT_AUTOTUNE = 3,
+    /* Target-row shard emulation (the row partition a multi-GPU product
+     * would use, run on one GPU): with SHARD_COUNT = P > 1, krr_kernel_mvp
+     * on this handle computes and writes only shard SHARD_INDEX = k of its
+     * target rows: the sorted (Morton-order) super-blocks
+     * [k nsb / P, (k+1) nsb / P) of 256 targets, that is 1/P of the work.
+     * The other rows of Y are left as they were (a host Y is uploaded
+     * first).  The plans are those of the whole product, so the P shards
+     * written into one Y equal the unsharded product bit for bit.  Other
+     * entry points ignore the setting.  SHARD_COUNT: 1 (default) to 4096;
+     * SHARD_INDEX: 0 to SHARD_COUNT - 1 (checked at the call). */
+    KRR_OPT_SHARD_COUNT = 4,
+    KRR_OPT_SHARD_INDEX = 5
 } krr_option;
 
 /* Kernel functions (KRR_OPT_KERNEL). */

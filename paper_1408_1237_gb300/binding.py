@@ -364,6 +364,7 @@ def krr_measure_rsqrt_rate(handle=None, stream=None):
 KRR_OPT_TCGEN05 = 1
 KRR_OPT_KERNEL = 2
 KRR_OPT_AUTOTUNE = 3
+KRR_OPT_SHARD_COUNT, KRR_OPT_SHARD_INDEX = 4, 5
 KRR_KERNEL_GAUSSIAN, KRR_KERNEL_MATERN32 = 0, 1
 
 

@@ -109,6 +109,11 @@ struct Ctx {
   // fastest; split_scale is the scale in force for the product being planned
   bool autotune = false;
   bool tuning = false;
+  // target-row shard emulation (KRR_OPT_SHARD_COUNT / _INDEX): the products
+  // of krr_kernel_mvp compute and write only sorted target rows
+  // [row_lo, row_hi) (whole super-blocks); elsewhere the range is everything
+  int shard_count = 1, shard_index = 0;
+  int64_t row_lo = 0, row_hi = INT64_MAX;
   int prod_depth = 0;
   double split_scale = 1.0;
   std::unordered_map<std::string, double> tune_cache;

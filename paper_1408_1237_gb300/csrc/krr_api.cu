@@ -268,6 +268,16 @@ krr_status krr_set_option(krr_handle h, int option, int value) {
     case KRR_OPT_AUTOTUNE:
       h->ctx.autotune = value != 0;
       return KRR_OK;
+    case KRR_OPT_SHARD_COUNT:
+      if (value < 1 || value > 4096)
+        return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: shard count %d out of [1, 4096]", value);
+      h->ctx.shard_count = value;
+      return KRR_OK;
+    case KRR_OPT_SHARD_INDEX:
+      if (value < 0)
+        return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: shard index %d < 0", value);
+      h->ctx.shard_index = value;
+      return KRR_OK;
     case KRR_OPT_KERNEL:
       if (value != KRR_KERNEL_GAUSSIAN && value != KRR_KERNEL_MATERN32)
         return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: unknown kernel family %d", value);
@@ -324,15 +334,31 @@ krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float 
   if (!Q || !Y) return set_error(c, KRR_ERR_INVALID_ARG, "%s: Q or Y is NULL", fn);
   if (Y == Q || (const void*)Y == (const void*)X)
     return set_error(c, KRR_ERR_INVALID_ARG, "%s: Y aliases an input", fn);
+  const bool sharded = c.shard_count > 1;
+  if (c.shard_index >= c.shard_count)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: shard index %d >= shard count %d", fn, c.shard_index,
+                     c.shard_count);
   cudaStream_t st = (cudaStream_t)stream;
   float *dX, *dQ, *dY;
   bool sX, sQ, sY;
   if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
   if ((s = device_view(c, "stage.Q", Q, (size_t)N * m, true, st, &dQ, &sQ))) return s;
-  if ((s = device_view(c, "stage.Y", Y, (size_t)N * m, false, st, &dY, &sY))) return s;
+  // a shard leaves the other rows of Y as they were: a host Y goes up first
+  if ((s = device_view(c, "stage.Y", Y, (size_t)N * m, sharded, st, &dY, &sY))) return s;
   PointsDev P;
   cudaError_t e = prepare_points(c, dX, N, d, sigma, "pts", P, st);
   if (e) return cuda_error(c, e, fn);
+  struct RowRange {
+    Ctx& c;
+    ~RowRange() {
+      c.row_lo = 0;
+      c.row_hi = INT64_MAX;
+    }
+  } row_range{c};
+  if (sharded) {
+    c.row_lo = (int64_t)SB * (P.nsb * c.shard_index / c.shard_count);
+    c.row_hi = (int64_t)SB * (P.nsb * (c.shard_index + 1) / c.shard_count);
+  }
   void* qs;
   if ((e = c.ws.get("mvp.qs", sizeof(float) * P.Npad * m, &qs))) return cuda_error(c, e, fn);
   if ((e = gather_sorted(dQ, N, m, P.perm, P.Npad, (float*)qs, st))) return cuda_error(c, e, fn);

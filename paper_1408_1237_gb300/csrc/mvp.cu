@@ -72,6 +72,8 @@ struct MvpParams {
   const int* active;    // predication flag (null: always run)
   int64_t part_stride;  // distance between splits in part (Nt_pad for one column)
   int64_t slot0;        // first block slot of the grid (blocks before it are not processed)
+  // sorted target rows computed (shard emulation): blocks outside are skipped
+  int64_t row_lo = 0, row_hi = INT64_MAX;
 };
 
 // Warp-cooperative transform of one raw source tile for this warp's centre:
@@ -213,7 +215,11 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
   const int64_t slot = p.slot0 + (int64_t)blockIdx.x * NW + warp;
   const int64_t nexp = *p.tn_exp;
   const bool live = slot < p.nblk;
-  const int64_t blk = live ? p.torder[slot] : 0;
+  int64_t blk = live ? p.torder[slot] : 0;
+  // a warp whose block lies outside the shard computes nothing; a CTA with
+  // no such warp leaves at once
+  const bool work = live && blk * 32 * T >= p.row_lo && blk * 32 * T < p.row_hi;
+  if (!__syncthreads_or(work)) return;
   const int64_t last = min(p.slot0 + ((int64_t)blockIdx.x + 1) * NW, p.nblk);  // CTA's block slots end
   const bool expanded = last <= nexp;  // uniform over the CTA
   float ctr[D];
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
     }
     r2[u] = a;
   }
-  if (blockIdx.y == 0 && live) {
+  if (blockIdx.y == 0 && work) {
 #pragma unroll
     for (int u = 0; u < T; ++u) {
       const int64_t i = blk * 32 * T + lane + 32 * u;
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
     if (!ok) {
       abort_flag = 1;
       if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
-    } else {
+    } else if (work) {
       transform_tile<D>(raw + (r % RS) * kRawFloats, wbuf, ctr, p.s, expanded);
       __syncwarp();
       if (expanded)
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(NT, 2) mvp_f32_kernel(const MvpParams p) {
     return;
   }
 
-  if (live) {
+  if (work) {
     double* part = p.part + (int64_t)blockIdx.y * p.part_stride;
 #pragma unroll
     for (int u = 0; u < T; ++u) {
@@ -359,8 +365,10 @@ __global__ void __launch_bounds__(NT, (D > 8 ? 1 : 2)) mvp_dirm_kernel(const Mvp
   const int64_t cta_end = min(slot0 + ((int64_t)blockIdx.x + 1) * bpc, p.nblk);
   if (cta_end <= nexp) return;  // every block of this CTA is expanded-form
   const int64_t slot = slot0 + (int64_t)blockIdx.x * bpc + warp / T;
-  const bool live = slot < p.nblk && slot >= nexp;
-  const int64_t blk = live ? p.torder[slot] : 0;
+  const bool in_range = slot < p.nblk && slot >= nexp;
+  const int64_t blk = in_range ? p.torder[slot] : 0;
+  const bool live = in_range && blk * 32 * T >= p.row_lo && blk * 32 * T < p.row_hi;  // shard
+  if (!__syncthreads_or(live)) return;  // no block of this CTA to compute
   const int64_t i = blk * 32 * T + 32 * (warp % T) + lane;
   const bool valid = live && i < p.Nt_pad;
   float xi[D];
@@ -487,6 +495,7 @@ struct FinParams {
   MvpOut o;
   double* dot_part;        // [columns][gridDim.x] per-block dot partials
   unsigned int* dot_count; // [columns] arrival counters (reset by the last block)
+  int64_t row_lo = 0, row_hi = INT64_MAX;  // sorted rows written (shard emulation)
 };
 
 __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
@@ -502,7 +511,8 @@ __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
   const int64_t cv = (int64_t)col * f.Npad;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double out = 0.0, dotv = 0.0;
-  if (i < f.N) {
+  const bool mine = i >= f.row_lo && i < f.row_hi;
+  if (i < f.N && mine) {
     const bool second = f.sb_flag && f.sb_flag[i / SB] == 0;
     const double* part = (second ? f.part2 : f.part) + cv;
     const int splits = second ? f.splits2 : f.splits;
@@ -515,7 +525,7 @@ __global__ void __launch_bounds__(256) mvp_finalize_kernel(const FinParams f) {
     if (f.o.out_orig) f.o.out_orig[(int64_t)col * f.N + f.o.perm[i]] = (float)out;
     if (f.o.dotw) dotv = out * (double)f.o.dotw[cv + i];
   }
-  if (i < f.Npad) {
+  if (i < f.Npad && mine) {
     if (f.o.out_f) f.o.out_f[cv + i] = (float)out;
     if (f.o.out_d) f.o.out_d[cv + i] = out;
   }
@@ -575,13 +585,14 @@ cudaError_t launch_typed(const MvpParams& p, int splits, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Split count minimising the makespan ceil(blocks*S/slots) * ceil(tiles/S).
-int choose_splits(int64_t blocks, int tiles, int slots) {
+// Split count minimising the makespan ceil(blocks*S/slots) * (ceil(tiles/S) +
+// setup), setup = a CTA's fixed cost in units of one source tile.
+int choose_splits(int64_t blocks, int tiles, int slots, double setup = 0.0) {
   int best = 1;
   double best_cost = 1e300;
   for (int s = 1; s <= std::min(tiles, 64); ++s) {
     const double waves = std::ceil((double)blocks * s / slots);
-    const double cost = waves * std::ceil((double)tiles / s);
+    const double cost = waves * (std::ceil((double)tiles / s) + setup);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = s;
@@ -614,12 +625,13 @@ struct Plan {
   int tiles_per_split = 1;
 };
 
-// scale: the autotuner's factor on the modelled split count (1: the model).
-Plan make_plan(int64_t nblk, int ntiles, int num_sms, int plan_slots, double scale) {
+// scale: the autotuner's factor on the modelled split count (1: the model);
+// setup: a CTA's fixed cost in source tiles.
+Plan make_plan(int64_t nblk, int ntiles, int num_sms, int plan_slots, double scale, double setup = 0.0) {
   const int slots = plan_slots > 0 ? plan_slots : num_sms * 2;
   const int64_t ctas = (nblk + NW - 1) / NW;
   Plan pl;
-  int splits = choose_splits(ctas, ntiles, slots);
+  int splits = choose_splits(ctas, ntiles, slots, setup);
   if (scale != 1.0)
     splits = std::max(1, std::min({(int)std::lround(splits * scale), ntiles, 256}));
   pl.tiles_per_split = (ntiles + splits - 1) / splits;
@@ -772,6 +784,13 @@ Plan tcx_dir_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
 }
 
 Plan tcx_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+  if (Tp.d > 8) {
+    // high-dimensional kernel: one CTA per SM (two at d = 16), and a CTA
+    // first builds its 256 target K-vectors (about one source tile of work)
+    const int occ = Tp.d <= 16 ? 2 : 1;
+    return make_plan(Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
+                     c.plan_slots > 0 ? c.plan_slots : occ * c.num_sms, c.split_scale, 1.0);
+  }
   return make_plan(Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
                    c.plan_slots > 0 ? c.plan_slots : 4 * c.num_sms, c.split_scale);
 }
@@ -989,6 +1008,8 @@ cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const flo
     p.q = q;
     p.ntiles = (int)(Sp.Npad / TS);
     p.err = c.d_err;
+  p.row_lo = c.row_lo;
+  p.row_hi = c.row_hi;
     p.s = Sp.scale;
     p.active = o.active;
     p.part_stride = Tp.Npad;
@@ -1029,6 +1050,8 @@ cudaError_t tcx_path(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const flo
   f.o = o;
   f.dot_part = (double*)dpart;
   f.dot_count = (unsigned*)dcnt;
+  f.row_lo = c.row_lo;
+  f.row_hi = c.row_hi;
   mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
 }
@@ -1063,6 +1086,8 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   p.active = o.active;
   p.part_stride = Tp.Npad;
   p.err = c.d_err;
+  p.row_lo = c.row_lo;
+  p.row_hi = c.row_hi;
   if (Tp.d < 1 || Tp.d > 8) return cudaErrorNotSupported;
   const Plan pl = make_plan(Tp.nblk, p.ntiles, c.num_sms, c.plan_slots, c.split_scale);
   cudaError_t e = mvp_reserve(c, Tp, Sp, st);
@@ -1106,6 +1131,8 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
   f.o = o;
   f.dot_part = (double*)dpart;
   f.dot_count = (unsigned*)dcnt;
+  f.row_lo = c.row_lo;
+  f.row_hi = c.row_hi;
   mvp_finalize_kernel<<<fin_blocks, 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
 }
@@ -1161,6 +1188,8 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   p.xs = Sp.xs;
   p.ntiles = (int)(Sp.Npad / TS);
   p.err = c.d_err;
+  p.row_lo = c.row_lo;
+  p.row_hi = c.row_hi;
   p.s = Sp.scale;
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
@@ -1215,6 +1244,8 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   f.o = o;
   f.dot_part = (double*)dpart;
   f.dot_count = (unsigned*)dcnt;
+  f.row_lo = c.row_lo;
+  f.row_hi = c.row_hi;
   mvp_finalize_kernel<<<dim3(fin_blocks, (unsigned)m), 256, 0, st>>>(f); count_launch();
   return cudaGetLastError();
 }

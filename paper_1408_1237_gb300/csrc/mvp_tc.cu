@@ -63,6 +63,9 @@ struct TcParams {
   // tile (8 KB) per source tile
   const uint16_t* qh_tiles;
   const uint16_t* ql_tiles;
+  // sorted target rows computed (shard emulation): whole super-blocks outside
+  // [row_lo, row_hi) are skipped
+  int64_t row_lo = 0, row_hi = INT64_MAX;
 };
 
 // Terms of the split exponent: 4 (Ah Bh + Ah Bl + Al Bh + Al Bl) when 4(D+1)
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(256) mvp_tc_kernel(const TcParams p) {
   constexpr int QBUF_W = (SPLIT ? 2 : 1) * MC * QSTRIDE_W;
 
   const int64_t blk = p.torder[blockIdx.x];
+  if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
   float ctr[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
@@ -461,6 +465,7 @@ __global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const Tc
   float* qbuf = reinterpret_cast<float*>(kvb + 2 * TS * L::KV_STRIDE_W);  // 2 x TS weights
 
   const int64_t blk = p.torder[blockIdx.x];
+  if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
   float ctr[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
@@ -707,6 +712,7 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
   const int64_t nexp = *p.tn_exp;
   if ((int64_t)blockIdx.x >= nexp) return;
   const int64_t blk = p.torder[blockIdx.x];
+  if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
   const int64_t row0 = blk * p.WB;
   for (int k = tid; k < D; k += nthreads) ctr[k] = p.tctr[blk * D + k];
   for (int w = tid; w < TS * ST; w += nthreads) kv[w] = 0u;  // padding slots stay zero
@@ -788,7 +794,12 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
     if (abort_flag) break;
     // ---- source K-vectors B' = [Bh, Bl, Bh] over [2 v, -|v|^2] and weights
     const float* rs = raw + (r % RSD) * RAW;
-    for (int j = tid; j < TS; j += nthreads) {
+    // with 2 TS threads, the two threads of a source write half of its
+    // components each (both form |v|^2)
+    const int parts = nthreads >= 2 * TS ? 2 : 1;
+    const int part = parts == 2 ? tid / TS : 0;
+    const int k_lo = part * (D / parts), k_hi = k_lo + D / parts;
+    for (int j = parts == 2 ? tid % TS : tid; j < TS; j += (parts == 2 ? TS : nthreads)) {
       float bb = 0.f;
 #pragma unroll 8
       for (int k = 0; k < D; ++k) {
@@ -798,7 +809,7 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
       const bool far = bb < -30000.f;  // farther than any target can see: contributes 0
       uint16_t* row = reinterpret_cast<uint16_t*>(kv + j * ST);
 #pragma unroll 4
-      for (int k = 0; k < D; ++k) {
+      for (int k = k_lo; k < k_hi; ++k) {
         const float v = far ? 0.f : 2.f * p.s * (rs[k * TS + j] - ctr[k]);
         const typename H::T vh = H::from(v);
         const typename H::T vl = H::from(v - H::to(vh));
@@ -806,13 +817,15 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
         row[W + k] = *reinterpret_cast<const uint16_t*>(&vl);
         row[2 * W + k] = *reinterpret_cast<const uint16_t*>(&vh);
       }
-      const float b = far ? -30000.f : bb;
-      const typename H::T bh = H::from(b);
-      const typename H::T bl = H::from(b - H::to(bh));
-      row[D] = *reinterpret_cast<const uint16_t*>(&bh);
-      row[W + D] = *reinterpret_cast<const uint16_t*>(&bl);
-      row[2 * W + D] = *reinterpret_cast<const uint16_t*>(&bh);
-      qbuf[j] = rs[D * TS + j];
+      if (part == parts - 1) {
+        const float b = far ? -30000.f : bb;
+        const typename H::T bh = H::from(b);
+        const typename H::T bl = H::from(b - H::to(bh));
+        row[D] = *reinterpret_cast<const uint16_t*>(&bh);
+        row[W + D] = *reinterpret_cast<const uint16_t*>(&bl);
+        row[2 * W + D] = *reinterpret_cast<const uint16_t*>(&bh);
+        qbuf[j] = rs[D * TS + j];
+      }
     }
     __syncthreads();  // kv ready; the raw stage may be refilled
     if (tid == 0 && r + RSD < nt) {
@@ -823,7 +836,9 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
 #pragma unroll 1
     for (int kk = 0; kk < TS / 16; ++kk) {
       const int j0 = kk * 16 + g, j1 = j0 + 8;
-      float e0[MT][4], e1[MT][4];
+      // even and odd contraction steps accumulate separately (twice the
+      // independent MMA chains), summed before the exponential
+      float e0[MT][4], e1[MT][4], o0[MT][4], o1[MT][4];
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
         const uint32_t b00 = kv[j0 * ST + 8 * ks + t], b01 = kv[j0 * ST + 8 * ks + t + 4];
@@ -833,12 +848,25 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
           if (ks == 0) {
             mma16816_z(e0[mt], afr[mt][0], b00, b01);
             mma16816_z(e1[mt], afr[mt][0], b10, b11);
+          } else if (ks == 1) {
+            mma16816_z(o0[mt], afr[mt][1], b00, b01);
+            mma16816_z(o1[mt], afr[mt][1], b10, b11);
+          } else if (ks & 1) {
+            mma16816<false>(o0[mt], afr[mt][ks], b00, b01);
+            mma16816<false>(o1[mt], afr[mt][ks], b10, b11);
           } else {
             mma16816<false>(e0[mt], afr[mt][ks], b00, b01);
             mma16816<false>(e1[mt], afr[mt][ks], b10, b11);
           }
         }
       }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          e0[mt][v] += o0[mt][v];
+          e1[mt][v] += o1[mt][v];
+        }
       const float2 q0 = *reinterpret_cast<const float2*>(qbuf + kk * 16 + 2 * t);
       const float2 q1 = *reinterpret_cast<const float2*>(qbuf + kk * 16 + 8 + 2 * t);
 #pragma unroll
@@ -1034,6 +1062,7 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
   unsigned char* sB = sA + 2 * ROWS * L::KV;  // two B buffers
 
   const int64_t blk = p.torder[sb_slot];
+  if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
   float ctr[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
@@ -1492,6 +1521,8 @@ cudaError_t mvp_tc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, cons
   p.part = part;
   p.fac = fac;
   p.err = c.d_err;
+  p.row_lo = c.row_lo;
+  p.row_hi = c.row_hi;
   p.s = S.scale;
   p.active = active;
   switch (T.d) {
@@ -1528,6 +1559,8 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
   p.part = part;
   p.fac = fac;
   p.err = c.d_err;
+  p.row_lo = c.row_lo;
+  p.row_hi = c.row_hi;
   p.s = S.scale;
   p.active = active;
   switch (T.d) {
@@ -1586,6 +1619,8 @@ cudaError_t mvp_umma_partials(Ctx& c, const PointsDev& T, const PointsDev& S, co
   p.part = part;
   p.fac = fac;
   p.err = c.d_err;
+  p.row_lo = c.row_lo;
+  p.row_hi = c.row_hi;
   p.s = S.scale;
   p.active = active;
   switch (T.d) {
