@@ -1348,6 +1348,223 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------------------
+// High-dimensional single-column product on the 5th-generation tensor cores
+// (tcgen05, option KRR_OPT_TCGEN05): the contraction of mvp_tch_kernel, the
+// split 3 (d + 1)-term K-vectors of 128 targets against 128 sources at a
+// time, as KSTEPS tcgen05.mma (M = N = 128, K = 16, f16 in, f32 out) into
+// tensor memory.  A synchronous CTA of 8 warps, per chunk of 128 sources:
+//   1. the two threads of a source write half of its K-vector each into the
+//      B operand (K-major core matrices, no swizzle); fence and barrier;
+//   2. one thread issues the MMAs and commits them to an mbarrier;
+//   3. after the (bounded) wait the threads read S from tensor memory (warp
+//      w: lanes 32 (w mod 4) on, i.e. target rows, and half of the chunk's
+//      columns) and add q_j 2^S_ij; the two halves of a row are summed at
+//      the end.
+// Two CTAs per compact super-block (128 targets each).  The raw source
+// tiles arrive by TMA bulk copies; a tile's stage is refilled as soon as the
+// B operands of its last chunk are written (its weights are copied first).
+namespace uhd {
+constexpr int ROWS = 128;     // targets per CTA (MMA M, tensor-memory lanes)
+constexpr int NC = 128;       // sources per chunk (MMA N, tensor-memory columns)
+constexpr int THREADS = 256;  // two threads per target row / source
+template <int D>
+struct L {
+  static constexpr int W = D + 1;
+  static constexpr int KSTEPS = (3 * W + 15) / 16;
+  static constexpr int KV = 16 * KSTEPS;  // halves per K-vector
+  static constexpr int KC = KV / 8;       // 16-byte k-chunks
+  static constexpr int RSD = D <= 48 ? 2 : 1;
+};
+template <int D>
+constexpr size_t smem_bytes() {
+  using LL = L<D>;
+  return (size_t)(ROWS + NC) * LL::KV * 2 + sizeof(float) * ((size_t)LL::RSD * (D + 1) * TS + TS);
+}
+// one f16 value into a K-major no-swizzle operand (row, slot k)
+__device__ __forceinline__ void put(unsigned char* base, int row, int k, int kc, __half v) {
+  *reinterpret_cast<__half*>(base + umma::kmaj(row, k, kc)) = v;
+}
+}  // namespace uhd
+
+template <int D>
+__global__ void __launch_bounds__(uhd::THREADS) mvp_uhd_kernel(const TcParams p) {
+  using LL = uhd::L<D>;
+  using H = Half<false>;
+  constexpr int W = LL::W, KS = LL::KSTEPS, KC = LL::KC, RSD = LL::RSD;
+  constexpr int ROWS = uhd::ROWS, NC = uhd::NC, NT = uhd::THREADS;
+  constexpr int RAW = (D + 1) * TS;  // coordinates, weights
+  constexpr int CPT = TS / NC;       // chunks per tile
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sA = smem_raw;
+  unsigned char* sB = sA + ROWS * LL::KV * 2;
+  float* raw = reinterpret_cast<float*>(sB + NC * LL::KV * 2);
+  float* qbuf = raw + RSD * RAW;
+  __shared__ __align__(8) uint64_t bars[RSD];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t dbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float ctr[D];
+  __shared__ double red[ROWS];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int half = tid / ROWS;  // which half of a source's components / a row's columns
+  if (p.active && *p.active == 0) return;
+  const int64_t nexp = *p.tn_exp;
+  const int64_t sb_slot = blockIdx.x >> 1;
+  if (sb_slot >= nexp) return;
+  const int64_t blk = p.torder[sb_slot];
+  if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
+  for (int k = tid; k < D; k += NT) ctr[k] = p.tctr[blk * D + k];
+  for (int w = tid; w < (ROWS + NC) * LL::KV * 2 / 16; w += NT)
+    reinterpret_cast<uint4*>(sA)[w] = make_uint4(0u, 0u, 0u, 0u);  // padding slots stay zero
+  __syncthreads();
+  const int row = tid % ROWS;
+  const int64_t i = blk * SB + (int64_t)(blockIdx.x & 1) * ROWS + row;
+  if (half == 0) {  // operand A: this row's K-vector [uh, uh, ul] over [u, 1]
+    const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+    float r2 = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < D; ++k) {
+      const float u = p.s * (p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS] - ctr[k]);
+      r2 = fmaf(u, u, r2);
+      const __half uh = H::from(u), ul = H::from(u - H::to(uh));
+      uhd::put(sA, row, k, KC, uh);
+      uhd::put(sA, row, W + k, KC, uh);
+      uhd::put(sA, row, 2 * W + k, KC, ul);
+    }
+    uhd::put(sA, row, D, KC, H::from(1.f));
+    uhd::put(sA, row, W + D, KC, H::from(1.f));
+    uhd::put(sA, row, 2 * W + D, KC, H::from(0.f));
+    if (blockIdx.y == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
+  }
+  if (tid == 0) {
+    for (int st = 0; st < RSD; ++st) mbar_init(&bars[st], 1);
+    mbar_init(&mma_bar, 1);
+    mbar_init(&dbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&tmem_slot)), "r"(NC) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async_smem();  // operand A: generic-proxy writes, read by the tensor cores
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+  auto issue = [&](int r) {
+    const int stage = r % RSD;
+    const int64_t tile = t_begin + r;
+    float* dst = raw + stage * RAW;
+    mbar_arrive_expect_tx(&bars[stage], (uint32_t)RAW * 4);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS, p.Q + tile * (int64_t)TS, TS * 4, &bars[stage]);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(RSD, nt); ++issued) issue(issued);
+  const uint32_t id_s = umma::idesc(0, NC, ROWS);
+  const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
+  float S = 0.f, C = 0.f;
+  uint32_t n_mma = 0;
+  bool ok = true;
+  for (int r = 0; r < nt && ok; ++r) {
+    ok = __syncthreads_and(mbar_wait_bounded(&bars[r % RSD], (r / RSD) & 1));
+    if (!ok) break;
+    const float* rs = raw + (r % RSD) * RAW;
+    // the tile's weights (read by the epilogues after its stage is refilled)
+    qbuf[tid] = rs[D * TS + tid];
+    for (int q = 0; q < CPT && ok; ++q) {
+      {  // operand B: source j's K-vector [vh, vl, vh] over [2 v, -|v|^2]
+        const int jr = tid % NC, j = q * NC + jr;
+        const int k_lo = half * (D / 2), k_hi = k_lo + D / 2;
+        float bb = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < D; ++k) {
+          const float v = p.s * (rs[k * TS + j] - ctr[k]);
+          bb = fmaf(-v, v, bb);
+        }
+        const bool far = bb < -30000.f;  // farther than any target can see: contributes 0
+#pragma unroll 4
+        for (int k = k_lo; k < k_hi; ++k) {
+          const float v = far ? 0.f : 2.f * p.s * (rs[k * TS + j] - ctr[k]);
+          const __half vh = H::from(v), vl = H::from(v - H::to(vh));
+          uhd::put(sB, jr, k, KC, vh);
+          uhd::put(sB, jr, W + k, KC, vl);
+          uhd::put(sB, jr, 2 * W + k, KC, vh);
+        }
+        if (half == 1) {
+          const float b = far ? -30000.f : bb;
+          const __half bh = H::from(b), bl = H::from(b - H::to(bh));
+          uhd::put(sB, jr, D, KC, bh);
+          uhd::put(sB, jr, W + D, KC, bl);
+          uhd::put(sB, jr, 2 * W + D, KC, bh);
+        }
+      }
+      fence_proxy_async_smem();
+      umma::fence_before();
+      __syncthreads();  // B written; the previous chunk's S has been read
+      if (q == CPT - 1 && tid == 0 && r + RSD < nt) {  // the stage is no longer read
+        fence_proxy_async_smem();
+        issue(r + RSD);
+        ++issued;
+      }
+      if (tid == 0) {
+        umma::fence_after();
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+          umma::mma_ss(tmem, umma::sdesc(a_addr + 256u * ks, KC * 128), umma::sdesc(b_addr + 256u * ks, KC * 128),
+                       id_s, ks > 0);
+        umma::commit(&mma_bar);
+      }
+      ok = __syncthreads_and(mbar_wait_bounded(&mma_bar, n_mma & 1));
+      ++n_mma;
+      if (!ok) break;
+      umma::fence_after();
+      // this row of S: 2^S_ij weighted by q_j over this half of the chunk
+#pragma unroll 1
+      for (int cb = half * (NC / 2); cb < (half + 1) * (NC / 2); cb += 32) {
+        uint32_t v[32];
+        umma::ld32(tmem + lanes + (uint32_t)cb, v);
+        umma::wait_ld();
+        const float* qc = qbuf + q * NC + cb;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 32; e += 2)
+          acc = ffma2(make_float2(qc[e], qc[e + 1]),
+                      make_float2(ex2(__uint_as_float(v[e])), ex2(__uint_as_float(v[e + 1]))), acc);
+        kahan_add(S, C, acc.x + acc.y);
+      }
+      umma::fence_before();
+    }
+    __syncthreads();  // the tile's epilogues are done with qbuf
+  }
+  if (!ok) {
+    // let every MMA issued complete before tensor memory is released, and
+    // drain the copies in flight
+    if (tid == 0) {
+      umma::commit(&dbar);
+      mbar_wait_bounded(&dbar, 0);
+      for (int rr = 0; rr < issued; ++rr) mbar_wait_bounded(&bars[rr % RSD], (rr / RSD) & 1);
+      atomicExch(p.err, DEV_TIMEOUT);
+    }
+  }
+  // the two halves of each row
+  if (half == 1) red[row] = (double)S - (double)C;
+  __syncthreads();
+  if (ok && half == 0 && i < p.Nt_pad)
+    p.part[(int64_t)blockIdx.y * p.Nt_pad + i] = ((double)S - (double)C) + red[row];
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NC) : "memory");
+}
+
 // Weights Q (m columns, stride ld, sorted, zero padded) -> per source tile a
 // 16 x 256 K-major f16 tile (core matrices 8 rows x 16 B): hi, and lo = the
 // float32 remainder when split; rows m..15 zero.  One thread per 8 sources of
@@ -1427,6 +1644,24 @@ cudaError_t tcx_launch_typed(const TcParams& p, int splits, cudaStream_t st, boo
   if (dry) return cudaSuccess;
   dim3 grid((unsigned)p.nblk, (unsigned)splits);
   mvp_tcx_kernel<D, TCX_MT><<<grid, 32 * (SB / (16 * TCX_MT)), tcx_smem_bytes<D>(), st>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t uhd_launch_typed(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(mvp_uhd_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)uhd::smem_bytes<D>());
+    if (e) return e;
+    done[dev] = true;
+  }
+  if (dry) return cudaSuccess;
+  dim3 grid((unsigned)(2 * p.nblk), (unsigned)splits);
+  mvp_uhd_kernel<D><<<grid, uhd::THREADS, uhd::smem_bytes<D>(), st>>>(p);
   count_launch();
   return cudaGetLastError();
 }
@@ -1572,10 +1807,10 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
     case 6: return tcx_launch_typed<6>(p, splits, st, dry);
     case 7: return tcx_launch_typed<7>(p, splits, st, dry);
     case 8: return tcx_launch_typed<8>(p, splits, st, dry);
-    case 16: return tch_launch_typed<16>(p, splits, st, dry);
-    case 32: return tch_launch_typed<32>(p, splits, st, dry);
-    case 48: return tch_launch_typed<48>(p, splits, st, dry);
-    case 64: return tch_launch_typed<64>(p, splits, st, dry);
+    case 16: return c.use_tcgen05 ? uhd_launch_typed<16>(p, splits, st, dry) : tch_launch_typed<16>(p, splits, st, dry);
+    case 32: return c.use_tcgen05 ? uhd_launch_typed<32>(p, splits, st, dry) : tch_launch_typed<32>(p, splits, st, dry);
+    case 48: return c.use_tcgen05 ? uhd_launch_typed<48>(p, splits, st, dry) : tch_launch_typed<48>(p, splits, st, dry);
+    case 64: return c.use_tcgen05 ? uhd_launch_typed<64>(p, splits, st, dry) : tch_launch_typed<64>(p, splits, st, dry);
     default: return cudaErrorNotSupported;
   }
 }
