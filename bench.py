@@ -637,9 +637,10 @@ def tensor_peak_tflops():
 def highd_form(K, torch, rank, dev):
     """High-dimensional single-column products (N = 65536 uniform in [0,1]^d):
     the cross term on the tensor cores (kernel width 0.3 sqrt(d): compact
-    super-blocks) against the direct form on the CUDA cores (the same points
-    at width 0.02 sqrt(d): no compact block).  The tensor path's contraction
-    is 3 (d + 1) split-f16 products per pair, 2 flops each."""
+    super-blocks), with tcgen05 (default) and with mma.sync (option), against
+    the direct form on the CUDA cores (the same points at width 0.02 sqrt(d):
+    no compact block).  The contraction is 3 (d + 1) split-f16 products per
+    pair, 2 flops each."""
     import numpy as np
     peak, src = tensor_peak_tflops()
     out = {}
@@ -650,11 +651,10 @@ def highd_form(K, torch, rank, dev):
         q = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
         y = torch.empty_like(q)
         row = {}
-        for name, width, tc5 in (("tensor", 0.3, 0), ("tcgen05", 0.3, 1), ("direct", 0.02, 0)):
+        for name, width, tc5 in (("tensor", 0.3, 0), ("tcgen05", 0.3, 1), ("direct", 0.02, 1)):
             sig = width * float(np.sqrt(d))
             h = K.Handle()
-            if tc5:
-                K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h)
+            K.krr_set_option(K.KRR_OPT_HIGHD_TCGEN05, tc5, handle=h)
             K.krr_kernel_mvp(X, q, sig, 1e-3, out=y, handle=h)
             torch.cuda.synchronize(dev)
             K.krr_profile_enable(True, handle=h)
@@ -668,13 +668,13 @@ def highd_form(K, torch, rank, dev):
         tflops = float(n) * n * 2 * 3 * (d + 1) / (row["tensor"]["kernel_ms"] / 1e3) / 1e12
         row["tensor"]["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                                      "frac": tflops / peak, "peak_source": f"bf16 dense, {src}",
-                                     "kernel": f"mvp_tch_kernel<{((d + 15) // 16) * 16}> (mma.sync m16n8k16)"}
+                                     "kernel": f"mvp_tch_kernel<{((d + 15) // 16) * 16}> (mma.sync m16n8k16, by option)"}
         tflops5 = float(n) * n * 2 * 3 * (d + 1) / (row["tcgen05"]["kernel_ms"] / 1e3) / 1e12
         row["tcgen05"]["roofline"] = {"bound": "tensor", "achieved": tflops5, "peak": peak, "unit": "TFLOP/s",
                                       "frac": tflops5 / peak, "peak_source": f"bf16 dense, {src}",
                                       "kernel": f"mvp_uhd_kernel<{((d + 15) // 16) * 16}> (tcgen05.mma, TMEM)"}
-        row["speedup"] = row["direct"]["kernel_ms"] / row["tensor"]["kernel_ms"]
-        row["speedup_tcgen05"] = row["direct"]["kernel_ms"] / row["tcgen05"]["kernel_ms"]
+        row["speedup_mma_sync"] = row["direct"]["kernel_ms"] / row["tensor"]["kernel_ms"]
+        row["speedup"] = row["direct"]["kernel_ms"] / row["tcgen05"]["kernel_ms"]
         out[f"d{d}"] = row
     return out
 

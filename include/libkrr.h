@@ -159,7 +159,13 @@ typedef enum {
      * entry points ignore the setting.  SHARD_COUNT: 1 (default) to 4096;
      * SHARD_INDEX: 0 to SHARD_COUNT - 1 (checked at the call). */
     KRR_OPT_SHARD_COUNT = 4,
-    KRR_OPT_SHARD_INDEX = 5
+    KRR_OPT_SHARD_INDEX = 5,
+    /* value != 0 (default): single-column products above 8 dimensions
+     * contract their compact super-blocks with tcgen05.mma into tensor
+     * memory; 0: with mma.sync.  Same results to the float32 bar; on GB300
+     * the default is faster (measured at N = 65536: d = 16 2696 vs 2505,
+     * d = 32 1439 vs 1188, d = 64 741 vs 657 Gpairs/s). */
+    KRR_OPT_HIGHD_TCGEN05 = 6
 } krr_option;
 
 /* Kernel functions (KRR_OPT_KERNEL). */

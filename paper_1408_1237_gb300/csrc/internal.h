@@ -101,6 +101,9 @@ struct Ctx {
   // multi-column tensor-core products on the tcgen05 / tensor-memory kernel
   // instead of the mma.sync kernel (krr_set_option)
   bool use_tcgen05 = false;
+  // single-column products above 8 dimensions on the tcgen05 kernel
+  // (mvp_uhd_kernel; false: the mma.sync kernel mvp_tch_kernel)
+  bool highd_tcgen05 = true;
   // kernel function of every product and solve (KRR_KERNEL_*, krr_set_option)
   int kernel_family = 0;
   // autotuning of the products' source splits (KRR_OPT_AUTOTUNE): the first

@@ -785,11 +785,11 @@ Plan tcx_dir_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
 
 Plan tcx_plan(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
   if (Tp.d > 8) {
-    if (c.use_tcgen05) {
+    if (c.highd_tcgen05) {
       // tcgen05 kernel: two CTAs of 128 targets per super-block, one
-      // resident per SM (three at d = 16); a CTA first builds its 128 target
-      // K-vectors (about half a source tile of work)
-      const int occ = Tp.d <= 16 ? 3 : 1;
+      // resident per SM (two at d = 16: shared and tensor memory); a CTA
+      // first builds its 128 target K-vectors (about half a source tile)
+      const int occ = Tp.d <= 16 ? 2 : 1;
       return make_plan(2 * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
                        c.plan_slots > 0 ? c.plan_slots : occ * c.num_sms, c.split_scale, 0.5);
     }

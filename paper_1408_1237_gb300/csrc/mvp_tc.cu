@@ -1350,102 +1350,137 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
 
 // ------------------------------------------------------------------------
 // High-dimensional single-column product on the 5th-generation tensor cores
-// (tcgen05, option KRR_OPT_TCGEN05): the contraction of mvp_tch_kernel, the
+// (tcgen05; the default above 8 dimensions, KRR_OPT_HIGHD_TCGEN05): the
+// contraction of mvp_tch_kernel, the
 // split 3 (d + 1)-term K-vectors of 128 targets against 128 sources at a
 // time, as KSTEPS tcgen05.mma (M = N = 128, K = 16, f16 in, f32 out) into
-// tensor memory.  A synchronous CTA of 8 warps, per chunk of 128 sources:
-//   1. the two threads of a source write half of its K-vector each into the
-//      B operand (K-major core matrices, no swizzle); fence and barrier;
-//   2. one thread issues the MMAs and commits them to an mbarrier;
-//   3. after the (bounded) wait the threads read S from tensor memory (warp
-//      w: lanes 32 (w mod 4) on, i.e. target rows, and half of the chunk's
-//      columns) and add q_j 2^S_ij; the two halves of a row are summed at
-//      the end.
-// Two CTAs per compact super-block (128 targets each).  The raw source
-// tiles arrive by TMA bulk copies; a tile's stage is refilled as soon as the
-// B operands of its last chunk are written (its weights are copied first).
+// tensor memory.  Warp-specialized pipeline over chunks of 128 sources:
+//  * 8 worker warps: write the K-vectors of chunk c + 1 into the B operand
+//    buffer (c + 1) & 1 (K-major core matrices, no swizzle; the two threads
+//    of a source take half of its components each), then read S of chunk c
+//    from tensor-memory buffer c & 1 (warp w: lanes 32 (w mod 4) on = target
+//    rows, half of the columns) and add q_j 2^S_ij;
+//  * 1 MMA warp: issues chunk c once its B operand is written and the
+//    epilogue of chunk c - 2 has released the S buffer, and commits to
+//    mdone[c & 1].
+// A B buffer is rewritten only after the epilogue of its previous chunk,
+// which waited for that chunk's MMAs.  Two CTAs per compact super-block (128
+// targets each).  Raw source tiles arrive by TMA bulk copies; a tile's stage
+// is refilled once the B operands of its last chunk are written (its weights
+// are copied to a per-tile buffer first).  Every wait is bounded; on abort
+// the issued MMAs and copies are drained before tensor memory is freed.
 namespace uhd {
 constexpr int ROWS = 128;     // targets per CTA (MMA M, tensor-memory lanes)
-constexpr int NC = 128;       // sources per chunk (MMA N, tensor-memory columns)
-constexpr int THREADS = 256;  // two threads per target row / source
+constexpr int WORKERS = 256;  // 8 worker warps; warp 8 issues the MMAs
+// K-vector layout: three terms, each padded to W8 = round_up(d + 1, 8) slots,
+// so that every 16-byte k-chunk holds 8 consecutive components of one term
+// (one vector store each).
 template <int D>
 struct L {
   static constexpr int W = D + 1;
-  static constexpr int KSTEPS = (3 * W + 15) / 16;
-  static constexpr int KV = 16 * KSTEPS;  // halves per K-vector
-  static constexpr int KC = KV / 8;       // 16-byte k-chunks
-  static constexpr int RSD = D <= 48 ? 2 : 1;
+  static constexpr int W8 = (W + 7) / 8 * 8;
+  static constexpr int G = W8 / 8;                 // k-chunks per term
+  static constexpr int KSTEPS = (3 * G + 1) / 2;   // K = 16 per MMA
+  static constexpr int KV = 16 * KSTEPS;           // halves per K-vector
+  static constexpr int KC = KV / 8;                // 16-byte k-chunks
+  // sources per chunk (MMA N) and raw stages, sized to the 227 KB of shared
+  // memory: A, two B buffers, the raw tiles, two tiles' weights
+  static constexpr int NC = D >= 64 ? 64 : 128;
+  static constexpr int RSD = D <= 32 ? 2 : 1;
+  static constexpr int TMEM_COLS = 2 * NC;
 };
 template <int D>
 constexpr size_t smem_bytes() {
   using LL = L<D>;
-  return (size_t)(ROWS + NC) * LL::KV * 2 + sizeof(float) * ((size_t)LL::RSD * (D + 1) * TS + TS);
+  return (size_t)(ROWS + 2 * LL::NC) * LL::KV * 2 + sizeof(float) * ((size_t)LL::RSD * (D + 1) * TS + 2 * TS);
 }
+static_assert(smem_bytes<64>() <= 225 * 1024 && smem_bytes<48>() <= 225 * 1024, "shared memory");
 // one f16 value into a K-major no-swizzle operand (row, slot k)
 __device__ __forceinline__ void put(unsigned char* base, int row, int k, int kc, __half v) {
   *reinterpret_cast<__half*>(base + umma::kmaj(row, k, kc)) = v;
 }
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(WORKERS) : "memory"); }
 }  // namespace uhd
 
 template <int D>
-__global__ void __launch_bounds__(uhd::THREADS) mvp_uhd_kernel(const TcParams p) {
+__global__ void __launch_bounds__(uhd::WORKERS + 32) mvp_uhd_kernel(const TcParams p) {
   using LL = uhd::L<D>;
   using H = Half<false>;
   constexpr int W = LL::W, KS = LL::KSTEPS, KC = LL::KC, RSD = LL::RSD;
-  constexpr int ROWS = uhd::ROWS, NC = uhd::NC, NT = uhd::THREADS;
+  constexpr int ROWS = uhd::ROWS, NC = LL::NC, NW8 = uhd::WORKERS;
+  constexpr int TPS = NW8 / NC;  // worker threads per source of a chunk
   constexpr int RAW = (D + 1) * TS;  // coordinates, weights
   constexpr int CPT = TS / NC;       // chunks per tile
+  constexpr uint32_t BBYTES = NC * LL::KV * 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sA = smem_raw;
-  unsigned char* sB = sA + ROWS * LL::KV * 2;
-  float* raw = reinterpret_cast<float*>(sB + NC * LL::KV * 2);
-  float* qbuf = raw + RSD * RAW;
+  unsigned char* sB = sA + ROWS * LL::KV * 2;  // two buffers
+  float* raw = reinterpret_cast<float*>(sB + 2 * BBYTES);
+  float* qbuf = raw + RSD * RAW;  // two tiles' weights
   __shared__ __align__(8) uint64_t bars[RSD];
-  __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ __align__(8) uint64_t dbar;
+  __shared__ __align__(8) uint64_t bready[2];  // B buffer written (worker warps)
+  __shared__ __align__(8) uint64_t mdone[2];   // chunk's MMAs complete (commit)
+  __shared__ __align__(8) uint64_t sfree[2];   // S buffer read (worker warps)
+  __shared__ __align__(8) uint64_t dbar;       // after an abort: every MMA issued is complete
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
   __shared__ float ctr[D];
   __shared__ double red[ROWS];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int half = tid / ROWS;  // which half of a source's components / a row's columns
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool mma_warp = warp == NW8 / 32;
+  const int half = (tid / ROWS) & 1;  // worker: half of a source's components / of a row's columns
   if (p.active && *p.active == 0) return;
   const int64_t nexp = *p.tn_exp;
   const int64_t sb_slot = blockIdx.x >> 1;
   if (sb_slot >= nexp) return;
   const int64_t blk = p.torder[sb_slot];
   if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
-  for (int k = tid; k < D; k += NT) ctr[k] = p.tctr[blk * D + k];
-  for (int w = tid; w < (ROWS + NC) * LL::KV * 2 / 16; w += NT)
+  for (int k = tid; k < D; k += blockDim.x) ctr[k] = p.tctr[blk * D + k];
+  for (int w = tid; w < (ROWS + 2 * NC) * LL::KV * 2 / 16; w += blockDim.x)
     reinterpret_cast<uint4*>(sA)[w] = make_uint4(0u, 0u, 0u, 0u);  // padding slots stay zero
   __syncthreads();
   const int row = tid % ROWS;
   const int64_t i = blk * SB + (int64_t)(blockIdx.x & 1) * ROWS + row;
-  if (half == 0) {  // operand A: this row's K-vector [uh, uh, ul] over [u, 1]
+  if (!mma_warp && half == 0) {  // operand A: this row's K-vector [uh | uh | ul] over [u, 1]
     const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+    const float* xr = p.xt + (ii / TS) * (int64_t)D * TS + ii % TS;
     float r2 = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < D; ++k) {
-      const float u = p.s * (p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS] - ctr[k]);
-      r2 = fmaf(u, u, r2);
-      const __half uh = H::from(u), ul = H::from(u - H::to(uh));
-      uhd::put(sA, row, k, KC, uh);
-      uhd::put(sA, row, W + k, KC, uh);
-      uhd::put(sA, row, 2 * W + k, KC, ul);
+    for (int g = 0; g < LL::G; ++g) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float u2[2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int k = 8 * g + 2 * e + h2;
+          u2[h2] = k < D ? p.s * (xr[(int64_t)k * TS] - ctr[k]) : (k == D ? 1.f : 0.f);
+          if (k < D) r2 = fmaf(u2[h2], u2[h2], r2);
+        }
+        hw[e] = H::pack(u2[0], u2[1]);
+        const float2 hv = H::unpack(hw[e]);
+        lw[e] = H::pack(u2[0] - hv.x, u2[1] - hv.y);
+      }
+      const uint4 hv4 = make_uint4(hw[0], hw[1], hw[2], hw[3]), lv4 = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      *reinterpret_cast<uint4*>(sA + umma::kmaj(row, 8 * g, KC)) = hv4;
+      *reinterpret_cast<uint4*>(sA + umma::kmaj(row, 8 * (LL::G + g), KC)) = hv4;
+      *reinterpret_cast<uint4*>(sA + umma::kmaj(row, 8 * (2 * LL::G + g), KC)) = lv4;
     }
-    uhd::put(sA, row, D, KC, H::from(1.f));
-    uhd::put(sA, row, W + D, KC, H::from(1.f));
-    uhd::put(sA, row, 2 * W + D, KC, H::from(0.f));
     if (blockIdx.y == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
   }
   if (tid == 0) {
+    abort_flag = 0;
     for (int st = 0; st < RSD; ++st) mbar_init(&bars[st], 1);
-    mbar_init(&mma_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bready[b], NW8 / 32);
+      mbar_init(&mdone[b], 1);
+      mbar_init(&sfree[b], NW8 / 32);
+    }
     mbar_init(&dbar, 1);
     fence_barrier_init();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_addr(&tmem_slot)), "r"(NC) : "memory");
+                 :: "r"(smem_addr(&tmem_slot)), "r"(LL::TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   fence_proxy_async_smem();  // operand A: generic-proxy writes, read by the tensor cores
@@ -1453,9 +1488,18 @@ __global__ void __launch_bounds__(uhd::THREADS) mvp_uhd_kernel(const TcParams p)
   __syncthreads();
   umma::fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
   const int t_begin = blockIdx.y * p.tiles_per_split;
   const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+  const int total = nt * CPT;
+  // a bounded wait that also gives up once the other role has aborted
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+      if (abort_flag || clock64() - t0 > WAIT_LIMIT_CLOCKS) return false;
+    }
+    return true;
+  };
   auto issue = [&](int r) {
     const int stage = r % RSD;
     const int64_t tile = t_begin + r;
@@ -1465,73 +1509,109 @@ __global__ void __launch_bounds__(uhd::THREADS) mvp_uhd_kernel(const TcParams p)
     bulk_g2s(dst + D * TS, p.Q + tile * (int64_t)TS, TS * 4, &bars[stage]);
   };
   int issued = 0;
-  if (tid == 0)
-    for (; issued < min(RSD, nt); ++issued) issue(issued);
-  const uint32_t id_s = umma::idesc(0, NC, ROWS);
-  const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
   float S = 0.f, C = 0.f;
-  uint32_t n_mma = 0;
   bool ok = true;
-  for (int r = 0; r < nt && ok; ++r) {
-    ok = __syncthreads_and(mbar_wait_bounded(&bars[r % RSD], (r / RSD) & 1));
-    if (!ok) break;
-    const float* rs = raw + (r % RSD) * RAW;
-    // the tile's weights (read by the epilogues after its stage is refilled)
-    qbuf[tid] = rs[D * TS + tid];
-    for (int q = 0; q < CPT && ok; ++q) {
-      {  // operand B: source j's K-vector [vh, vl, vh] over [2 v, -|v|^2]
-        const int jr = tid % NC, j = q * NC + jr;
-        const int k_lo = half * (D / 2), k_hi = k_lo + D / 2;
-        float bb = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < D; ++k) {
-          const float v = p.s * (rs[k * TS + j] - ctr[k]);
-          bb = fmaf(-v, v, bb);
-        }
-        const bool far = bb < -30000.f;  // farther than any target can see: contributes 0
-#pragma unroll 4
-        for (int k = k_lo; k < k_hi; ++k) {
-          const float v = far ? 0.f : 2.f * p.s * (rs[k * TS + j] - ctr[k]);
-          const __half vh = H::from(v), vl = H::from(v - H::to(vh));
-          uhd::put(sB, jr, k, KC, vh);
-          uhd::put(sB, jr, W + k, KC, vl);
-          uhd::put(sB, jr, 2 * W + k, KC, vh);
-        }
-        if (half == 1) {
-          const float b = far ? -30000.f : bb;
-          const __half bh = H::from(b), bl = H::from(b - H::to(bh));
-          uhd::put(sB, jr, D, KC, bh);
-          uhd::put(sB, jr, W + D, KC, bl);
-          uhd::put(sB, jr, 2 * W + D, KC, bh);
-        }
-      }
-      fence_proxy_async_smem();
-      umma::fence_before();
-      __syncthreads();  // B written; the previous chunk's S has been read
-      if (q == CPT - 1 && tid == 0 && r + RSD < nt) {  // the stage is no longer read
-        fence_proxy_async_smem();
-        issue(r + RSD);
-        ++issued;
-      }
-      if (tid == 0) {
+  if (mma_warp) {
+    // ================= MMA warp (one lane issues)
+    if (lane == 0) {
+      const uint32_t id_s = umma::idesc(0, NC, ROWS);
+      const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
+      for (int c = 0; c < total && ok; ++c) {
+        const int b = c & 1;
+        ok = wait(&bready[b], (c >> 1) & 1);
+        if (ok && c >= 2) ok = wait(&sfree[b], ((c - 2) >> 1) & 1);
+        if (!ok) break;
         umma::fence_after();
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks)
-          umma::mma_ss(tmem, umma::sdesc(a_addr + 256u * ks, KC * 128), umma::sdesc(b_addr + 256u * ks, KC * 128),
-                       id_s, ks > 0);
-        umma::commit(&mma_bar);
+          umma::mma_ss(tmem + (uint32_t)(b * NC), umma::sdesc(a_addr + 256u * ks, KC * 128),
+                       umma::sdesc(b_addr + (uint32_t)b * BBYTES + 256u * ks, KC * 128), id_s, ks > 0);
+        umma::commit(&mdone[b]);
       }
-      ok = __syncthreads_and(mbar_wait_bounded(&mma_bar, n_mma & 1));
-      ++n_mma;
-      if (!ok) break;
+      if (!ok) {
+        abort_flag = 1;
+        umma::commit(&dbar);
+        mbar_wait_bounded(&dbar, 0);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ================= worker warps
+    if (tid == 0)
+      for (; issued < min(RSD, nt); ++issued) issue(issued);
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    // chunk c's B operand (and, at a tile's first chunk, the tile's
+    // weights).  Every worker calls it for every chunk, aborted or not, so
+    // the named worker barriers always match.
+    auto make_b = [&](int c) {
+      const int r = c / CPT, q = c % CPT;
+      if (q == 0) {
+        if (!abort_flag && !wait(&bars[r % RSD], (r / RSD) & 1)) abort_flag = 1;
+        uhd::workers_sync();
+        if (!abort_flag) qbuf[(r & 1) * TS + tid] = raw[(r % RSD) * RAW + D * TS + tid];
+      }
+      if (!abort_flag) {
+      const float* rs = raw + (r % RSD) * RAW;
+      unsigned char* bdst = sB + (c & 1) * BBYTES;
+      const int jr = tid % NC, j = q * NC + jr;
+      // the TPS threads of a source take interleaved k-chunks of each term
+      float bb = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < D; ++k) {
+        const float v = p.s * (rs[k * TS + j] - ctr[k]);
+        bb = fmaf(-v, v, bb);
+      }
+      const bool far = bb < -30000.f;  // farther than any target can see: contributes 0
+      const float b_aug = far ? -30000.f : bb;
+      for (int g = tid / NC; g < LL::G; g += TPS) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float v2[2];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int k = 8 * g + 2 * e + h2;
+            v2[h2] = k < D ? (far ? 0.f : 2.f * p.s * (rs[k * TS + j] - ctr[k])) : (k == D ? b_aug : 0.f);
+          }
+          hw[e] = H::pack(v2[0], v2[1]);
+          const float2 hv = H::unpack(hw[e]);
+          lw[e] = H::pack(v2[0] - hv.x, v2[1] - hv.y);
+        }
+        const uint4 hv4 = make_uint4(hw[0], hw[1], hw[2], hw[3]), lv4 = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        *reinterpret_cast<uint4*>(bdst + umma::kmaj(jr, 8 * g, KC)) = hv4;
+        *reinterpret_cast<uint4*>(bdst + umma::kmaj(jr, 8 * (LL::G + g), KC)) = lv4;
+        *reinterpret_cast<uint4*>(bdst + umma::kmaj(jr, 8 * (2 * LL::G + g), KC)) = hv4;
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&bready[c & 1]);
+      }
+      if (q == CPT - 1) {  // the tile's stage is no longer read: refill it
+        uhd::workers_sync();
+        if (tid == 0 && r + RSD < nt && !abort_flag) {
+          fence_proxy_async_smem();
+          issue(r + RSD);
+          ++issued;
+        }
+      }
+    };
+    if (total > 0) make_b(0);
+    for (int c = 0; c < total; ++c) {
+      if (c + 1 < total) make_b(c + 1);
+      if (abort_flag) continue;  // keep passing the worker barriers
+      const int b = c & 1, r = c / CPT, q = c % CPT;
+      if (!__all_sync(0xffffffffu, wait(&mdone[b], (c >> 1) & 1))) {
+        abort_flag = 1;
+        continue;
+      }
       umma::fence_after();
-      // this row of S: 2^S_ij weighted by q_j over this half of the chunk
+      const float* qc0 = qbuf + (r & 1) * TS + q * NC;
 #pragma unroll 1
       for (int cb = half * (NC / 2); cb < (half + 1) * (NC / 2); cb += 32) {
         uint32_t v[32];
-        umma::ld32(tmem + lanes + (uint32_t)cb, v);
+        umma::ld32(tmem + lanes + (uint32_t)(b * NC + cb), v);
         umma::wait_ld();
-        const float* qc = qbuf + q * NC + cb;
+        const float* qc = qc0 + cb;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int e = 0; e < 32; e += 2)
@@ -1540,29 +1620,27 @@ __global__ void __launch_bounds__(uhd::THREADS) mvp_uhd_kernel(const TcParams p)
         kahan_add(S, C, acc.x + acc.y);
       }
       umma::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&sfree[b]);
     }
-    __syncthreads();  // the tile's epilogues are done with qbuf
+    if (abort_flag && lane == 0) atomicExch(p.err, DEV_TIMEOUT);
   }
-  if (!ok) {
-    // let every MMA issued complete before tensor memory is released, and
-    // drain the copies in flight
-    if (tid == 0) {
-      umma::commit(&dbar);
-      mbar_wait_bounded(&dbar, 0);
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0)
       for (int rr = 0; rr < issued; ++rr) mbar_wait_bounded(&bars[rr % RSD], (rr / RSD) & 1);
-      atomicExch(p.err, DEV_TIMEOUT);
-    }
+    __syncthreads();
   }
   // the two halves of each row
-  if (half == 1) red[row] = (double)S - (double)C;
+  if (!mma_warp && half == 1) red[row] = (double)S - (double)C;
   __syncthreads();
-  if (ok && half == 0 && i < p.Nt_pad)
+  if (!abort_flag && !mma_warp && half == 0 && i < p.Nt_pad)
     p.part[(int64_t)blockIdx.y * p.Nt_pad + i] = ((double)S - (double)C) + red[row];
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NC) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(LL::TMEM_COLS) : "memory");
 }
 
 // Weights Q (m columns, stride ld, sorted, zero padded) -> per source tile a
@@ -1661,7 +1739,7 @@ cudaError_t uhd_launch_typed(const TcParams& p, int splits, cudaStream_t st, boo
   }
   if (dry) return cudaSuccess;
   dim3 grid((unsigned)(2 * p.nblk), (unsigned)splits);
-  mvp_uhd_kernel<D><<<grid, uhd::THREADS, uhd::smem_bytes<D>(), st>>>(p);
+  mvp_uhd_kernel<D><<<grid, uhd::WORKERS + 32, uhd::smem_bytes<D>(), st>>>(p);
   count_launch();
   return cudaGetLastError();
 }
@@ -1807,10 +1885,10 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
     case 6: return tcx_launch_typed<6>(p, splits, st, dry);
     case 7: return tcx_launch_typed<7>(p, splits, st, dry);
     case 8: return tcx_launch_typed<8>(p, splits, st, dry);
-    case 16: return c.use_tcgen05 ? uhd_launch_typed<16>(p, splits, st, dry) : tch_launch_typed<16>(p, splits, st, dry);
-    case 32: return c.use_tcgen05 ? uhd_launch_typed<32>(p, splits, st, dry) : tch_launch_typed<32>(p, splits, st, dry);
-    case 48: return c.use_tcgen05 ? uhd_launch_typed<48>(p, splits, st, dry) : tch_launch_typed<48>(p, splits, st, dry);
-    case 64: return c.use_tcgen05 ? uhd_launch_typed<64>(p, splits, st, dry) : tch_launch_typed<64>(p, splits, st, dry);
+    case 16: return c.highd_tcgen05 ? uhd_launch_typed<16>(p, splits, st, dry) : tch_launch_typed<16>(p, splits, st, dry);
+    case 32: return c.highd_tcgen05 ? uhd_launch_typed<32>(p, splits, st, dry) : tch_launch_typed<32>(p, splits, st, dry);
+    case 48: return c.highd_tcgen05 ? uhd_launch_typed<48>(p, splits, st, dry) : tch_launch_typed<48>(p, splits, st, dry);
+    case 64: return c.highd_tcgen05 ? uhd_launch_typed<64>(p, splits, st, dry) : tch_launch_typed<64>(p, splits, st, dry);
     default: return cudaErrorNotSupported;
   }
 }

@@ -1,6 +1,7 @@
 """High-dimensional single-column products with the cross term on the tensor
 cores (d = 9..64, coordinates zero-padded to 16/32/48/64): compact target
-super-blocks take mvp_tch_kernel, the others the direct-form CUDA-core
+super-blocks take the tcgen05 kernel mvp_uhd_kernel (or, by handle option,
+the mma.sync kernel mvp_tch_kernel), the others the direct-form CUDA-core
 kernel.  Parity with the FP64 oracle at the float32 bar (1e-5 of the natural
 summation scale), the tensor-core path checked to have run, mixed clouds
 that exercise both kernels, a larger cloud on sampled rows, and a solve.
@@ -41,12 +42,13 @@ def _scaled_error(oracle_mod, X, q, y, sigma, gamma, rows=None):
     return float(np.max(np.abs(yy.astype(np.float64) - ref) / scale))
 
 
-def _product(K, X, q, sigma, gamma, tcgen05=False):
-    """y and the number of product launches that took the tensor-core path."""
+def _product(K, X, q, sigma, gamma, mma_sync=False):
+    """y and the number of product launches that took the tensor-core path
+    (the tcgen05 kernel by default, the mma.sync one on request)."""
     h = K.Handle()
     try:
-        if tcgen05:
-            K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h)
+        if mma_sync:
+            K.krr_set_option(K.KRR_OPT_HIGHD_TCGEN05, 0, handle=h)
         K.krr_profile_enable(True, handle=h)
         y = K.krr_kernel_mvp(_dev(X), _dev(q), sigma, gamma, handle=h).cpu().numpy()
         prof = K.krr_profile_read(handle=h)
@@ -130,29 +132,29 @@ def test_highd_solve_on_tensor_path(K, oracle_mod):
 
 
 @pytest.mark.parametrize("N,d", [(5000, 16), (777, 20), (3001, 32), (2600, 48), (4097, 64)])
-def test_highd_tcgen05_kernel_parity(K, oracle_mod, N, d):
-    # the same contraction on tcgen05 / tensor memory (handle option)
+def test_highd_mma_sync_kernel_parity(K, oracle_mod, N, d):
+    # the same contraction with mma.sync (handle option)
     rng = np.random.default_rng(700 + d)
     X = rng.random((N, d)).astype(np.float32)
     q = rng.standard_normal(N).astype(np.float32)
     sigma, gamma = 0.3 * np.sqrt(d), 1e-2
-    y, tensor_launches = _product(K, X, q, sigma, gamma, tcgen05=True)
+    y, tensor_launches = _product(K, X, q, sigma, gamma, mma_sync=True)
     assert tensor_launches == 1
     assert _scaled_error(oracle_mod, X, q, y, sigma, gamma) <= TOL_FP32
 
 
-def test_highd_tcgen05_mixed_and_larger(K, oracle_mod):
+def test_highd_mma_sync_mixed_and_larger(K, oracle_mod):
     rng = np.random.default_rng(701)
     d = 40
     X = np.concatenate([rng.random((3000, d)), 3.0 + 12.0 * rng.random((1500, d))]).astype(np.float32)
     q = rng.standard_normal(4500).astype(np.float32)
     sigma = 0.35 * np.sqrt(d)
-    y, tl = _product(K, X, q, sigma, 1e-3, tcgen05=True)
+    y, tl = _product(K, X, q, sigma, 1e-3, mma_sync=True)
     assert tl == 1 and _scaled_error(oracle_mod, X, q, y, sigma, 1e-3) <= TOL_FP32
     N, d = 65536, 64
     X = rng.random((N, d)).astype(np.float32)
     q = rng.standard_normal(N).astype(np.float32)
     sigma = 0.3 * np.sqrt(d)
-    y, tl = _product(K, X, q, sigma, 1e-3, tcgen05=True)
+    y, tl = _product(K, X, q, sigma, 1e-3, mma_sync=True)
     rows = inputs.sample_rows(N, 256, seed=702)
     assert tl == 1 and _scaled_error(oracle_mod, X, q, y, sigma, 1e-3, rows=rows) <= TOL_FP32
