@@ -38,9 +38,9 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "7929ff54debf9b5286ac1632d89154af72a7df60",
-                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "1ea52efd48eed195348b75518e71a1d329f13585"},
-               "bytes": 22316544 + 91850240 + 17240320 + 0}
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "af3421004812d11340dfbd8dc8ff17ecb360f609",
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "21dd9842446f1f65ed4f9177077618fff2bd7c05"},
+               "bytes": 22775808 + 92288000 + 17172736 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 
@@ -62,6 +62,8 @@ def parse_args(argv=None):
                     help="points of the log-marginal-likelihood gradient (0 skips it)")
     ap.add_argument("--no-matern", dest="matern", action="store_false",
                     help="skip the Matern-kernel product and solves")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the autotuned-plan comparison")
     ap.add_argument("--no-highd", dest="highd", action="store_false",
                     help="skip the high-dimensional product comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -324,7 +326,8 @@ def run_libkrr(args):
     matern = None
     if args.matern:
         matern = matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
-    tuned = autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream, kern_ms, m16_ms)
+    tuned = (autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream, kern_ms, m16_ms)
+             if args.autotune else None)
     highd = highd_form(K, torch, rank, dev) if args.highd else None
 
     # ---- FP64 oracle on the host cores (rank 0, one GPU only)
