@@ -97,3 +97,20 @@ def test_mll_grad_high_dimension(K, oracle_mod):
     gX = gX.cpu().numpy()
     assert gX.shape == (N, d)
     assert np.max(np.abs(gX - oX)) <= 1e-4 * np.max(np.abs(oX))
+
+
+def test_mll_grad_full_size_identities(K):
+    # the gradient workload at its full size (65,536 points in [0,1]^4; fewer
+    # probes to keep it short): every solve converges, and the two invariance
+    # identities pinned on the oracle (test_oracle_mll.py) hold for the GPU's
+    # gradients -- sum_i dL/dx_i = 0 and sum_i x_i . dL/dx_i = -dL/dlog(sigma),
+    # tying the adjoint kernel's dX to the separately formed dlog(sigma)
+    p = inputs.gradient_problem(seed=6, N=65536, d=4, probes=4)
+    gs, gg, gX, infos = K.krr_mll_grad(_dev(p["X"]), _dev(p["y"]), p["sigma"], p["gamma"],
+                                       n_probes=4, seed=p["seed"])
+    assert all(i["status"] == K.KRR_OK and i["relres_true"] <= 1e-6 for i in infos), infos
+    X = p["X"].astype(np.float64)
+    dX = gX.cpu().numpy().astype(np.float64)
+    assert np.isfinite(dX).all() and np.isfinite(gs) and np.isfinite(gg)
+    assert np.abs(dX.sum(0)).max() <= 1e-4 * np.abs(dX).sum()
+    assert abs((X * dX).sum() + gs) <= 1e-4 * np.abs(X * dX).sum()

@@ -118,3 +118,23 @@ def test_rademacher_probes_shape_and_balance(oracle_mod):
     # column p of an N-row draw is the same stream slice as in any other draw
     Z2 = oracle_mod.rademacher_probes(3, 1000, 3)
     np.testing.assert_array_equal(Z[:, :3], Z2)
+
+
+def test_gradient_invariance_identities(oracle_mod):
+    # The likelihood is unchanged by translating X, and by scaling X and sigma
+    # together (the kernel depends on (x_i - x_j) / sigma).  Hence, for the
+    # exact gradient and for any estimate built from one symmetric weight
+    # matrix W (the Hutchinson one included):
+    #   sum_i dL/dx_i = 0,    sum_i x_i . dL/dx_i + dL/dlog(sigma) = 0.
+    # A dropped term, a wrong sign or a wrong 1/sigma^2 in either gradient
+    # breaks them.
+    from paper_1408_1237_gb300 import inputs
+    p = inputs.gradient_problem(seed=3, N=300, d=2, probes=4)
+    X, y = p["X"].astype(np.float64), p["y"].astype(np.float64)
+    s, g = 0.2, 1e-2
+    Zp = oracle_mod.rademacher_probes(p["seed"], 300, 4)
+    for ds, dg, dX in (oracle_mod.mll_grad_exact(X, y, s, g)[:3],
+                       oracle_mod.mll_grad_hutchinson(X, y, s, g, Zp)[:3]):
+        scale = np.abs(X * dX).sum()
+        assert np.abs(dX.sum(0)).max() <= 1e-12 * np.abs(dX).sum()
+        assert abs((X * dX).sum() + ds) <= 1e-12 * scale
