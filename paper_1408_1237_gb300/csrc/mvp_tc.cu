@@ -1395,10 +1395,6 @@ constexpr size_t smem_bytes() {
   return (size_t)(ROWS + 2 * LL::NC) * LL::KV * 2 + sizeof(float) * ((size_t)LL::RSD * (D + 1) * TS + 2 * TS);
 }
 static_assert(smem_bytes<64>() <= 225 * 1024 && smem_bytes<48>() <= 225 * 1024, "shared memory");
-// one f16 value into a K-major no-swizzle operand (row, slot k)
-__device__ __forceinline__ void put(unsigned char* base, int row, int k, int kc, __half v) {
-  *reinterpret_cast<__half*>(base + umma::kmaj(row, k, kc)) = v;
-}
 __device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(WORKERS) : "memory"); }
 }  // namespace uhd
 
