@@ -159,17 +159,38 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- reference ---
-def cpu_oracle_rate(X, q, sigma, gamma, rows):
-    """Oracle FP64 product on a row sample: returns (Gpairs/s, seconds, threads)."""
+def cpu_oracle_rate(X, q, sigma, gamma, rows, with_values=False):
+    """Oracle FP64 product on a row sample: returns (Gpairs/s, seconds,
+    threads) and, with_values, the sampled rows' values."""
     import numpy as np
     import oracle
     oracle.build_oracle()
     X64 = X.astype(np.float64)
     q64 = q.astype(np.float64)
     t0 = time.perf_counter()
-    oracle.mvp(X64, q64, sigma, gamma, rows=rows)
+    y = oracle.mvp(X64, q64, sigma, gamma, rows=rows)
     dt = time.perf_counter() - t0
-    return len(rows) * X.shape[0] / dt / 1e9, dt, oracle.num_threads()
+    out = (len(rows) * X.shape[0] / dt / 1e9, dt, oracle.num_threads())
+    return out + (y,) if with_values else out
+
+
+def precision_errors(K, X, q, y32, sigma, gamma, p, rows, ref):
+    """Max error per element of the float32, f16 and bf16 products (the
+    last two: the inner-product precisions of the solver) against the FP64
+    oracle on sampled rows, each scaled by the row's summation scale
+    sum_j |q_j| K_hat_ij + gamma |q_i| (the oracle on the rows' |q|)."""
+    import numpy as np
+    import oracle
+    f32 = lambda v: float(np.float32(v))
+    scale = oracle.mvp(p["X"].astype(np.float64), np.abs(p["Q"].astype(np.float64)), f32(sigma), f32(gamma),
+                       rows=rows)
+    out = {"rows": int(len(rows)), "reference": "FP64 oracle (C, OpenMP) over all 2^20 sources"}
+    for name, prec in (("fp32", None), ("fp16", "fp16"), ("bf16", "bf16")):
+        y = y32 if prec is None else K.krr_kernel_mvp(X, q, sigma, gamma, prec=prec)
+        yy = y.cpu().numpy().astype(np.float64)[rows]
+        out[name] = float(np.max(np.abs(yy - ref) / scale))
+    out["fp32_bar"] = 1e-5
+    return out
 
 
 def run_reference(args):
@@ -332,12 +353,16 @@ def run_libkrr(args):
 
     # ---- FP64 oracle on the host cores (rank 0, one GPU only)
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nrows = 32768  # about 10 s of the oracle on 16 cores
         rows = inputs.sample_rows(MVP_N, nrows, seed=11)
-        rate, dt, cores = cpu_oracle_rate(p["X"], p["Q"], sigma, gamma, rows)
+        rate, dt, cores, ref = cpu_oracle_rate(p["X"], p["Q"], sigma, gamma, rows, with_values=True)
         cpu = {"value": rate, "unit": "Gpairs/s", "cores": cores, "kind": "oracle",
                "sample": f"{nrows} seeded target rows x {MVP_N} sources ({dt:.1f} s)"}
+        # the products' error against these oracle sums (every 8th sampled row)
+        sub = np.arange(0, nrows, 8)
+        errors = precision_errors(K, X, q, y, sigma, gamma, p, rows[sub], ref[sub])
 
     if rank == 0:
         line = {
@@ -374,6 +399,7 @@ def run_libkrr(args):
             "autotune": tuned,
             "highd": highd,
             "cpu_baseline": cpu,
+            "precision_errors": errors,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
