@@ -193,6 +193,17 @@ def precision_errors(K, X, q, y32, sigma, gamma, p, rows, ref):
     return out
 
 
+def bench_config(world):
+    """The workload both arms report (`config`)."""
+    return {
+        "workload": f"gaussian kernel product y=(K_hat+gamma I)q, N={MVP_N} uniform "
+                    "unit cube d=3, sigma=0.05, gamma=1e-3, q~N(0,1), m=1; step = "
+                    "prep (Morton sort, pack) + product + finalize through the C ABI",
+        "l2": "512 MB buffer written between timed steps (inputs are 16 MB)",
+        "parallelism": f"{world} independent problems (one per GPU)",
+    }
+
+
 def run_reference(args):
     # host-only: rank 0 times the oracle, the other ranks exit without work
     # (no process group is needed)
@@ -211,14 +222,14 @@ def run_reference(args):
         times.append(dt)
     pairs = rows_per_step * MVP_N
     value = pairs * len(times) / sum(times) / 1e9
-    sample = f"{rows_per_step} seeded target rows x {MVP_N} sources per step"
+    sample = (f"{rows_per_step} seeded target rows x {MVP_N} sources per step (the FP64 oracle "
+              "on the host cores; the rate is per evaluated pair, as on the GPU)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpairs/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"gaussian kernel product, N={MVP_N} uniform unit cube d=3, "
-                               "sigma=0.05, gamma=1e-3, q~N(0,1), m=1 (FP64 oracle, row sample)"},
+        "config": bench_config(int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "Gpairs/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "Gpairs/s", "h2d_bytes_per_step": 0,
@@ -370,13 +381,7 @@ def run_libkrr(args):
             "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {
-                "workload": f"gaussian kernel product y=(K_hat+gamma I)q, N={MVP_N} uniform "
-                            "unit cube d=3, sigma=0.05, gamma=1e-3, q~N(0,1), m=1; step = "
-                            "prep (Morton sort, pack) + product + finalize through the C ABI",
-                "l2": "512 MB buffer written between timed steps (inputs are 16 MB)",
-                "parallelism": f"{world} independent problems (one per GPU)",
-            },
+            "config": bench_config(world),
             "roofline": {
                 "bound": "alu", "achieved": achieved, "peak": peak_pairs / 1e9,
                 "unit": "Gpairs/s", "frac": achieved * 1e9 / peak_pairs,
