@@ -1,6 +1,6 @@
 """GPU parity of the FGMRES solver (Alg. 1 with the Sec. 5 preconditioner).
 
-Every solution is judged by the FP64 oracle: its relative residual
+Every solution is checked by the FP64 oracle: its relative residual
 |b - K x| / |b| recomputed in FP64 (dense K at small N, the on-the-fly oracle
 product at larger N) must meet the 1e-6 tolerance, the library's own
 reported true residual must agree with the oracle's, and at small N x must

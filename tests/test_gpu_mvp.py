@@ -2,7 +2,7 @@
 
 Error measure (the FP32 bar is 1e-5): per element, |y_i - y*_i| divided by the
 natural summation scale sum_j |q_j| K_hat_ij + gamma |q_i| (so rows whose
-signed sum nearly cancels are judged against the size of what was summed).
+signed sum nearly cancels are measured against the size of what was summed).
 Small cases compare every element; the full-size 2^20-point cloud compares a
 seeded sample of rows, each summed by the oracle over all 2^20 sources.
 """
