@@ -174,6 +174,35 @@ def cpu_oracle_rate(X, q, sigma, gamma, rows, with_values=False):
     return out + (y,) if with_values else out
 
 
+def cpu_oracle_solves(p):
+    """The FP64 oracle's own solves of the 2000-point problem, timed on the
+    host cores beside the GPU's: dense K, the Cholesky direct solve, and the
+    paper's FGMRES with truncated-CG inner solves (same restart, delta and
+    tolerances as the GPU run), both on dense NumPy products."""
+    import numpy as np
+    import oracle
+    f32 = lambda v: float(np.float32(v))
+    X, b = p["X"].astype(np.float64), p["b"].astype(np.float64)
+    sigma, gamma, delta = f32(p["sigma"]), f32(p["gamma"]), f32(p["delta"])
+    t0 = time.perf_counter()
+    Kmat = oracle.regularised_matrix(X, sigma, gamma)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x_direct = oracle.direct_solve(Kmat, b)
+    t_direct = time.perf_counter() - t0
+    Mmat = Kmat + delta * np.eye(len(b))
+    t0 = time.perf_counter()
+    res = oracle.krr_fgmres(lambda v: Kmat @ v, lambda v: Mmat @ v, b, restart=p["restart"],
+                            tol=p["tol"], inner_tol=p["inner_tol"])
+    t_fgmres = time.perf_counter() - t0
+    rel = lambda x: float(np.linalg.norm(b - Kmat @ x) / np.linalg.norm(b))
+    return {"N": int(len(b)), "dense_K_ms": t_build * 1e3,
+            "cholesky_ms": t_direct * 1e3, "cholesky_relres": rel(x_direct),
+            "fgmres_ms": t_fgmres * 1e3, "fgmres_relres": rel(res.x),
+            "fgmres_outer": int(res.outer_iters), "fgmres_inner": int(res.inner_iters),
+            "threads": "NumPy/SciPy BLAS defaults"}
+
+
 def precision_errors(K, X, q, y32, sigma, gamma, p, rows, ref):
     """Max error per element of the float32, f16 and bf16 products (the
     last two: the inner-product precisions of the solver) against the FP64
@@ -374,6 +403,7 @@ def run_libkrr(args):
         # the products' error against these oracle sums (every 8th sampled row)
         sub = np.arange(0, nrows, 8)
         errors = precision_errors(K, X, q, y, sigma, gamma, p, rows[sub], ref[sub])
+        cpu["solves_2000pt_2d"] = cpu_oracle_solves(inputs.small_problem(seed=0))
 
     if rank == 0:
         line = {
