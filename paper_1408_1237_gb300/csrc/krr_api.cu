@@ -232,6 +232,10 @@ krr_status krr_create(krr_handle* out) {
     cudaGetLastError();
     if (c.d_err) cudaFree(c.d_err);
     if (c.h_status) cudaFreeHost(c.h_status);
+    for (cudaEvent_t ev : {c.ev0, c.ev1, c.ev_in, c.ev_out})
+      if (ev) cudaEventDestroy(ev);
+    if (c.work) cudaStreamDestroy(c.work);
+    cudaGetLastError();
     delete h;
     return e == cudaErrorMemoryAllocation ? KRR_ERR_OOM : KRR_ERR_CUDA;
   }
