@@ -40,9 +40,11 @@
  *             sigma > 0; shifts (gamma, delta) >= 0; all finite.
  * Dimension:  up to 8 the kernels are specialised per d and compact target
  *             blocks use the expanded exponent form (tensor cores where it
- *             pays); above 8 the coordinates are held padded with zeros to 16,
- *             32, 48 or 64 and every pair takes the direct form (exact
- *             differences on the CUDA cores).
+ *             pays).  Above 8 the coordinates are held padded with zeros to
+ *             16, 32, 48 or 64; single-column float32 products contract the
+ *             cross term of compact blocks on the tensor cores, and every
+ *             other pair takes the direct form (exact differences on the CUDA
+ *             cores).
  */
 #ifndef LIBKRR_H
 #define LIBKRR_H
@@ -163,8 +165,8 @@ typedef enum {
     /* value != 0 (default): single-column products above 8 dimensions
      * contract their compact super-blocks with tcgen05.mma into tensor
      * memory; 0: with mma.sync.  Same results to the float32 bar; on GB300
-     * the default is faster (measured at N = 65536: d = 16 2696 vs 2505,
-     * d = 32 1439 vs 1188, d = 64 741 vs 657 Gpairs/s). */
+     * the default is faster (measured at N = 65536: d = 16 2685 vs 2500,
+     * d = 32 1434 vs 1185, d = 64 739 vs 655 Gpairs/s). */
     KRR_OPT_HIGHD_TCGEN05 = 6
 } krr_option;
 
@@ -188,8 +190,10 @@ krr_status krr_set_option(krr_handle h, int option, int value);
  *     Y[i,c] = sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) Q[j,c] + gamma Q[i,c]
  * over all N^2 pairs (no cut-off), summed on the fly in O(N) memory.
  * X: N x d; Q, Y: N x m column-major, 1 <= m <= 64.  Y must not alias X or Q.
- * m = 1 runs the float32 CUDA-core product; m >= 2 evaluates each kernel
- * value once for up to 16 columns (tensor cores for compact target blocks).
+ * m = 1 takes one exponential per pair, with the exponent contraction on the
+ * tensor cores for compact target blocks and the CUDA-core kernel for the
+ * rest; m >= 2 evaluates each kernel value once for up to 16 columns
+ * (tensor cores for compact target blocks).
  * prec: KRR_FP32 (max relative error per element, against the FP64 sum
  * scaled by sum_j |Q_jc| K_hat_ij + gamma |Q_ic|, below 1e-5) or KRR_BF16 /
  * KRR_FP16 (reduced-precision kernel values, float32 accumulation).
