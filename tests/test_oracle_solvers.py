@@ -2,8 +2,12 @@
 
 Fixed by mathematics: hand-solved 2x2 systems, manufactured solutions, finite
 termination of CG and GMRES in exact-enough arithmetic, the flexible Arnoldi
-relation, orthonormality, the CG error bound quoted in Sec. 3 and the
-one-step convergence of FGMRES when the inner solve is exact with delta = 0.
+relation, orthonormality, the CG error bound quoted in Sec. 3, the
+one-step convergence of FGMRES when the inner solve is exact with delta = 0,
+and the optimality that defines each method, checked by brute force against
+bases built with library QR: GMRES minimises the residual over the Krylov
+space, flexible GMRES over the span of the inner solves' vectors, and CG's
+iterates are the Galerkin solutions.
 """
 import math
 
@@ -113,6 +117,68 @@ def test_estimate_equals_true_residual(oracle_mod):
         res = oracle_mod.fgmres(lambda v: K @ v, b, restart=steps, tol=1e-14, max_cycles=1)
         true = np.linalg.norm(b - K @ res.x) / np.linalg.norm(b)
         assert res.history[-1] == pytest.approx(true, rel=1e-8)
+
+
+def _krylov_basis(A, v, k):
+    """Orthonormal basis of span{v, A v, ..., A^(k-1) v}, grown by one library
+    (Householder) QR per step, independently of the oracle's Gram-Schmidt."""
+    Q = (v / np.linalg.norm(v))[:, None]
+    for _ in range(k - 1):
+        Q, _ = np.linalg.qr(np.column_stack([Q, A @ Q[:, -1]]))
+    return Q
+
+
+def test_gmres_minimises_the_residual_over_the_krylov_space(oracle_mod):
+    # Alg. 1 with M = I: after k steps the residual is the minimum of
+    # |b - K x| over x in the Krylov space K_k(K, b) (x0 = 0).
+    X = inputs.uniform_points(60, 2, seed=36).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.15, 1e-2)
+    b = np.random.default_rng(37).standard_normal(60)
+    m = 15
+    res = oracle_mod.fgmres(lambda v: K @ v, b, restart=m, tol=1e-15, max_cycles=1)
+    assert len(res.history) == m
+    Q = _krylov_basis(K, b, m)
+    for k in range(1, m + 1):
+        y = np.linalg.lstsq(K @ Q[:, :k], b, rcond=None)[0]
+        best = np.linalg.norm(b - K @ Q[:, :k] @ y) / np.linalg.norm(b)
+        assert res.history[k - 1] == pytest.approx(best, rel=1e-7, abs=1e-12)
+
+
+def test_cg_iterates_are_galerkin_solutions(oracle_mod):
+    # Step k of CG is the x in K_k(A, b) whose residual is orthogonal to
+    # K_k(A, b), i.e. the minimiser of the A-norm error there (Sec. 3).
+    X = inputs.uniform_points(60, 2, seed=38).astype(np.float64)
+    A = oracle_mod.regularised_matrix(X, 0.15, 5e-2)
+    b = np.random.default_rng(39).standard_normal(60)
+    Q = _krylov_basis(A, b, 12)
+    for k in range(1, 13):
+        xk, it = oracle_mod.cg(lambda v: A @ v, b, tol=0.0, maxit=k)
+        assert it == k
+        Qk = Q[:, :k]
+        xg = Qk @ np.linalg.solve(Qk.T @ A @ Qk, Qk.T @ b)
+        np.testing.assert_allclose(xk, xg, rtol=0, atol=1e-8 * np.linalg.norm(xg))
+
+
+def test_fgmres_minimises_the_residual_over_the_span_of_z(oracle_mod):
+    # With a preconditioner that changes from step to step (a truncated inner
+    # CG), the flexible iterate after k steps minimises |b - K x| over x in
+    # span(z_1, ..., z_k), the vectors the inner solves returned.
+    X = inputs.uniform_points(80, 2, seed=40).astype(np.float64)
+    K = oracle_mod.regularised_matrix(X, 0.15, 1e-2)
+    M = K + 0.1 * np.eye(80)
+    b = np.random.default_rng(41).standard_normal(80)
+    inner = lambda v: oracle_mod.cg(lambda u: M @ u, v, 1e-1, 100)
+    res = oracle_mod.fgmres(lambda v: K @ v, b, restart=10, tol=1e-15, max_cycles=1,
+                            inner=inner)
+    Z = res.last_cycle[1]
+    assert Z.shape[0] == 10
+    for k in range(1, 11):
+        Zk, _ = np.linalg.qr(Z[:k].T)
+        y = np.linalg.lstsq(K @ Zk, b, rcond=None)[0]
+        best = np.linalg.norm(b - K @ Zk @ y) / np.linalg.norm(b)
+        assert res.history[k - 1] == pytest.approx(best, rel=1e-7, abs=1e-12)
+    true = np.linalg.norm(b - K @ res.x) / np.linalg.norm(b)
+    assert true == pytest.approx(res.history[-1], rel=1e-7, abs=1e-12)
 
 
 def test_preconditioned_spectrum_bound(oracle_mod):
