@@ -258,6 +258,24 @@ def test_fcg_exact_preconditioner_one_step(oracle_mod):
     np.testing.assert_allclose(r.x, np.linalg.solve(A, b), rtol=1e-10)
 
 
+def test_fcg_fixed_preconditioner_iterates_are_galerkin_solutions(oracle_mod):
+    # A fixed SPD preconditioner B and a window longer than the run make
+    # flexible CG preconditioned CG: step k minimises the A-norm error over
+    # the Krylov space K_k(B^-1 A, B^-1 b), whose Galerkin solution is
+    # Q (Q^T A Q)^-1 Q^T b for any basis Q of it.
+    A = _spd(40, 5, cond=1e2)
+    P = A + 0.3 * np.diag(np.linspace(1.0, 3.0, 40))
+    b = np.random.default_rng(6).standard_normal(40)
+    Q = _krylov_basis(np.linalg.solve(P, A), np.linalg.solve(P, b), 10)
+    for k in range(1, 11):
+        r = oracle_mod.fcg(lambda v: A @ v, b, 0.0, k, mmax=50,
+                           inner=lambda v: (np.linalg.solve(P, v), 1))
+        assert r.iters == k
+        Qk = Q[:, :k]
+        xg = Qk @ np.linalg.solve(Qk.T @ A @ Qk, Qk.T @ b)
+        np.testing.assert_allclose(r.x, xg, rtol=0, atol=1e-8 * np.linalg.norm(xg))
+
+
 def test_fcg_directions_are_conjugate_with_varying_preconditioner(oracle_mod):
     # a preconditioner that changes every step (truncated inner CG) still
     # yields A-conjugate directions within the window, by construction
