@@ -71,3 +71,52 @@ def test_product_path_has_no_oracle_dependency():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "krr_oracle" not in text, path
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "libkrr.h"
+
+int main(void) {
+    krr_fgmres_opts o;
+    krr_fgmres_default_opts(&o);
+    if (o.restart != 30 || o.tol != 1e-6 || o.inner_maxit != 100) return 2;
+    if (strcmp(krr_status_string(KRR_NOT_CONVERGED), "KRR_NOT_CONVERGED") != 0) return 3;
+    if (krr_version() < 100) return 4;
+    if (krr_create(NULL) != KRR_ERR_INVALID_ARG) return 5;
+    krr_handle h = NULL;
+    krr_status s = krr_create(&h);          /* KRR_ERR_CUDA where no GPU is visible */
+    if (s == KRR_OK) {
+        if (krr_set_option(h, 999, 1) != KRR_ERR_INVALID_ARG) return 6;
+        if (krr_destroy(h) != KRR_OK) return 7;
+    } else if (s != KRR_ERR_CUDA || h != NULL) {
+        return 8;
+    }
+    if (krr_kernel_mvp(NULL, NULL, 1, 3, 1.f, 0.f, NULL, 1, NULL, KRR_FP32, NULL)
+        != KRR_ERR_INVALID_ARG) return 9;
+    printf("ok %d\n", (int)s);
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(clib, tmp_path):
+    # The boundary is a C ABI: the header compiles as C99 with warnings as
+    # errors, and a C program links against libkrr.so and runs its host-only
+    # calls (no device work).
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.join(ROOT, "paper_1408_1237_gb300")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lkrr", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.startswith("ok")
