@@ -120,3 +120,20 @@ def test_header_is_plain_c_and_links(clib, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
     assert out.stdout.startswith("ok")
+
+
+def test_binding_constants_match_header():
+    # Every enumerator of include/libkrr.h that the binding repeats has the
+    # header's value (status codes, options, kernel families, precisions).
+    from paper_1408_1237_gb300 import binding
+    text = open(os.path.join(ROOT, "include", "libkrr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(KRR_\w+)\s*=\s*(\d+)", text)}
+    assert len(enums) >= 20
+    repeated = [n for n in enums if hasattr(binding, n)]
+    assert len(repeated) >= 18
+    for name in repeated:
+        assert getattr(binding, name) == enums[name], name
+    prec = {"fp32": "KRR_FP32", "bf16": "KRR_BF16", "fp16": "KRR_FP16"}
+    for key, name in prec.items():
+        assert binding.PRECISION[key] == enums[name]
