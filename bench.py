@@ -39,7 +39,7 @@ TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
 TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "af3421004812d11340dfbd8dc8ff17ecb360f609",
-                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "da16e1dbd27f6918d165583ecdab57e884a35713"},
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "cc922b230208a1c66336969f0d0101d458166d4c"},
                "bytes": 22775808 + 92288000 + 17172736 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 

@@ -1402,7 +1402,7 @@ template <int D>
 __global__ void __launch_bounds__(uhd::WORKERS + 32) mvp_uhd_kernel(const TcParams p) {
   using LL = uhd::L<D>;
   using H = Half<false>;
-  constexpr int W = LL::W, KS = LL::KSTEPS, KC = LL::KC, RSD = LL::RSD;
+  constexpr int KS = LL::KSTEPS, KC = LL::KC, RSD = LL::RSD;
   constexpr int ROWS = uhd::ROWS, NC = LL::NC, NW8 = uhd::WORKERS;
   constexpr int TPS = NW8 / NC;  // worker threads per source of a chunk
   constexpr int RAW = (D + 1) * TS;  // coordinates, weights
