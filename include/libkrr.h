@@ -92,6 +92,13 @@ typedef struct {
     int use_graph;        /* 1: run the whole solve as one CUDA graph with
                              device-side loop control; 0: host-driven loop
                              with one status read per step               [1]    */
+    int x0_given;         /* 1: the solution array holds an initial guess x0
+                             on entry and the solve starts from it: the first
+                             cycle takes r0 = b - K x0 from the accurate
+                             product, as every restart of Alg. 1 (x0 <- x_m)
+                             does, so a capped solve resumes where it
+                             stopped; 0: x0 = 0 and the array is output only
+                                                                          [0]    */
 } krr_fgmres_opts;
 
 /* Per-right-hand-side solver report. */
@@ -111,7 +118,8 @@ typedef struct {
 typedef struct {
     const float* X;   /* N x d row-major                                       */
     const float* B;   /* N x m_rhs column-major right-hand sides               */
-    double* Xsol;     /* N x m_rhs column-major FP64 solutions (in: ignored)   */
+    double* Xsol;     /* N x m_rhs column-major FP64 solutions (in: the initial
+                         guess when opts->x0_given, else ignored)            */
     int64_t N;
     float gamma;
 } krr_problem;
@@ -228,7 +236,8 @@ krr_status krr_cg_solve(krr_handle h, const float* X, int64_t N, int d,
 
 /* ----------------------------------------------------------- FGMRES solve
  * Algorithm 1 on K = K_hat + gamma I with the paper's preconditioner:
- * truncated CG on M = K + delta I (Sec. 5), restart m, x0 = 0.  Arnoldi
+ * truncated CG on M = K + delta I (Sec. 5), restart m, x0 = 0 (or the
+ * initial guess in Xsol when opts->x0_given).  Arnoldi
  * (classical Gram-Schmidt applied twice, equal to the modified Gram-Schmidt
  * of Alg. 1 to working precision) and the Givens least-squares update run in
  * FP64; the outer products K z_j and the true residual in float32 with
@@ -310,6 +319,30 @@ krr_status krr_measure_alu_peaks(krr_handle h, double* ex2_per_s, double* ffma_p
  * way (a few ms of GPU time; waits).  rsqrt_per_s: HOST double, not NULL. */
 krr_status krr_measure_rsqrt_rate(krr_handle h, double* rsqrt_per_s, void* stream);
 
+/* Rates behind the reduced-precision design, measured the same way (a few
+ * ms of GPU time; waits): exponential VALUES per second through the packed
+ * half-precision instructions ex2.approx.f16x2 and ex2.approx.ftz.bf16x2 (two
+ * values per instruction; on GB300 they give the same values per second as
+ * ex2.approx.ftz.f32, so half-precision kernel values do not raise the
+ * exponential bound), and dense f16 FLOP/s of the warp-level tensor-core MMA
+ * mma.sync m16n8k16 with f32 accumulation.  Outputs: HOST doubles; any may
+ * be NULL. */
+krr_status krr_measure_half_rates(krr_handle h, double* ex2_f16x2_values_per_s,
+                                  double* ex2_bf16x2_values_per_s,
+                                  double* mma_sync_f16_flops_per_s, void* stream);
+
+/* Failure-path self-test (not part of the method: failure detection checked
+ * without a GPU fault).  Every device wait of the library is
+ * bounded: a kernel whose wait runs out records it in the handle's error word,
+ * drains what it has in flight and returns, and the call reports
+ * KRR_ERR_TIMEOUT.  This entry point runs a one-thread kernel that waits, with
+ * that same bounded routine, on an mbarrier phase nothing completes (no copy,
+ * MMA or other warp is outstanding on it), giving up after limit_clocks SM
+ * clocks (1 to 2e9; a few thousand take microseconds).  It waits for `stream`
+ * and returns KRR_ERR_TIMEOUT, after which the handle stays usable: the error
+ * word is cleared and later calls run normally. */
+krr_status krr_selftest_wait_timeout(krr_handle h, long long limit_clocks, void* stream);
+
 /* Launch and timing counters for measurement (not part of the method). */
 typedef struct {
     long long launches;     /* kernels the library launched since it was loaded
@@ -334,22 +367,27 @@ krr_status krr_profile_read(krr_handle h, krr_profile* out);
 
 /* ------------------------------------------------ no-allocation product
  * The paper has no counterpart to this entry point.  It serves callers that
- * cannot allocate device memory: code running inside host callbacks or
- * allocator hooks, processes whose device memory pool belongs to another
- * framework, and latency-bound paths where cudaMalloc's implicit device
+ * cannot allocate device memory: processes whose device memory pool belongs
+ * to another framework (which forbids or is fragmented by foreign cudaMalloc
+ * calls), and latency-bound paths where cudaMalloc's implicit device
  * synchronisation is not allowed.  Such callers cannot create a krr_handle
  * either, since a handle grows its workspace with cudaMalloc.
  * Result: that of krr_kernel_mvp with KRR_FP32, for DEVICE arrays X (N x d
  * row-major), Q and Y (N x m column-major) with N <= 16384, d <= 8 and
  * m <= 16.  Larger problems return KRR_ERR_SIZE_LIMIT; host arrays and bad
  * values return KRR_ERR_INVALID_ARG.
- * It allocates nothing.  Its scratch is one fixed device array of 10,415,616
- * bytes, held by every GPU that loads the library until the process exits.
- * The first call made with a device current looks up that array's device
- * address (cudaGetSymbolAddress), so make it before any stream capture.  All
- * calls on a device share the array and it keeps the last call's contents;
- * calls that overlap on the GPU race on it and give wrong results.
- * Asynchronous on `stream`. */
+ * It allocates nothing.  Its scratch is one fixed device array of 10,415,872
+ * bytes, held by every GPU that loads the library until the process exits;
+ * an internal request beyond a region of it returns KRR_ERR_OOM instead of
+ * allocating.  The first call made with a device current looks up that
+ * array's device address (cudaGetSymbolAddress).  All calls on a device
+ * share the array and it keeps the last call's contents; calls that overlap
+ * on the GPU race on it and give wrong results.
+ * The call waits for `stream`: the point preparation reads two block counts
+ * back to the host before the product is queued.  So it returns
+ * KRR_ERR_INVALID_ARG while `stream` is being captured into a CUDA graph,
+ * and it must not be called from a host function enqueued on a stream
+ * (CUDA forbids CUDA calls there). */
 krr_status krr_kernel_mvp_noalloc(const float* X, int64_t N, int d, float sigma,
                                   float gamma, const float* Q, int m, float* Y,
                                   void* stream);

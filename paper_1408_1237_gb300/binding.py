@@ -35,7 +35,8 @@ class krr_fgmres_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
-                ("inner_prec", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("inner_prec", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("x0_given", ctypes.c_int)]
 
 
 class krr_solve_info(ctypes.Structure):
@@ -86,10 +87,12 @@ _SIGNATURES = {
     "krr_measure_alu_peaks": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
                                _vp], _int),
     "krr_measure_rsqrt_rate": ([_vp, ctypes.POINTER(_d), _vp], _int),
+    "krr_measure_half_rates": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), _vp], _int),
     "krr_profile_enable": ([_vp, _int], _int),
     "krr_set_option": ([_vp, _int, _int], _int),
     "krr_kernel_mvp_noalloc": ([_vp, _i64, _int, _f, _f, _vp, _int, _vp, _vp], _int),
     "krr_profile_read": ([_vp, ctypes.POINTER(krr_profile)], _int),
+    "krr_selftest_wait_timeout": ([_vp, ctypes.c_longlong, _vp], _int),
 }
 
 
@@ -361,6 +364,23 @@ def krr_measure_rsqrt_rate(handle=None, stream=None):
     return a.value
 
 
+def krr_measure_half_rates(handle=None, stream=None):
+    """(ex2.f16x2 values/s, ex2.bf16x2 values/s, mma.sync f16 FLOP/s) on the
+    current device."""
+    h = handle or default_handle()
+    a, b, c = _d(), _d(), _d()
+    h.check(lib().krr_measure_half_rates(h.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), stream))
+    return a.value, b.value, c.value
+
+
+def krr_selftest_wait_timeout(limit_clocks=4000, handle=None, stream=None):
+    """Run a kernel whose bounded wait cannot complete (an mbarrier phase
+    nothing arrives on) and give up after limit_clocks SM clocks; returns the
+    status the library reports (KRR_ERR_TIMEOUT), without raising."""
+    h = handle or default_handle()
+    return lib().krr_selftest_wait_timeout(h.h, int(limit_clocks), stream)
+
+
 KRR_OPT_TCGEN05 = 1
 KRR_OPT_KERNEL = 2
 KRR_OPT_AUTOTUNE = 3
@@ -395,10 +415,11 @@ def krr_profile_read(handle=None):
 
 def krr_kernel_mvp_noalloc(X, Q, sigma, gamma, out=None, stream=None):
     """The kernel product through the entry point that allocates no device
-    memory (for callers that cannot allocate: callbacks, allocator hooks,
-    foreign memory pools, latency-bound paths).  Device tensors only;
-    N <= 16384, d <= 8, m <= 16.  The output is allocated here, by the caller
-    side, unless `out` is given."""
+    memory (for callers that cannot allocate: processes whose memory pool
+    belongs to another framework, latency-bound paths).  Device tensors only;
+    N <= 16384, d <= 8, m <= 16.  Waits for the stream; refuses a capturing
+    stream.  The output is allocated here, by the caller side, unless `out`
+    is given."""
     N, d = X.shape
     m = _cols(Q, N)
     Y = out if out is not None else _empty_like_cols(Q, m, N)

@@ -65,15 +65,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete, giving up after
-// WAIT_LIMIT_CLOCKS.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of `bar` to complete, giving up after `limit` SM
+// clocks.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > WAIT_LIMIT_CLOCKS) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// The bounded wait of every kernel: WAIT_LIMIT_CLOCKS.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, WAIT_LIMIT_CLOCKS);
 }
 
 // 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.

@@ -22,9 +22,13 @@ struct Buf {
   size_t bytes = 0;
 };
 
-// Grow-only device workspace addressed by name.
+// Grow-only device workspace addressed by name.  A fixed workspace (slots laid
+// out over memory the caller owns) never allocates: a request for a name it
+// does not hold, or for more bytes than that slot has, fails with
+// cudaErrorMemoryAllocation before any kernel could use the buffer.
 struct Workspace {
   std::unordered_map<std::string, Buf> slots;
+  bool fixed = false;
   cudaError_t get(const std::string& name, size_t bytes, void** out);
   void release_all();
 };

@@ -22,6 +22,7 @@ cudaError_t Workspace::get(const std::string& name, size_t bytes, void** out) {
     *out = it->second.p;
     return cudaSuccess;
   }
+  if (fixed) return cudaErrorMemoryAllocation;
   if (it != slots.end()) {
     // cudaFree waits for the device, so work queued on the old buffer is done
     cudaFree(it->second.p);
@@ -182,7 +183,7 @@ using namespace krr;
 
 extern "C" {
 
-int krr_version(void) { return 100; }
+int krr_version(void) { return 200; }
 
 const char* krr_status_string(krr_status s) {
   switch (s) {
@@ -210,6 +211,7 @@ void krr_fgmres_default_opts(krr_fgmres_opts* o) {
   o->inner_maxit = 100;
   o->inner_prec = KRR_FP32;
   o->use_graph = 1;
+  o->x0_given = 0;
 }
 
 krr_status krr_create(krr_handle* out) {

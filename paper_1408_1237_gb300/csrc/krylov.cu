@@ -511,6 +511,30 @@ __global__ void solve_init_kernel(KState* S0, const float* __restrict__ b, int64
   }
 }
 
+// x = x0 (FP64, original order, column c at x0 + c N; columns >= nx and the
+// padding start at 0) in float-float, and |b| per column.  The residual
+// r = b - K x follows from the accurate product (the start of a restart
+// cycle of Alg. 1 with x0 <- the given guess).
+__global__ void solve_init_x0_kernel(KState* S0, const float* __restrict__ b,
+                                     const double* __restrict__ x0, const int* __restrict__ perm,
+                                     int64_t N, int nx, int64_t Np, float* __restrict__ xh,
+                                     float* __restrict__ xl, double* partials) {
+  __shared__ double red[8];
+  KRR_COL;
+  double acc = 0.0;
+  KRR_GRID_LOOP(i) {
+    const double v = (col < nx && i < N) ? x0[(int64_t)col * N + perm[i]] : 0.0;
+    const float h = (float)v;
+    xh[co + i] = h;
+    xl[co + i] = (float)(v - (double)h);
+    const double bi = b[co + i];
+    acc += bi * bi;
+  }
+  double tot;
+  if (grid_sum_last(acc, partials + col * PSTRIDE, &S->ticket, red, tot) && threadIdx.x == 0)
+    S->bnorm = sqrt(tot);
+}
+
 // CG restart setup: stop when the true relative residual meets tol_stop,
 // else aim the next CG run at reducing |r| to tol_stop |b| (residual
 // replacement: CG restarted on A z = r from the accurate residual).
@@ -851,6 +875,19 @@ struct Solver {
     return cudaGetLastError();
   }
 
+  // Start of a solve: x = 0, r = b (x0 == null), or x = x0 (first nx
+  // columns of x0, N apart) and r = b - K x0 from the accurate product
+  cudaError_t init_solution(const double* x0, int64_t N, int nx) {
+    if (!x0) {
+      solve_init_kernel<<<vgrid(), VT, 0, st>>>(S, b, Np, xh, xl, r64, partials); count_launch();
+      return cudaGetLastError();
+    }
+    solve_init_x0_kernel<<<vgrid(), VT, 0, st>>>(S, b, x0, P.perm, N, nx, Np, xh, xl, partials); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    return residual(false);
+  }
+
   // r64 = b - K x (accurate), rnorm2 = |r|^2; only for the columns in a
   // restart cycle when in_cycle is set
   cudaError_t residual(bool in_cycle) {
@@ -879,6 +916,7 @@ struct SolveCfg {
   double tol, delta, inner_tol;
   krr_precision inner_prec;
   bool graph;
+  bool x0_given;
 };
 
 // Host-side initial state for one right-hand side.
@@ -1012,17 +1050,19 @@ cudaError_t capture_after(cudaStream_t st, cudaGraph_t g, const std::vector<cuda
   return fe ? fe : (ie ? ie : e);
 }
 
-// One independent branch of a batched graph: solve init and first check,
+// One independent branch of a batched graph: solve init (x0 = 0, or the
+// guess in xout when x0_given) and first check,
 // WHILE restart { ... }, scatter of the first `ncols_out` solution columns
 // to `xout` (original order, columns N apart).
 cudaError_t build_branch(cudaGraph_t g, Solver& s, double tol_stop, int64_t N, double* xout,
-                         int ncols_out) {
+                         int ncols_out, bool x0_given) {
   cudaError_t e;
   if ((e = cudaGraphConditionalHandleCreate(&s.rst_c.h, g, 0, cudaGraphCondAssignDefault))) return e;
   s.rst_c.use = 1;
   std::vector<cudaGraphNode_t> f0, f1;
   if ((e = capture_after(s.st, g, {}, [&]() -> cudaError_t {
-         solve_init_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
+         cudaError_t ie = s.init_solution(x0_given ? xout : nullptr, N, ncols_out);
+         if (ie) return ie;
          restart_check_kernel<<<1, 32, 0, s.st>>>(s.S, s.mc, s.G, s.rst_c, tol_stop); count_launch();
          return cudaGetLastError();
        }, f0)))
@@ -1091,6 +1131,7 @@ krr_status resolve_opts(Ctx& c, const char* fn, const krr_fgmres_opts* opts, flo
   cfg.inner_maxit = o.inner_maxit;
   cfg.inner_prec = o.inner_prec;
   cfg.graph = o.use_graph != 0;
+  cfg.x0_given = o.x0_given != 0;
   if (!std::isfinite(cfg.delta) || !std::isfinite(cfg.inner_tol))
     return set_error(c, KRR_ERR_INVALID_ARG, "%s: delta / inner_tol not finite", fn);
   return KRR_OK;
@@ -1111,15 +1152,16 @@ void fill_info(const KState& h, float ms, krr_solve_info* info) {
 // One block solve of the sorted right-hand sides already in s.b (exec: the
 // solve graph, or null for the host-driven loop); final states in hs.
 krr_status fgmres_block(Solver& s, const SolveCfg& cfg, cudaGraphExec_t exec,
-                        std::vector<KState>& hs, float* ms_out) {
+                        std::vector<KState>& hs, float* ms_out, const double* x0 = nullptr,
+                        int64_t N = 0, int nx = 0) {
   Ctx& c = s.c;
   const char* fn = "krr_fgmres_solve";
   cudaError_t e;
   if ((e = upload_states(s, cfg, hs))) return cuda_error(c, e, fn);
   const double tol_stop = 0.5 * cfg.tol;
   cudaEventRecord(c.ev0, s.st);
-  solve_init_kernel<<<s.vgrid(), VT, 0, s.st>>>(s.S, s.b, s.Np, s.xh, s.xl, s.r64, s.partials); count_launch();
-  // the first restart check turns x0 = 0, r0 = b into the first cycle
+  if ((e = s.init_solution(x0, N, nx))) return cuda_error(c, e, fn);
+  // the first restart check turns x0, r0 = b - K x0 into the first cycle
   restart_check_kernel<<<1, 32, 0, s.st>>>(s.S, s.mc, s.G, Cond{}, tol_stop); count_launch();
   Group g;
   if (exec) {
@@ -1211,7 +1253,8 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
   bool sX, sB, sXs;
   if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
   if ((s = device_view(c, "stage.B", B, (size_t)N * m_rhs, true, st, &dB, &sB))) return s;
-  if ((s = device_view_d(c, "stage.Xsol", Xsol, (size_t)N * m_rhs, false, st, &dXs, &sXs))) return s;
+  if ((s = device_view_d(c, "stage.Xsol", Xsol, (size_t)N * m_rhs, cfg.x0_given, st, &dXs, &sXs)))
+    return s;
   Solver sv(c);
   sv.st = st;
   cudaError_t e = prepare_points(c, dX, N, d, sigma, "kry.pts", sv.P, st);
@@ -1244,7 +1287,8 @@ krr_status krr_fgmres_solve(krr_handle h, const float* X, int64_t N, int d, floa
     const int ncols = std::min(width, m_rhs - col0);
     if ((e = load_rhs(sv, dB + (size_t)col0 * N, N, ncols))) return cuda_error(c, e, fn);
     float ms = 0.f;
-    if ((s = fgmres_block(sv, cfg, exec, hs, &ms))) return s;
+    const double* x0 = cfg.x0_given ? dXs + (size_t)col0 * N : nullptr;
+    if ((s = fgmres_block(sv, cfg, exec, hs, &ms, x0, N, ncols))) return s;
     scatter_x64_kernel<<<dim3(sv.vblocks, (unsigned)ncols), VT, 0, st>>>(sv.xh, sv.xl, sv.P.perm, N, sv.Np,
                                                                           dXs + (size_t)col0 * N); count_launch();
     if ((e = cudaGetLastError())) return cuda_error(c, e, fn);
@@ -1292,7 +1336,8 @@ krr_status krr_fcg_solve(krr_handle h, const float* X, int64_t N, int d, float s
   bool sX, sB, sXs;
   if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
   if ((s = device_view(c, "stage.B", B, (size_t)N * m_rhs, true, st, &dB, &sB))) return s;
-  if ((s = device_view_d(c, "stage.Xsol", Xsol, (size_t)N * m_rhs, false, st, &dXs, &sXs))) return s;
+  if ((s = device_view_d(c, "stage.Xsol", Xsol, (size_t)N * m_rhs, cfg.x0_given, st, &dXs, &sXs)))
+    return s;
   Solver sv(c);
   sv.st = st;
   cudaError_t e = prepare_points(c, dX, N, d, sigma, "kry.pts", sv.P, st);
@@ -1334,12 +1379,14 @@ krr_status krr_fcg_solve(krr_handle h, const float* X, int64_t N, int d, float s
       return ee;
     };
     cudaEventRecord(c.ev0, st);
-    solve_init_kernel<<<vb, VT, 0, st>>>(sv.S, sv.b, Np, sv.xh, sv.xl, sv.r64, sv.partials); count_launch();
+    // x0 = 0 and r = b, or the given guess and r = b - K x0 (accurate)
+    if ((e = sv.init_solution(cfg.x0_given ? dXs + (size_t)col * N : nullptr, N, 1)))
+      return cuda_error(c, e, fn);
     KState ks;
     if ((e = read_state(c, sv.S, ks, st))) return cuda_error(c, e, fn);
     const double bnorm = ks.bnorm;
     if ((e = reset_window(bnorm))) return cuda_error(c, e, fn);
-    double rr = ks.rnorm2, relres_true = bnorm > 0.0 ? 1.0 : 0.0;
+    double rr = ks.rnorm2, relres_true = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
     int it = 0, head = 0, cycles = 1;
     krr_status st_col = KRR_OK;
     bool done = bnorm == 0.0;
@@ -1600,7 +1647,8 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
     for (size_t b = b0; b < b1; ++b) {
       const Branch& x = br[b];
       const krr_problem& pr = probs[x.prob];
-      if ((e = build_branch(g, *x.sv, 0.5 * cfg.tol, pr.N, pr.Xsol + (size_t)x.col0 * pr.N, x.ncols))) {
+      if ((e = build_branch(g, *x.sv, 0.5 * cfg.tol, pr.N, pr.Xsol + (size_t)x.col0 * pr.N, x.ncols,
+                            cfg.x0_given))) {
         cudaGraphDestroy(g);
         cudaGetLastError();
         return cuda_error(c, e, "krr_fgmres_solve_batched (graph build)");

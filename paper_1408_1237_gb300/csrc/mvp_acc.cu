@@ -12,10 +12,12 @@
 //     differences (TwoSum), exact products (FMA error terms) and TwoSum
 //     accumulation;
 //   * e = -s^2 r^2 with s^2 = log2(e)/(2 sigma^2) split into float hi + lo;
-//   * 2^e by table-driven reduction e = n + k/64 + t, |t| <= 1/128: 2^(k/64)
-//     from a 64-entry float-float table, 2^t = 1 + u with u from the Taylor
-//     series of exp(t ln 2) to degree 4 (remainder < 1e-13), u itself in
-//     float-float; the result is within about 3e-12 (relative);
+//   * 2^e by Tang's table-driven reduction (ffexp2.h) e = n + k/64 + t,
+//     |t| <= 1/128: 2^(k/64) from a 64-entry float-float table, 2^t = 1 + u
+//     with u from the Taylor series of exp(t ln 2) to degree 4 (remainder
+//     < 1e-13), u itself in float-float; relative error 5e-12 + 2e-7 |el| +
+//     (ln 2 el)^2 / 2, below 6e-11 for the terms that matter (a bound
+//     tests/test_ffexp2.py checks on the CPU);
 //   * q_j (the FP64 iterate) arrives as float hi + lo; each product q_j Phi_ij
 //     is split exactly (FMA error term) and summed with TwoSum.
 // The Matern kernel of Sec. 6.1 (KF = 1) follows the same scheme: r^2 as
@@ -33,6 +35,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "ffexp2.h"
 #include "internal.h"
 
 namespace krr {
@@ -45,13 +48,10 @@ constexpr int RS = 3;
 template <int KF>
 constexpr float far_e() { return KF == 0 ? 30.f : 625.f; }
 
-struct AccConst {
+struct AccConst : FFExp2Const {
   float s2h, s2l;  // s^2 = s2h + s2l
   float sh, sl;    // s = sh + sl (Matern: sqrt(3) / h)
   float l2eh, l2el;  // log2(e) = l2eh + l2el
-  float c1h, c1l;  // ln 2 = c1h + c1l
-  float c2, c3, c4;  // (ln 2)^k / k!, k = 2..4
-  float th[64], tl[64];  // 2^(k/64) = th[k] + tl[k]
 };
 
 struct AccParams {
@@ -70,12 +70,6 @@ struct AccParams {
   size_t state_stride;
   AccConst k;
 };
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
 
 // a - b exactly as s + e (Knuth's TwoSum on a and -b).
 __device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
@@ -105,36 +99,11 @@ __device__ __forceinline__ void acc_r2(const float (&xi)[D], const float* __rest
   }
 }
 
-// 2^(eh + el) (eh <= 0, |el| small) as the float-float Hout + Lout.
+// 2^(eh + el) as the float-float Hout + Lout (ffexp2.h).
 __device__ __forceinline__ void acc_exp2(float eh, float el, const AccConst& k,
                                          const float* __restrict__ tab_h,
                                          const float* __restrict__ tab_l, float& Hout, float& Lout) {
-  // e = n + j/64 + (r + el), m = 64 n + j = rint(64 eh); below -200 the value
-  // flushes to zero anyway
-  const float y = 64.f * fmaxf(eh, -200.f);  // exact scaling
-  const float tm = y + 12582912.f;          // 1.5 * 2^23: rounds to an integer
-  const float mf = tm - 12582912.f;
-  const float r = (y - mf) * 0.015625f;     // exact, |r| <= 1/128
-  const int m = __float_as_int(tm) - 0x4B400000;
-  const int n = m >> 6;                     // floor(m / 64)
-  const int jt = m - (n << 6);              // 0..63
-  // 2^(r + el) = 1 + uh + ul: the linear term ln2 (r + el) in float-float,
-  // the series tail c2 r^2 + c3 r^3 + c4 r^4 at r plus its first-order
-  // change (2 c2 + 3 c3 r) r el (el is up to ~2e-6: leaving the change out
-  // costs ~4e-9 relative, with it the result is within ~3e-12)
-  const float uh = k.c1h * r;
-  const float ul = fmaf(k.c1h, r, -uh) + fmaf(k.c1l, r, k.c1h * el) +
-                   fmaf(r * r, fmaf(fmaf(k.c4, r, k.c3), r, k.c2),
-                        (fmaf(3.f * k.c3, r, 2.f * k.c2) * r) * el);
-  // (Th + Tl)(1 + uh + ul) = H + L2
-  const float Th = tab_h[jt], Tl = tab_l[jt];
-  const float P = Th * uh;
-  const float Pe = fmaf(Th, uh, -P);
-  float H = Th + P;                          // |Th| >= 1 > |P|: Fast2Sum
-  float L2 = ((Th - H) + P) + Pe + fmaf(Th, ul, Tl * (1.f + uh));
-  const float sc = (n >= -126) ? __int_as_float((n + 127) << 23) : 0.f;
-  Hout = H * sc;
-  Lout = L2 * sc;
+  ff_exp2(eh, el, k, tab_h, tab_l, Hout, Lout);
 }
 
 // Kernel value of the pair (xi, xj) as the float-float Hout + Lout:
@@ -560,23 +529,13 @@ __global__ void __launch_bounds__(256) acc_finalize_kernel(const AccFin f) {
   }
 }
 
-// log2(e) and ln 2 in float-float, the Taylor coefficients (ln 2)^k / k! (k = 2..4) and
-// the table 2^(j/64), j = 0..63, in float-float.
+// log2(e) in float-float, and the constants of the float-float 2^x.
 AccConst make_consts() {
   AccConst k;
+  ff_exp2_consts(k);
   const double ln2 = std::log(2.0);
   k.l2eh = (float)(1.0 / ln2);
   k.l2el = (float)(1.0 / ln2 - (double)k.l2eh);
-  k.c1h = (float)ln2;
-  k.c1l = (float)(ln2 - (double)k.c1h);
-  k.c2 = (float)(ln2 * ln2 / 2.0);
-  k.c3 = (float)(ln2 * ln2 * ln2 / 6.0);
-  k.c4 = (float)(ln2 * ln2 * ln2 * ln2 / 24.0);
-  for (int j = 0; j < 64; ++j) {
-    const double v = std::exp2(j / 64.0);
-    k.th[j] = (float)v;
-    k.tl[j] = (float)(v - (double)k.th[j]);
-  }
   return k;
 }
 

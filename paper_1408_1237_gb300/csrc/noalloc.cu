@@ -1,10 +1,10 @@
 // krr_kernel_mvp_noalloc: the kernel product for callers that cannot
 // allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc is off limits -- inside a
-// host callback or a custom allocator hook, in a process whose memory pool is
-// owned by another framework and must not be fragmented, or on a path with a
-// hard real-time bound where cudaMalloc's implicit device synchronisation is
+// Who needs it: a process whose device memory pool belongs to another
+// framework (an inference server, a game engine) that forbids foreign
+// cudaMalloc calls or would be fragmented by them, and code on a
+// latency-bound path where cudaMalloc's implicit device synchronisation is
 // not acceptable.  Such a caller cannot create a krr_handle either (the handle
 // grows its workspace with cudaMalloc).
 //
@@ -18,8 +18,16 @@
 // is looked up with cudaGetSymbolAddress, once per device, by the first call
 // made with that device current; that first call should therefore come
 // before any stream capture.  The carved-up workspace is presented to the
-// same prep and product code as a handle's workspace, already sized for the
-// largest accepted problem, so none of it allocates.
+// same prep and product code as a handle's workspace, marked fixed: each
+// region is recorded with its real size, and a request for more than a
+// region holds (or for a buffer the table does not list) fails with
+// KRR_ERR_OOM before any kernel could write past the region.
+//
+// The call is not asynchronous: the point preparation reads two block counts
+// back to the host to size the product grids, so the call waits for `stream`
+// up to that point.  It must therefore not be made while `stream` is being
+// captured into a graph (it returns KRR_ERR_INVALID_ARG then), nor from a
+// host function enqueued on a stream (CUDA forbids CUDA calls there).
 //
 // Every call on a device shares the one array and it keeps the previous
 // call's contents; the counters that must start at zero are cleared by each
@@ -93,8 +101,9 @@ constexpr size_t total_bytes() {
 
 #define KRR_NOALLOC_SCRATCH_BYTES (krr::total_bytes())
 
-// The scratch array: 10,415,616 bytes (about 10 MB).  Host code must not take its address
+// The scratch array: 10,415,872 bytes (about 10 MB).  Host code must not take its address
 // directly: use the pointer from cudaGetSymbolAddress.
+static_assert(KRR_NOALLOC_SCRATCH_BYTES == 10415872, "the documented scratch size");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KRR_NOALLOC_SCRATCH_BYTES];
 
 namespace krr {
@@ -133,10 +142,12 @@ krr_status setup_device(int dev, DeviceScratch*& out) {
     d.ctx.allow_tcx = false;
     size_t off = 0;
     for (const Region& r : kRegions) {
-      // recorded as larger than any request, so the workspace never regrows
-      d.ctx.ws.slots[r.name] = Buf{d.base + off, (size_t)1 << 62};
+      // each region with its real (256-byte rounded) size; the workspace is
+      // fixed, so a larger request fails instead of allocating
+      d.ctx.ws.slots[r.name] = Buf{d.base + off, align256(r.bytes)};
       off += align256(r.bytes);
     }
+    d.ctx.ws.fixed = true;
     d.ctx.d_err = (int*)d.ctx.ws.slots["na.err"].p;
     d.ready = true;
   }
@@ -168,6 +179,15 @@ extern "C" krr_status krr_kernel_mvp_noalloc(const float* X, int64_t N, int d, f
   if (N == 0) return KRR_OK;
   if (!X || !Q || !Y || (const void*)Y == (const void*)Q || (const void*)Y == (const void*)X)
     return KRR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the preparation waits for the stream, which a capture does not allow
+  // (checked before any other CUDA call of this entry point)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return KRR_ERR_INVALID_ARG;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return KRR_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -180,7 +200,6 @@ extern "C" krr_status krr_kernel_mvp_noalloc(const float* X, int64_t N, int d, f
   std::lock_guard<std::mutex> lk(ds->mu);
   // device arrays only: staging host arrays would need an allocation
   if (!on_device(dev, X) || !on_device(dev, Q) || !on_device(dev, Y)) return KRR_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
   const size_t nslots = c.ws.slots.size();
   // counters that must start at zero: the error word and the dot ticket
   cudaError_t e = cudaMemsetAsync(c.d_err, 0, sizeof(int), st);

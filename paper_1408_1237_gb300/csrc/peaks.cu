@@ -1,7 +1,14 @@
 // Issue-rate microbenchmarks for the ALU roofline of the kernel product:
 // MUFU.EX2 (ex2.approx.ftz.f32), scalar FFMA and packed FFMA2 (f32x2)
-// results per second on this GPU, measured at its current clocks; and the
-// reciprocal square root (rsqrtf) the Matern kernel takes per pair.
+// results per second on this GPU, measured at its current clocks; the
+// reciprocal square root (rsqrtf) the Matern kernel takes per pair; and the
+// rates that decide the reduced-precision design: packed half-precision
+// exponentials (ex2.approx.f16x2, ex2.approx.ftz.bf16x2: two values per
+// instruction) and the warp-level tensor-core MMA (mma.sync m16n8k16, f16 in,
+// f32 accumulate) the multi-column product issues.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "api_util.h"
 #include "common.cuh"
 #include "internal.h"
@@ -70,6 +77,77 @@ __global__ void __launch_bounds__(256) rsqrt_rate_kernel(float* out, float seed)
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Two exponentials per instruction: a chain of ex2.approx.f16x2 on packed
+// halves (2^-x converges to a fixed point, so the values stay finite).
+__global__ void __launch_bounds__(256) ex2_f16x2_rate_kernel(float* out, float seed) {
+  uint32_t x[CHAINS];
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) {
+    __half2 h = __floats2half2_rn(-(seed + 0.01f * c), -(seed + 0.02f * c));
+    x[c] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  for (int it = 0; it < ITERS; ++it) {
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) {
+      uint32_t y;
+      asm volatile("ex2.approx.f16x2 %0, %1;" : "=r"(y) : "r"(x[c] ^ 0x80008000u));
+      x[c] = y;
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) s ^= x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+}
+
+__global__ void __launch_bounds__(256) ex2_bf16x2_rate_kernel(float* out, float seed) {
+  uint32_t x[CHAINS];
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(seed + 0.01f * c, seed + 0.02f * c);
+    x[c] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  for (int it = 0; it < ITERS; ++it) {
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) {
+      uint32_t y;
+      asm volatile("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(y) : "r"(x[c] ^ 0x80008000u));
+      x[c] = y;
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) s ^= x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+}
+
+// Four independent accumulators per warp, each m16n8k16 (f16 in, f32 out).
+constexpr int MMA_CHAINS = 4;
+__global__ void __launch_bounds__(256) mma_sync_rate_kernel(float* out, float seed) {
+  float d[MMA_CHAINS][4];
+#pragma unroll
+  for (int a = 0; a < MMA_CHAINS; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) d[a][b] = 0.f;
+  __half2 h = __floats2half2_rn(seed, 0.5f * seed);
+  const uint32_t v = *reinterpret_cast<uint32_t*>(&h);
+  for (int it = 0; it < ITERS; ++it) {
+#pragma unroll
+    for (int a = 0; a < MMA_CHAINS; ++a)
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+          "{%8,%9}, {%0,%1,%2,%3};"
+          : "+f"(d[a][0]), "+f"(d[a][1]), "+f"(d[a][2]), "+f"(d[a][3])
+          : "r"(v), "r"(v), "r"(v), "r"(v), "r"(v), "r"(v));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int a = 0; a < MMA_CHAINS; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) s += d[a][b];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace krr
 
@@ -126,5 +204,42 @@ extern "C" krr_status krr_measure_rsqrt_rate(krr_handle h, double* rsqrt_per_s, 
     if (rep > 0 && ms < best) best = ms;
   }
   *rsqrt_per_s = (double)blocks * threads * CHAINS * ITERS / (best * 1e-3);
+  return KRR_OK;
+}
+
+extern "C" krr_status krr_measure_half_rates(krr_handle h, double* ex2_f16x2_values_per_s,
+                                             double* ex2_bf16x2_values_per_s,
+                                             double* mma_sync_f16_flops_per_s, void* stream) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = c.num_sms * 8, threads = 256;
+  void* out;
+  cudaError_t e = c.ws.get("peaks.out", sizeof(float) * blocks * threads, &out);
+  if (e) return cuda_error(c, e, "krr_measure_half_rates");
+  double res[3];
+  for (int k = 0; k < 3; ++k) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(c.ev0, st);
+      if (k == 0) ex2_f16x2_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f);
+      if (k == 1) ex2_bf16x2_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f);
+      if (k == 2) mma_sync_rate_kernel<<<blocks, threads, 0, st>>>((float*)out, 0.5f);
+      count_launch();
+      cudaEventRecord(c.ev1, st);
+      if ((e = cudaEventSynchronize(c.ev1))) return cuda_error(c, e, "krr_measure_half_rates");
+      float ms;
+      cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+      if (rep > 0 && ms < best) best = ms;
+    }
+    const double threads_it = (double)blocks * threads * ITERS;
+    // values: 2 per ex2 instruction and chain; MMA: one per warp and chain,
+    // 2 * 16 * 8 * 16 flops
+    const double work = k < 2 ? threads_it * CHAINS * 2.0 : threads_it / 32.0 * MMA_CHAINS * 4096.0;
+    res[k] = work / (best * 1e-3);
+  }
+  if (ex2_f16x2_values_per_s) *ex2_f16x2_values_per_s = res[0];
+  if (ex2_bf16x2_values_per_s) *ex2_bf16x2_values_per_s = res[1];
+  if (mma_sync_f16_flops_per_s) *mma_sync_f16_flops_per_s = res[2];
   return KRR_OK;
 }

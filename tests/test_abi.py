@@ -52,11 +52,12 @@ def test_host_only_functions(clib):
     # Sec. 6 defaults: outer tol 1e-6, delta and inner tol from the rules
     assert (o.restart, o.tol, o.delta, o.inner_tol) == (30, 1e-6, -1.0, -1.0)
     assert o.inner_maxit == 100 and o.inner_prec == 0
+    assert o.use_graph == 1 and o.x0_given == 0
 
 
 def test_struct_layouts_match_header(clib):
     from paper_1408_1237_gb300 import binding
-    # krr_fgmres_opts: 2 ints, 3 doubles, 3 ints (with padding) -> 48 bytes
+    # krr_fgmres_opts: 2 ints, 3 doubles, 4 ints -> 48 bytes
     assert ctypes.sizeof(binding.krr_fgmres_opts) == 48
     assert ctypes.sizeof(binding.krr_solve_info) == 48
     assert ctypes.sizeof(binding.krr_problem) == 40
@@ -81,7 +82,8 @@ C_PROGRAM = r"""
 int main(void) {
     krr_fgmres_opts o;
     krr_fgmres_default_opts(&o);
-    if (o.restart != 30 || o.tol != 1e-6 || o.inner_maxit != 100) return 2;
+    if (o.restart != 30 || o.tol != 1e-6 || o.inner_maxit != 100 || o.x0_given != 0) return 2;
+    if (sizeof(krr_fgmres_opts) != 48) return 10;
     if (strcmp(krr_status_string(KRR_NOT_CONVERGED), "KRR_NOT_CONVERGED") != 0) return 3;
     if (krr_version() < 100) return 4;
     if (krr_create(NULL) != KRR_ERR_INVALID_ARG) return 5;
