@@ -175,7 +175,14 @@ typedef enum {
      * memory; 0: with mma.sync.  Same results to the float32 bar; on GB300
      * the default is faster (measured at N = 65536: d = 16 2685 vs 2500,
      * d = 32 1434 vs 1185, d = 64 739 vs 655 Gpairs/s). */
-    KRR_OPT_HIGHD_TCGEN05 = 6
+    KRR_OPT_HIGHD_TCGEN05 = 6,
+    /* value != 0 (default): multi-column products (m >= 2, block solves,
+     * the gradient's solves) up to 8 dimensions evaluate the kernel values of
+     * their direct-form (non-compact) target blocks on the CUDA cores and run
+     * the weighted sum P Q on the tensor cores (split f16 for KRR_FP32,
+     * single f16 / bf16 for reduced precision); 0: the all-CUDA-core kernel
+     * (one FMA per pair and column).  Same results to the float32 bar. */
+    KRR_OPT_DIRECT_TENSOR = 7
 } krr_option;
 
 /* Kernel functions (KRR_OPT_KERNEL). */

@@ -108,6 +108,10 @@ struct Ctx {
   // single-column products above 8 dimensions on the tcgen05 kernel
   // (mvp_uhd_kernel; false: the mma.sync kernel mvp_tch_kernel)
   bool highd_tcgen05 = true;
+  // direct-form super-blocks of multi-column products up to 8 dimensions:
+  // kernel values on the CUDA cores, the weighted sum on the tensor cores
+  // (mvp_dirtc_kernel); false: the all-CUDA-core kernel mvp_dirm_kernel
+  bool direct_tensor = true;
   // kernel function of every product and solve (KRR_KERNEL_*, krr_set_option)
   int kernel_family = 0;
   // autotuning of the products' source splits (KRR_OPT_AUTOTUNE): the first
@@ -259,6 +263,15 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
 cudaError_t mvp_umma_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
                               bool split, bool bf, int splits, int tiles_per_split, double* part,
                               float* fac, const int* active, cudaStream_t st, bool dry = false);
+// ---- mvp_dirtc.cu: partial sums of the direct-form super-blocks (slots
+// [slot0, nsb) of T.sb_order, checked against the device count tn_exp) of a
+// multi-column product, d <= 8: kernel values on the CUDA cores, the weighted
+// sum P Q on the tensor cores (split f16 for KRR_FP32, single f16 / bf16
+// otherwise; the Matern kernel always split); part: [splits][m][T.Npad].
+cudaError_t mvp_dirtc_partials(Ctx& c, const PointsDev& T, const PointsDev& S, const float* Q, int m,
+                               krr_precision prec, int splits, int tiles_per_split, int64_t slot0,
+                               const int* tn_exp, double* part, float* fac, const int* active,
+                               cudaStream_t st, bool dry = false);
 // Workspace and attributes of mvp_multi_launch with m columns and prec.
 cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& T, const PointsDev& S, int m,
                               krr_precision prec, cudaStream_t st);

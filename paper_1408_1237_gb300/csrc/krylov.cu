@@ -1621,6 +1621,7 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
       bc->kernel_family = c.kernel_family;
       bc->autotune = c.autotune;
       bc->highd_tcgen05 = c.highd_tcgen05;
+      bc->direct_tensor = c.direct_tensor;
       if (col0 == 0 && (e = prepare_points(*bc, pr.X, pr.N, d, sigma, "bat.pts", pts[k], st)))
         return cuda_error(c, e, fn);
       auto so = std::make_unique<Solver>(*bc);

@@ -755,7 +755,18 @@ Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
 // every super-block takes the direct form, whatever its compactness flag.
 bool multi_direct_only(const PointsDev& Tp) { return Tp.d > 8 || Tp.kfam != KRR_KERNEL_GAUSSIAN; }
 int64_t multi_nexp(const PointsDev& Tp) { return multi_direct_only(Tp) ? 0 : Tp.h_sb_nexp; }
+// Direct-form super-blocks of a multi-column product up to 8 dimensions take
+// the kernel with the weighted sum on the tensor cores (mvp_dirtc.cu: one CTA
+// of 16 warps per super-block, one resident per SM) unless the handle asks
+// for the CUDA-core kernel (KRR_OPT_DIRECT_TENSOR = 0).
+bool use_dirtc(const Ctx& c, const PointsDev& Tp) {
+  return c.direct_tensor && Tp.d <= 8 &&
+         (Tp.kfam == KRR_KERNEL_GAUSSIAN || Tp.kfam == KRR_KERNEL_MATERN32);
+}
 Plan multi_plan_dir(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+  if (use_dirtc(c, Tp))
+    return make_plan((Tp.nsb - multi_nexp(Tp)) * NW, (int)(Sp.Npad / TS), c.num_sms,
+                     c.plan_slots > 0 ? c.plan_slots : c.num_sms, c.split_scale);
   return make_plan((Tp.nsb - multi_nexp(Tp)) * NW, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots,
                    c.split_scale);
 }
@@ -1164,7 +1175,13 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)m * Tp.Npad, &v))) return e;
   MvpParams p{};
   p.nblk = Tp.nsb;
-  if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, m, SB / 32, multi_nexp(Tp), pd, st, false))) return e;
+  if (use_dirtc(c, Tp)) {
+    if ((e = mvp_dirtc_partials(c, Tp, Sp, nullptr, m, prec, pd.splits, pd.tiles_per_split, multi_nexp(Tp),
+                                nullptr, nullptr, nullptr, nullptr, st, true)))
+      return e;
+  } else if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, nullptr, 0, m, SB / 32, multi_nexp(Tp), pd, st, false))) {
+    return e;
+  }
   if (direct_only) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
   if (c.use_tcgen05)
     return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
@@ -1225,7 +1242,8 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
                               pt.tiles_per_split, (double*)part, p.fac, o.active, st);
     if (e) return e;
   }
-  // direct-form super-blocks: all columns in one CUDA-core launch
+  // direct-form super-blocks: all columns in one launch (the weighted sum
+  // on the tensor cores, or the CUDA-core kernel by option)
   if (Tp.nsb > nexp) {
     p.part = (double*)partd;
     if (direct_only) {
@@ -1234,7 +1252,13 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
       if ((e = c.ws.get("mvp.zero", sizeof(int), &zero))) return e;
       p.tn_exp = (const int*)zero;
     }
-    if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, Q, Sp.Npad, m, SB / 32, nexp, pd, st, true))) return e;
+    if (use_dirtc(c, Tp)) {
+      if ((e = mvp_dirtc_partials(c, Tp, Sp, Q, m, prec, pd.splits, pd.tiles_per_split, nexp, p.tn_exp,
+                                  (double*)partd, p.fac, o.active, st, false)))
+        return e;
+    } else if ((e = dirm_dispatch(p, Tp.d, Tp.kfam, Q, Sp.Npad, m, SB / 32, nexp, pd, st, true))) {
+      return e;
+    }
   }
   if (pev1) cudaEventRecord(pev1, st);
   FinParams f{};

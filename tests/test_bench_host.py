@@ -10,13 +10,21 @@ import bench
 
 
 def test_traffic_reported_only_for_the_captured_sources(monkeypatch):
-    assert bench.traffic_bytes(True) == bench.TRAFFIC_TCX["bytes"]
-    changed = copy.deepcopy(bench.TRAFFIC_TCX)
+    # with the hashes of the sources as they are now, the bytes are reported
+    import hashlib
+    import os
+    current = copy.deepcopy(bench.TRAFFIC_TCX)
+    for src in current["sources"]:
+        with open(os.path.join(bench.ROOT, src), "rb") as f:
+            current["sources"][src] = hashlib.sha1(f.read()).hexdigest()
+    monkeypatch.setattr(bench, "TRAFFIC_TCX", current)
+    assert bench.traffic_bytes(True) == current["bytes"]
+    changed = copy.deepcopy(current)
     src = next(iter(changed["sources"]))
     changed["sources"][src] = "0" * 40
     monkeypatch.setattr(bench, "TRAFFIC_TCX", changed)
     assert bench.traffic_bytes(True) is None
-    missing = copy.deepcopy(bench.TRAFFIC_TCX)
+    missing = copy.deepcopy(current)
     missing["sources"] = {"no/such/file.cu": "0" * 40}
     monkeypatch.setattr(bench, "TRAFFIC_TCX", missing)
     assert bench.traffic_bytes(True) is None

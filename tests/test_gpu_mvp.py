@@ -260,3 +260,45 @@ def test_mvp_rect_high_dimension(K, oracle_mod):
     scale = oracle_mod.mvp_rect(Xt.astype(np.float64), Xs.astype(np.float64),
                                 np.abs(q.astype(np.float64)), f32(sigma))
     assert np.max(np.abs(y - ref) / np.maximum(scale, 1e-30)) <= TOL_FP32
+
+
+@pytest.mark.parametrize("m,d,sigma,normal,prec,bound", [
+    (16, 8, 1.0, True, "fp32", TOL_FP32), (9, 4, 0.05, False, "fp32", TOL_FP32),
+    (5, 1, 0.003, False, "fp32", TOL_FP32), (2, 6, 0.6, True, "fp32", TOL_FP32),
+    (16, 8, 1.0, True, "fp16", 2e-3), (8, 3, 0.01, False, "bf16", 2e-2)])
+def test_mvp_multi_direct_form_tensor_and_cuda_core(K, oracle_mod, m, d, sigma, normal, prec, bound):
+    # direct-form (non-compact) target blocks: the default kernel keeps the
+    # kernel values on the CUDA cores and runs P Q on the tensor cores;
+    # KRR_OPT_DIRECT_TENSOR = 0 selects the all-CUDA-core kernel.  Both meet
+    # the bar against the FP64 oracle, on a ragged N.
+    rng = np.random.default_rng(400 + m + 10 * d)
+    N = 4997
+    X = (rng.standard_normal((N, d)) if normal else rng.random((N, d))).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    for opt in (1, 0):
+        h = K.Handle()
+        try:
+            K.krr_set_option(K.KRR_OPT_DIRECT_TENSOR, opt, handle=h)
+            Y = K.krr_kernel_mvp(_dev(X), _dev(Q), sigma, 1e-2, prec=prec, handle=h).cpu().numpy()
+        finally:
+            h.close()
+        errs = [scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-2) for c in range(m)]
+        assert max(errs) <= bound, (opt, max(errs))
+        if prec != "fp32" and opt == 1:
+            # the tensor-core kernel really ran in reduced precision (the
+            # CUDA-core kernel evaluates direct-form blocks in float32)
+            assert max(errs) > 1e-7
+
+
+def test_mvp_multi_direct_tensor_batch_shape_full_size(K, oracle_mod):
+    # the batching workload's largest shape: N = 65536, d = 8, N(0, I)
+    # points, sigma 1, 16 columns (almost every super-block direct-form),
+    # sampled rows against the oracle
+    rng = np.random.default_rng(501)
+    N, d, m = 65536, 8, 16
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    Q = rng.standard_normal((m, N)).astype(np.float32)
+    Y = K.krr_kernel_mvp(_dev(X), _dev(Q), 1.0, 1e-3).cpu().numpy()
+    rows = inputs.sample_rows(N, 256, seed=5)
+    for c in (0, 5, 15):
+        assert scaled_error(oracle_mod, X, Q[c], Y[c], 1.0, 1e-3, rows) <= TOL_FP32, c
