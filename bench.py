@@ -7,11 +7,16 @@ gamma I) q through the C ABI on the 2^20-point unit-cube cloud (d = 3,
 sigma 0.05, gamma 1e-3): point preparation (Morton sort, packing, block
 metadata), the product kernel and its finalize.  `value` is whole-job
 Gpairs/s (N^2 pairs per step per rank, all ranks, over the slowest rank's
-device time).  Extra keys report the 16-column product, the FGMRES solves
-(time to a 1e-6 relative residual, the plain float32 inner form next to the
-reduced-precision inner form), the roofline of the product kernel, the
-host-buffer end-to-end rate, the SM clocks seen during the timed region and
-the FP64 oracle timed on the host cores.
+device time).  Extra keys report the 16-column product, the roofline of the
+product kernel, the host-buffer end-to-end rate, the SM clocks seen during
+the timed region, the measured issue rates behind the design, and the FP64
+oracle timed on the host cores.  On one GPU the solver forms follow, each
+timed to a true relative residual of 1e-6: the batching workload at full
+size (64 problems, mixed-precision and float32 batched calls against plain
+float32 single-column solves), the precision-form mixture at full size
+(262,144 points), every form compared on the same mixture at 65,536 points,
+the log-marginal-likelihood gradient, and the high-d, Matern and autotuner
+extras, in that order while the --budget-s wall clock lasts.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl libkrr|reference]
 For N > 1 launch one process per GPU with torchrun; every rank solves its
@@ -50,16 +55,31 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libkrr", choices=["libkrr", "reference"])
-    ap.add_argument("--solve-n", type=int, default=1 << 15,
-                    help="points of the mixture-cloud FGMRES solves (0 skips them)")
-    ap.add_argument("--plain-cols", type=int, default=4,
+    ap.add_argument("--precision-n", type=int, default=1 << 18,
+                    help="points of the full-size precision-form solve (the 16-component mixture; "
+                         "plain FP32 inner products; 0 skips it)")
+    ap.add_argument("--precision-cap", type=int, default=800,
+                    help="inner CG steps per outer step of the precision-form solves")
+    ap.add_argument("--solve-cap", type=int, default=400,
+                    help="inner CG steps per outer step of the compared forms")
+    ap.add_argument("--solve-n", type=int, default=1 << 16,
+                    help="points of the mixture cloud on which every form is compared (plain FP32, "
+                         "f16 and bf16 inner, 16-column blocks; 0 skips it)")
+    ap.add_argument("--plain-cols", type=int, default=2,
                     help="right-hand sides solved one at a time for the per-RHS plain FP32 time")
-    ap.add_argument("--batch-probs", type=int, default=4,
-                    help="problems of the batching-form subset (0 skips it)")
-    ap.add_argument("--batch-nmax", type=int, default=8192,
-                    help="largest problem of the batching-form subset")
+    ap.add_argument("--batch-probs", type=int, default=64,
+                    help="problems of the batching form (0 skips it)")
+    ap.add_argument("--batch-nmax", type=int, default=65536,
+                    help="largest problem of the batching form")
+    ap.add_argument("--batch-plain", type=int, default=8,
+                    help="seeded sample of problems solved one right-hand side at a time for the "
+                         "plain FP32 per-RHS time of the batching form")
+    ap.add_argument("--batch-fp16", action="store_true",
+                    help="also time the batching form with f16 inner products")
     ap.add_argument("--grad-n", type=int, default=1 << 16,
                     help="points of the log-marginal-likelihood gradient (0 skips it)")
+    ap.add_argument("--budget-s", type=float, default=660.0,
+                    help="wall-clock seconds after which the remaining extra forms are skipped")
     ap.add_argument("--no-matern", dest="matern", action="store_false",
                     help="skip the Matern-kernel product and solves")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -67,7 +87,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-highd", dest="highd", action="store_false",
                     help="skip the high-dimensional product comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args(argv)
+    a = ap.parse_args(argv)
+    a.batch_forms = [("batched_fp32_inner", "fp32")] + ([("batched_fp16_inner", "fp16")] if a.batch_fp16 else [])
+    return a
 
 
 # ------------------------------------------------------------ distributed ---
@@ -269,6 +291,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ libkrr ---
+T_START = time.perf_counter()
+
+
+def progress(msg):
+    """One line on stderr per bench phase (the JSON line stays alone on stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - T_START:7.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
 def run_libkrr(args):
     import numpy as np
     import torch
@@ -297,6 +328,10 @@ def run_libkrr(args):
 
     ex2_rate, ffma_rate, ffma2_lanes = K.krr_measure_alu_peaks()
     fp32_lanes = max(ffma_rate, ffma2_lanes)
+    ex2_f16x2, ex2_bf16x2, mma_sync_flops = K.krr_measure_half_rates()
+    rates = {"ex2_f32_per_s": ex2_rate, "ex2_f16x2_values_per_s": ex2_f16x2,
+             "ex2_bf16x2_values_per_s": ex2_bf16x2, "fp32_lanes_per_s": fp32_lanes,
+             "mma_sync_m16n8k16_f16_flops_per_s": mma_sync_flops}
 
     barrier(world, dev)
     torch.cuda.synchronize(dev)
@@ -335,6 +370,7 @@ def run_libkrr(args):
     kernel_name = ("mvp_tcx_kernel (exponent on the tensor cores) + direct-form tail"
                    if tensor_exp else "mvp_f32_kernel")
 
+    progress(f"headline product: {value:.0f} Gpairs/s")
     # ---- 16 right-hand sides (one launch over all columns)
     Q16 = torch.from_numpy(inputs.mvp_problem(seed=rank + 7, N=MVP_N, d=MVP_D, m=16)["Q"].T.copy()).to(dev)
     Y16 = torch.empty_like(Q16)
@@ -358,6 +394,7 @@ def run_libkrr(args):
     m16_tc5_ms = e0.elapsed_time(e1)
     h5.close()
 
+    progress(f"16-column product: {m16_ms:.1f} ms (tcgen05 kernel {m16_tc5_ms:.1f} ms)")
     # ---- end to end through the C ABI with pinned host buffers
     Xh = torch.from_numpy(p["X"]).pin_memory()
     qh = torch.from_numpy(p["Q"]).pin_memory()
@@ -369,27 +406,6 @@ def run_libkrr(args):
         K.krr_kernel_mvp(Xh, qh, sigma, gamma, out=yh)  # copies in, product, copy out, sync
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     e2e_value = whole_job_rate(pairs, world, e2e_s)
-
-    # ---- FGMRES time to a 1e-6 relative residual: the plain FP32 form next
-    # to the precision, block (many right-hand sides) and batching forms
-    solve = {}
-    sp = inputs.small_problem(seed=rank)
-    solve["small_2000pt_2d"] = {"fgmres": solve_once(K, torch, sp, dev, stream, "fp32"),
-                                "cg": cg_once(K, torch, sp, dev, stream),
-                                "fcg": fcg_once(K, torch, sp, dev, stream)}
-    if args.solve_n > 0:
-        solve[f"mixture_{args.solve_n}pt_2d"] = mixture_forms(K, torch, inputs, args, rank, dev, stream)
-    if args.batch_probs > 0:
-        solve["batching_d8"] = batching_form(K, torch, inputs, args, rank, dev, stream)
-    grad = None
-    if args.grad_n > 0:
-        grad = gradient_form(K, torch, inputs, args, rank, dev, stream)
-    matern = None
-    if args.matern:
-        matern = matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
-    tuned = (autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream, kern_ms, m16_ms)
-             if args.autotune else None)
-    highd = highd_form(K, torch, rank, dev, ex2_rate) if args.highd else None
 
     # ---- FP64 oracle on the host cores (rank 0, one GPU only)
     cpu = None
@@ -404,6 +420,47 @@ def run_libkrr(args):
         sub = np.arange(0, nrows, 8)
         errors = precision_errors(K, X, q, y, sigma, gamma, p, rows[sub], ref[sub])
         cpu["solves_2000pt_2d"] = cpu_oracle_solves(inputs.small_problem(seed=0))
+
+    progress("end-to-end and CPU baseline done")
+    # ---- FGMRES time to a 1e-6 relative residual: the plain FP32 form next
+    # to the precision, block (many right-hand sides) and batching forms, the
+    # gradient, and the Matern / high-d / autotune extras.  They run on one
+    # GPU only (a multi-GPU run measures the product) and in this order while
+    # the wall-clock budget lasts; a skipped form is recorded as such.
+    solve, grad, matern, tuned, highd = {}, None, None, None, None
+    skipped = []
+    extras = world == 1
+
+    def budget_left(name):
+        el = time.perf_counter() - T_START
+        if el <= args.budget_s:
+            progress(f"{name} (at {el:.0f} s)")
+            return True
+        skipped.append(name)
+        return False
+
+    if extras:
+        sp = inputs.small_problem(seed=rank)
+        solve["small_2000pt_2d"] = {"fgmres": solve_once(K, torch, sp, dev, stream, "fp32"),
+                                    "cg": cg_once(K, torch, sp, dev, stream),
+                                    "fcg": fcg_once(K, torch, sp, dev, stream)}
+        if args.batch_probs > 0 and budget_left("batching_d8"):
+            solve["batching_d8"] = batching_form(K, torch, inputs, args, rank, dev, stream)
+        if args.precision_n > 0 and budget_left("precision_full"):
+            solve[f"precision_mixture_{args.precision_n}pt_2d"] = precision_full(K, torch, inputs, args,
+                                                                                  rank, dev, stream)
+        if args.grad_n > 0 and budget_left("mll_grad"):
+            grad = gradient_form(K, torch, inputs, args, rank, dev, stream)
+        if args.solve_n > 0 and budget_left("mixture_forms"):
+            solve[f"mixture_forms_{args.solve_n}pt_2d"] = mixture_forms(K, torch, inputs, args, rank, dev,
+                                                                        stream)
+        if args.highd and budget_left("highd"):
+            highd = highd_form(K, torch, rank, dev, ex2_rate)
+        if args.matern and budget_left("matern"):
+            matern = matern_form(K, torch, inputs, X, q, rank, dev, stream, ex2_rate, fp32_lanes)
+        if args.autotune and budget_left("autotune"):
+            tuned = autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream,
+                                  kern_ms, m16_ms)
 
     if rank == 0:
         line = {
@@ -429,6 +486,8 @@ def run_libkrr(args):
                         "kernel": "mma.sync (default)",
                         "tcgen05_ms": m16_tc5_ms},
             "fgmres": solve,
+            "skipped_for_wall_budget": skipped,
+            "rates": rates,
             "mll_grad": grad,
             "matern": matern,
             "autotune": tuned,
@@ -523,49 +582,91 @@ def fcg_once(K, torch, p, dev, stream):
             "inner": i["inner_iters"], "status": K.status_string(i["status"])}
 
 
+def mixture_opts(K, prec, cap, cycles=4, delta=1e-2):
+    """Solver settings of the precision form: delta = 10 gamma (Sec. 6), inner
+    tolerance 1e-2, restart 30, outer tolerance 1e-6, at most `cycles`
+    restart cycles (a form that stalls is reported unconverged, not run on)."""
+    return K.default_opts(delta=delta, inner_tol=1e-2, inner_maxit=cap, restart=30, max_cycles=cycles,
+                          inner_prec=prec)
+
+
+def precision_full(K, torch, inputs, args, rank, dev, stream):
+    """The precision-form configuration at full size: 262,144 points of the
+    16-component mixture (sigma 0.03, gamma 1e-3), b = smooth field plus
+    N(0, 0.01^2) noise, FGMRES with the truncated-CG preconditioner and
+    float32 inner products, to a true relative residual of 1e-6 (reported by
+    the library's accurate product; the tests recheck such solutions with the
+    FP64 oracle)."""
+    mp = inputs.mixture_problem(seed=rank, N=args.precision_n)
+    X = torch.from_numpy(mp["X"]).to(dev)
+    b = torch.from_numpy(mp["b"]).to(dev)
+    K.krr_fgmres_solve(X, b, mp["sigma"], mp["gamma"], opts=K.default_opts(max_cycles=1, inner_maxit=1))
+    (x, info), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+        X, b, mp["sigma"], mp["gamma"], opts=mixture_opts(K, "fp32", args.precision_cap, cycles=2)))
+    i = info[0]
+    return {"N": args.precision_n, "form": "plain FP32 inner, single right-hand side",
+            "delta": 1e-2, "inner_tol": 1e-2, "inner_cap": args.precision_cap,
+            "time_to_solution_ms": ms, "relres_true": i["relres_true"], "outer": i["outer_iters"],
+            "inner": i["inner_iters"], "status": K.status_string(i["status"])}
+
+
 def mixture_forms(K, torch, inputs, args, rank, dev, stream):
-    """The mixture cloud (kernel sigma 0.03, gamma 1e-3, delta 0.03, inner tol
-    1e-2, at most 200 inner steps, restart 30) with 16 right-hand sides (the
-    smooth field and 15 N(0,1) columns): per-RHS time to 1e-6 of the plain
-    float32 form (single-column solves of the first plain-cols columns), of the
-    half-precision inner form, and of 16-column lockstep block solves."""
+    """Every form on the mixture cloud at --solve-n points (kernel sigma 0.03,
+    gamma 1e-3, delta = 10 gamma, inner tol 1e-2, restart 30): the paper's
+    right-hand side b (smooth field plus noise) solved alone with float32
+    and f16 inner products, and 16 right-hand sides (b and 15 N(0,1)
+    columns) per RHS: single-column float32 solves of the first plain-cols
+    columns against 16-column lockstep blocks with float32 and f16 inner
+    products."""
     import numpy as np
     mp = inputs.mixture_problem(seed=rank, N=args.solve_n)
     rng = np.random.default_rng(100 + rank)
     B = np.stack([mp["b"]] + [rng.standard_normal(args.solve_n).astype(np.float32) for _ in range(15)])
     X = torch.from_numpy(mp["X"]).to(dev)
     Bd = torch.from_numpy(B).to(dev)
-    out = {"N": args.solve_n, "rhs": 16}
-
-    def opts(prec):
-        return K.default_opts(delta=0.03, inner_tol=1e-2, inner_maxit=200, restart=30, inner_prec=prec)
-
+    out = {"N": args.solve_n, "inner_cap": args.solve_cap}
+    cap = args.solve_cap
     K.krr_fgmres_solve(X, Bd[0].contiguous(), mp["sigma"], mp["gamma"],
                        opts=K.default_opts(max_cycles=1, inner_maxit=1))  # workspace
-    for form, prec in (("plain_fp32", "fp32"), ("single_fp16_inner", "fp16")):
-        ms_all, infos = [], []
-        for c in range(min(args.plain_cols, 16)):
-            (x, info), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
-                X, Bd[c].contiguous(), mp["sigma"], mp["gamma"], opts=opts(prec)))
-            ms_all.append(ms)
-            infos += info
-        out[form] = dict(per_rhs_ms=sum(ms_all) / len(ms_all), rhs_timed=len(ms_all), **_report(K, infos))
+    for prec, cyc in (("fp32", 4), ("fp16", 2)):
+        (x, info), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+            X, Bd[0].contiguous(), mp["sigma"], mp["gamma"], opts=mixture_opts(K, prec, cap, cyc)))
+        out[f"b_{prec}_inner"] = dict(time_to_solution_ms=ms, **_report(K, info))
+    ms_all, infos = [], []
+    for c in range(min(args.plain_cols, 16)):
+        (x, info), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+            X, Bd[c].contiguous(), mp["sigma"], mp["gamma"], opts=mixture_opts(K, "fp32", cap)))
+        ms_all.append(ms)
+        infos += info
+    out["plain_fp32"] = dict(per_rhs_ms=sum(ms_all) / len(ms_all), rhs_timed=len(ms_all), **_report(K, infos))
     for form, prec in (("block16_fp32", "fp32"), ("block16_fp16_inner", "fp16")):
         (x, infos), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
-            X, Bd, mp["sigma"], mp["gamma"], opts=opts(prec)))
+            X, Bd, mp["sigma"], mp["gamma"], opts=mixture_opts(K, prec, cap, cycles=3)))
         out[form] = dict(total_ms=ms, per_rhs_ms=ms / 16, **_report(K, infos))
     plain = out["plain_fp32"]["per_rhs_ms"]
-    for form in ("single_fp16_inner", "block16_fp32", "block16_fp16_inner"):
+    for form in ("block16_fp32", "block16_fp16_inner"):
         out[form]["speedup_vs_plain_fp32"] = plain / out[form]["per_rhs_ms"]
+    out["b_fp16_inner"]["speedup_vs_fp32_inner"] = (out["b_fp32_inner"]["time_to_solution_ms"] /
+                                                    out["b_fp16_inner"]["time_to_solution_ms"])
     return out
 
 
+def batch_opts(K, prec):
+    """Solver settings of the batching form: delta = 10 gamma_k (Sec. 6),
+    inner tolerance 1e-2, at most 400 inner steps, restart 30, at most 8
+    restart cycles."""
+    return K.default_opts(inner_tol=1e-2, inner_maxit=400, restart=30, max_cycles=8, inner_prec=prec)
+
+
 def batching_form(K, torch, inputs, args, rank, dev, stream, handle=None, plain=True):
-    """A subset of the batching workload (d = 8, N(0, I) points, sigma 1,
-    gamma log-uniform in [1e-4, 1e-1], 16 N(0,1) right-hand sides each, N
-    log-uniform in [1024, batch-nmax]): all problems in one batched call vs
-    the plain float32 form (single-column solves of 2 columns per problem,
-    per-RHS mean)."""
+    """The batching workload (d = 8, N(0, I) points, sigma 1, gamma
+    log-uniform in [1e-4, 1e-1], 16 N(0,1) right-hand sides each, N
+    log-uniform in [1024, batch-nmax]): all problems in one batched call
+    (float32 inner products by default; --batch-fp16 adds the f16-inner
+    call) against the plain float32 form: single-column
+    solves, one right-hand side of each problem of a seeded sample of
+    batch-plain problems; its per-RHS time is the sample mean, an unbiased
+    estimate of the mean over all problems."""
     import numpy as np
     bp = inputs.batch_problems(seed=rank, nprob=args.batch_probs, d=8, m=16, n_lo=1024,
                                n_hi=args.batch_nmax)
@@ -576,28 +677,37 @@ def batching_form(K, torch, inputs, args, rank, dev, stream, handle=None, plain=
                           B=torch.from_numpy(np.ascontiguousarray(pr["B"].T)).to(dev),
                           gamma=pr["gamma"],
                           Xsol=torch.empty((16, N), dtype=torch.float64, device=dev)))
+    nrhs = 16 * len(probs)
+    out = {"problems": len(probs), "N_min": int(min(p["X"].shape[0] for p in probs)),
+           "N_max": int(max(p["X"].shape[0] for p in probs)),
+           "pairs_per_sweep": float(sum(float(p["X"].shape[0]) ** 2 for p in probs)),
+           "rhs_per_problem": 16}
     first_ms = None
     if handle is not None:  # the first call tunes every product shape of the batch
         _, first_ms = _timed(torch, stream, lambda: K.krr_fgmres_solve_batched(
-            probs, d=8, sigma=bp["sigma"], m_rhs=16, handle=handle))
-    infos, ms = _timed(torch, stream, lambda: K.krr_fgmres_solve_batched(probs, d=8, sigma=bp["sigma"],
-                                                                         m_rhs=16, handle=handle))
-    out = {"N": [int(p["X"].shape[0]) for p in probs], "rhs_per_problem": 16,
-           "batched": dict(total_ms=ms, per_rhs_ms=ms / (16 * len(probs)), **_report(K, infos))}
-    if first_ms is not None:
-        out["batched"]["first_call_ms"] = first_ms
-    if not plain:
-        return out
-    tot, n, pinfos = 0.0, 0, []
-    for pr in probs:
-        for c in range(2):
-            (x, info), ms1 = _timed(torch, stream, lambda: K.krr_fgmres_solve(
-                pr["X"], pr["B"][c].contiguous(), bp["sigma"], pr["gamma"]))
-            tot += ms1
-            n += 1
-            pinfos += info
-    out["plain_fp32"] = dict(per_rhs_ms=tot / n, rhs_timed=n, **_report(K, pinfos))
-    out["batched"]["speedup_vs_plain_fp32"] = out["plain_fp32"]["per_rhs_ms"] / out["batched"]["per_rhs_ms"]
+            probs, d=8, sigma=bp["sigma"], m_rhs=16, opts=batch_opts(K, "fp16"), handle=handle))
+    for form, prec in args.batch_forms:
+        infos, ms = _timed(torch, stream, lambda: K.krr_fgmres_solve_batched(
+            probs, d=8, sigma=bp["sigma"], m_rhs=16, opts=batch_opts(K, prec), handle=handle))
+        out[form] = dict(total_ms=ms, per_rhs_ms=ms / nrhs, **_report(K, infos))
+        if first_ms is not None:
+            out[form]["first_call_ms"] = first_ms
+            first_ms = None
+        if not plain:
+            return out
+    rng = np.random.default_rng(500 + rank)
+    sample = sorted(rng.choice(len(probs), size=min(args.batch_plain, len(probs)), replace=False).tolist())
+    tot, pinfos = 0.0, []
+    for k in sample:
+        pr = probs[k]
+        (x, info), ms1 = _timed(torch, stream, lambda: K.krr_fgmres_solve(
+            pr["X"], pr["B"][0].contiguous(), bp["sigma"], pr["gamma"], opts=batch_opts(K, "fp32")))
+        tot += ms1
+        pinfos += info
+    out["plain_fp32"] = dict(per_rhs_ms=tot / len(sample), sampled_problems=sample,
+                             estimated_total_ms=tot / len(sample) * nrhs, **_report(K, pinfos))
+    for form, _ in args.batch_forms:
+        out[form]["speedup_vs_plain_fp32"] = out["plain_fp32"]["per_rhs_ms"] / out[form]["per_rhs_ms"]
     return out
 
 
@@ -608,8 +718,9 @@ def gradient_form(K, torch, inputs, args, rank, dev, stream):
     gp = inputs.gradient_problem(seed=rank, N=args.grad_n, d=4, probes=32)
     X = torch.from_numpy(gp["X"]).to(dev)
     y = torch.from_numpy(gp["y"]).to(dev)
+    opts = K.default_opts(inner_tol=1e-2, inner_maxit=400, restart=30, max_cycles=8)
     (gs, gg, gX, infos), ms = _timed(torch, stream, lambda: K.krr_mll_grad(
-        X, y, gp["sigma"], gp["gamma"], n_probes=32, seed=gp["seed"]))
+        X, y, gp["sigma"], gp["gamma"], n_probes=32, seed=gp["seed"], opts=opts))
     return dict(N=args.grad_n, d=4, probes=32, time_ms=ms, dlogsigma=gs, dloggamma=gg, **_report(K, infos))
 
 
@@ -683,8 +794,12 @@ def autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, st
     out = {"product_m1": {"model_kernel_ms": kern_ms, "tuned_kernel_ms": t1, "first_call_ms": tune1_ms},
            "product_m16": {"model_ms": m16_ms, "tuned_ms": t16, "first_call_ms": tune16_ms}}
     if args.batch_probs > 0:
-        out["batching_d8"] = batching_form(K, torch, inputs, args, rank, dev, stream, handle=h,
-                                           plain=False)
+        # a 4-problem subset (N <= 8192) of the batching workload: the first
+        # call tunes each branch's product shapes
+        sub = argparse.Namespace(**vars(args))
+        sub.batch_probs, sub.batch_nmax = 4, 8192
+        out["batching_subset_4x8192"] = batching_form(K, torch, inputs, sub, rank, dev, stream, handle=h,
+                                                      plain=False)
     h.close()
     return out
 

@@ -1,10 +1,21 @@
 // Helpers shared by the C-ABI translation units (defined in krr_api.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
 
 namespace krr {
+
+// NVTX range over an entry point (host side; shown by profilers that read
+// NVTX, free otherwise: the header-only NVTX v3 only forwards when a tool is
+// attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 krr_status set_error(Ctx& c, krr_status s, const char* fmt, ...);
 krr_status cuda_error(Ctx& c, cudaError_t e, const char* what);

@@ -332,6 +332,7 @@ krr_status krr_profile_read(krr_handle h, krr_profile* out) {
 
 krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float sigma, float gamma,
                           const float* Q, int m, float* Y, krr_precision prec, void* stream) {
+  NvtxRange nvtx_range("krr_kernel_mvp");
   if (!h) return KRR_ERR_INVALID_ARG;
   Ctx& c = h->ctx;
   const char* fn = "krr_kernel_mvp";
@@ -405,6 +406,7 @@ krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float 
 krr_status krr_kernel_mvp_rect(krr_handle h, const float* Xt, int64_t Nt, const float* Xs,
                                int64_t Ns, int d, float sigma, const float* Q, int m, float* Y,
                                krr_precision prec, void* stream) {
+  NvtxRange nvtx_range("krr_kernel_mvp_rect");
   if (!h) return KRR_ERR_INVALID_ARG;
   Ctx& c = h->ctx;
   const char* fn = "krr_kernel_mvp_rect";

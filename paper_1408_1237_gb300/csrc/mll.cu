@@ -319,6 +319,7 @@ extern "C" krr_status krr_mll_grad(krr_handle h, const float* X, int64_t N, int 
                                    const krr_fgmres_opts* opts, double* dlogsigma,
                                    double* dloggamma, float* dX, krr_solve_info* info,
                                    void* stream) {
+  NvtxRange nvtx_range("krr_mll_grad");
   if (!h) return KRR_ERR_INVALID_ARG;
   Ctx& c = h->ctx;
   const char* fn = "krr_mll_grad";

@@ -909,26 +909,30 @@ __global__ void __launch_bounds__(32 * HighD<D>::WARPS) mvp_tch_kernel(const TcP
 // operands where the tcgen05 datapath wants them.
 //
 // One CTA = 128 targets (half of an expanded-form super-block) = the 128
-// TMEM lanes, 8 warps: warp w serves lanes 32 (w % 4) .. + 31 and, of every
-// chunk of 64 sources, the 32 sources of its warpgroup w / 4.  Per source
-// tile (256 sources) the CTA transforms the raw tile into f16 K-major
-// operands in shared memory (source K-vectors B and the weight columns Q, hi
-// and lo), then for each chunk of 64 sources:
-//   1. one elected thread issues S = A B^T (M = 128, N = 64, K = 16 per
-//      instruction) into one of three TMEM buffers (fp32); the next chunk's
-//      S is issued as soon as this one is complete, so the tensor cores work
-//      while the threads exponentiate;
-//   2. every thread reads its 32 values of S (tcgen05.ld), forms P = 2^S
-//      with MUFU.EX2 and writes P as f16 (hi, and lo when split) over the
-//      same 32 TMEM columns (tcgen05.st);
+// TMEM lanes, 9 warps: warp 8 issues the MMAs (one elected thread); warps 0-3
+// and 4-7 form two chunk groups, each covering the 128 lanes (warp w serves
+// lanes 32 (w % 4) .. + 31), that take alternate chunks of 64 sources.  Per
+// source tile (256 sources) the groups build the f16 K-major source operand B
+// in shared memory (half each), the weight columns Q arrive pre-split (hi,
+// lo) by bulk copies, and for each chunk:
+//   1. the elected thread issues S = A B^T (M = 128, N = 64, K = 16 per
+//      instruction) into one of three TMEM buffers (fp32), two chunks ahead
+//      of the P Q in hand, so the tensor cores work while the threads
+//      exponentiate;
+//   2. the chunk's group reads S (tcgen05.ld, 32 columns at a time), forms
+//      P = 2^S with MUFU.EX2 and writes P as f16 (hi, and lo when split) over
+//      the same TMEM columns (tcgen05.st); the other group meanwhile works on
+//      its own chunk;
 //   3. the elected thread issues Y += P Q with P read from TMEM (M = 128,
 //      N = 16, K = 16 per instruction: Ph Qh + Pl Qh + Ph Ql when split).
-// Each S buffer has its own mbarrier (a commit per chunk), Y its own; every
-// barrier phase is awaited by all threads before the barrier is committed
-// again.  Y lives in TMEM for a tile and is folded into float32 Kahan sums
-// per tile.  Shared operands use the canonical no-swizzle K-major layout:
-// 8-row x 16-byte core matrices, adjacent along K 128 bytes apart (leading
-// byte offset), 8-row groups KC*128 bytes apart (stride byte offset).
+// Each S buffer has its own mbarriers (a commit per chunk, the group's
+// arrivals), Y its own; every barrier phase is awaited before the barrier can
+// complete again.  Y lives in TMEM for a tile (two buffers by tile parity)
+// and is folded into float32 Kahan sums one tile later, after which the
+// tile's TMA stage (three stages) is refilled.  Shared operands use the
+// canonical no-swizzle K-major layout: 8-row x 16-byte core matrices,
+// adjacent along K 128 bytes apart (leading byte offset), 8-row groups
+// KC*128 bytes apart (stride byte offset).
 namespace umma {
 
 constexpr int ROWS = 128;       // targets per CTA (MMA M)
@@ -938,6 +942,8 @@ constexpr int NBUF = 3;         // S/P buffers of NC columns
 constexpr int YN = 16;          // Y columns (N of the P Q MMA)
 constexpr int TMEM_COLS = 256;  // S/P buffers at 0, 64, 128; Y buffers at 192, 208
 constexpr int SMEM_FLOOR = 80 * 1024;  // at most two CTAs per SM (TMEM holds two)
+constexpr int URS = 3;          // raw TMA stages (a tile's stage is refilled one tile after use)
+constexpr int GROUP_WARPS = 4;  // compute warps per chunk group (all 128 TMEM lanes)
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo) {
   return ((uint64_t)((saddr >> 4) & 0x3FFF)) | ((uint64_t)(128 >> 4) << 16) |
@@ -1015,7 +1021,7 @@ constexpr uint32_t stage_bytes(bool split) {
 template <int D>
 constexpr size_t smem_bytes(bool split) {
   using L = ExpLayout<D>;
-  const size_t need = RS * (size_t)stage_bytes<D>(split) + 2 * ROWS * L::KV + 2 * (2 * TS * L::KV);
+  const size_t need = URS * (size_t)stage_bytes<D>(split) + 2 * ROWS * L::KV + 2 * (2 * TS * L::KV);
   return need > SMEM_FLOOR ? need : SMEM_FLOOR;
 }
 
@@ -1038,9 +1044,9 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
   constexpr int AHEAD = NBUF - 1;    // exponent MMAs issued ahead of the P Q in hand
   constexpr uint32_t BBYTES = 2 * TS * L::KV;  // one B operand buffer
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[RS];        // TMA stages
+  __shared__ __align__(8) uint64_t bars[URS];       // TMA stages
   __shared__ __align__(8) uint64_t sfull[NBUF];     // S of buffer b complete (commit)
-  __shared__ __align__(8) uint64_t pfull[NBUF];     // P of buffer b written (compute warps)
+  __shared__ __align__(8) uint64_t pfull[NBUF];     // P of buffer b written (one chunk group)
   __shared__ __align__(8) uint64_t pdone[NBUF];     // P Q reading buffer b complete (commit)
   __shared__ __align__(8) uint64_t bready[2];       // B operand buffer written (compute warps)
   __shared__ __align__(8) uint64_t yfull[2];        // Y buffer complete for its tile (commit)
@@ -1050,15 +1056,15 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool mma_warp = warp == NCW;
-  const int wg = (warp >> 2) & 1;  // compute warpgroup: columns 32 wg .. of each chunk
+  const int grp = (warp >> 2) & 1;  // chunk group of a compute warp: chunks c with c % 2 == grp
   if (p.active && *p.active == 0) return;
   const int64_t nexp = *p.tn_exp;
   const int64_t sb_slot = blockIdx.x >> 1;
   if (sb_slot >= nexp) return;
   constexpr uint32_t SBYTES = stage_bytes<D>(SPLIT);
   constexpr uint32_t QTILE = 2 * YN * TS;  // bytes of one weight tile
-  unsigned char* stages = smem_raw;        // RS stages: coordinates, Qh, Ql
-  unsigned char* sA = smem_raw + RS * SBYTES;
+  unsigned char* stages = smem_raw;        // URS stages: coordinates, Qh, Ql
+  unsigned char* sA = smem_raw + URS * SBYTES;
   unsigned char* sB = sA + 2 * ROWS * L::KV;  // two B buffers
 
   const int64_t blk = p.torder[sb_slot];
@@ -1096,10 +1102,10 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
   }
   if (tid == 0) {
     abort_flag = 0;
-    for (int st = 0; st < RS; ++st) mbar_init(&bars[st], 1);
+    for (int st = 0; st < URS; ++st) mbar_init(&bars[st], 1);
     for (int b = 0; b < NBUF; ++b) {
       mbar_init(&sfull[b], 1);
-      mbar_init(&pfull[b], NCW);
+      mbar_init(&pfull[b], GROUP_WARPS);
       mbar_init(&pdone[b], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -1125,7 +1131,7 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
   const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
 
   auto issue = [&](int r) {
-    const int stage = r % RS;
+    const int stage = r % URS;
     const int64_t tile = t_begin + r;
     unsigned char* dst = stages + stage * SBYTES;
     mbar_arrive_expect_tx(&bars[stage], SBYTES);
@@ -1191,7 +1197,7 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
         }
         if (!ok) break;
         fence_after();
-        const uint32_t qh_addr = smem_addr(stages + (r % RS) * SBYTES + D * TS * 4);
+        const uint32_t qh_addr = smem_addr(stages + (r % URS) * SBYTES + D * TS * 4);
         const uint32_t ql_addr = qh_addr + QTILE;
         const uint32_t sbuf = tmem + (uint32_t)(b * NC);
         const uint32_t yd = tmem + y_col + (uint32_t)(YN * yb);
@@ -1220,19 +1226,25 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
     }
     __syncwarp();  // the idle lanes wait for the issuing lane before the block barrier
   } else {
-    // ================= compute warps: exponentials, the B operands, Y folds
+    // ================= compute warps: two groups of four (warps 0-3 and
+    // 4-7, each covering the 128 TMEM lanes) take alternate chunks, a whole
+    // chunk of 64 sources each, so that one group exponentiates while the
+    // other waits on tensor memory.  After its first chunk of tile r a group
+    // folds its half of tile r - 1's Y (that tile's MMAs are complete by then
+    // or soon after) and builds its half of tile r + 1's B operand (one source
+    // per thread); the stage of tile r - 1 is then refilled with tile
+    // r - 1 + URS, one tile ahead of its use.
     if (tid == 0)
-      for (; issued < min(RS, nt); ++issued) issue(issued);
-    constexpr int YW = YN / 2;  // Y columns per warpgroup
+      for (; issued < min(URS, nt); ++issued) issue(issued);
+    constexpr int YW = YN / 2;  // Y columns folded per group
     float Ssum[YW], Scomp[YW];
 #pragma unroll
     for (int c = 0; c < YW; ++c) Ssum[c] = Scomp[c] = 0.f;
-    uint32_t n_sf[NBUF] = {0, 0, 0}, n_yfl[2] = {0, 0};
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
     // tile r's B operand into buffer r & 1 (its stage awaited first)
     auto make_b = [&](int r) -> bool {
-      if (!__all_sync(0xffffffffu, wait(&bars[r % RS], (r / RS) & 1))) return false;
-      const float* rs = reinterpret_cast<const float*>(stages + (r % RS) * SBYTES);
+      if (!__all_sync(0xffffffffu, wait(&bars[r % URS], (r / URS) & 1))) return false;
+      const float* rs = reinterpret_cast<const float*>(stages + (r % URS) * SBYTES);
       unsigned char* bdst = sB + (r & 1) * BBYTES;
       const int j = tid;  // one source per thread: its K-vector as 16-byte rows
       float bh[W], bl[W];
@@ -1265,71 +1277,75 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
       if (lane == 0) mbar_arrive1(&bready[r & 1]);
       return true;
     };
-    bool ok = nt > 0 ? make_b(0) : true;
-    for (int r = 0; r < nt && ok; ++r) {
-      for (int q = 0; q < CPT && ok; ++q) {
-        const int c = r * CPT + q, b = c % NBUF;
-        ok = __all_sync(0xffffffffu, wait(&sfull[b], n_sf[b] & 1));
-        ++n_sf[b];
-        if (!ok) break;
-        fence_after();
-        // P = 2^S over this warpgroup's 32 columns: hi in the first 16, lo in
-        // the last 16 (each thread reads its values before overwriting them)
-        const uint32_t cols = tmem + (uint32_t)(b * NC) + lanes + (uint32_t)(32 * wg);
-        uint32_t v[32];
-        ld32(cols, v);
-        wait_ld();
-        uint32_t ph[16], pl[16];
-#pragma unroll
-        for (int w = 0; w < 16; ++w) {
-          const float p0 = ex2(__uint_as_float(v[2 * w])), p1 = ex2(__uint_as_float(v[2 * w + 1]));
-          ph[w] = H::pack(p0, p1);
-          if (SPLIT) {
-            const float2 hv = H::unpack(ph[w]);
-            pl[w] = H::pack(p0 - hv.x, p1 - hv.y);
-          }
-        }
-        st16(cols, ph);
-        if (SPLIT) st16(cols + 16u, pl);
-        wait_st();
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive1(&pfull[b]);
-      }
-      if (!ok) break;
-      // the next tile's B (its buffer was last read by tile r - 1's exponent
-      // MMAs, complete since tile r - 1's Y was awaited)
-      if (r + 1 < nt) {
-        ok = make_b(r + 1);
-        if (!ok) break;
-      }
-      // ---- the tile's Y: fold into Kahan sums, then hand Y and the stage back
+    // tile r's Y (this group's YW columns) into the Kahan sums; Y buffer r & 1
+    // is handed back and, every MMA of tile r being complete, its stage refilled
+    auto fold_y = [&](int r) -> bool {
       const int yb = r & 1;
-      ok = __all_sync(0xffffffffu, wait(&yfull[yb], n_yfl[yb] & 1));
-      ++n_yfl[yb];
-      if (!ok) break;
+      if (!__all_sync(0xffffffffu, wait(&yfull[yb], (r >> 1) & 1))) return false;
       fence_after();
       uint32_t yv[8];
-      ld8(tmem + y_col + (uint32_t)(YN * yb) + lanes + (uint32_t)(YW * wg), yv);
+      ld8(tmem + y_col + (uint32_t)(YN * yb) + lanes + (uint32_t)(YW * grp), yv);
       wait_ld();
 #pragma unroll
       for (int c = 0; c < YW; ++c) kahan_add(Ssum[c], Scomp[c], __uint_as_float(yv[c]));
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive1(&yfree[yb]);
-      if (tid == 0 && r + RS < nt) {  // every MMA of tile r is complete: its stage is free
+      if (tid == 0 && r + URS < nt) {
         fence_proxy_async_smem();
-        issue(r + RS);
+        issue(r + URS);
         ++issued;
       }
+      return true;
+    };
+    bool ok = nt > 0 ? make_b(0) : true;
+    for (int r = 0; r < nt && ok; ++r) {
+      for (int h2 = 0; h2 < CPT / 2 && ok; ++h2) {
+        const int c = r * CPT + grp + 2 * h2, b = c % NBUF;
+        ok = __all_sync(0xffffffffu, wait(&sfull[b], (c / NBUF) & 1));
+        if (!ok) break;
+        fence_after();
+        // P = 2^S over the chunk's 64 columns, 32 at a time: hi in the first
+        // 16 columns of each half, lo in the last 16 (each thread reads its
+        // values before overwriting them); the second half's load overlaps the
+        // first half's store
+#pragma unroll 1
+        for (int hf = 0; hf < 2; ++hf) {
+          const uint32_t cols = tmem + (uint32_t)(b * NC) + lanes + (uint32_t)(32 * hf);
+          uint32_t v[32];
+          ld32(cols, v);
+          wait_ld();
+          uint32_t ph[16], pl[16];
+#pragma unroll
+          for (int w = 0; w < 16; ++w) {
+            const float p0 = ex2(__uint_as_float(v[2 * w])), p1 = ex2(__uint_as_float(v[2 * w + 1]));
+            ph[w] = H::pack(p0, p1);
+            if (SPLIT) {
+              const float2 hv = H::unpack(ph[w]);
+              pl[w] = H::pack(p0 - hv.x, p1 - hv.y);
+            }
+          }
+          st16(cols, ph);
+          if (SPLIT) st16(cols + 16u, pl);
+        }
+        wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&pfull[b]);
+        if (h2 == 0) {
+          if (r >= 1 && !(ok = fold_y(r - 1))) break;
+          if (r + 1 < nt && !(ok = make_b(r + 1))) break;
+        }
+      }
     }
+    if (ok && nt > 0) ok = fold_y(nt - 1);
     if (!ok) {
       abort_flag = 1;
       if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
     } else if (i < p.Nt_pad) {
 #pragma unroll
       for (int c = 0; c < YW; ++c) {
-        const int col = YW * wg + c;
+        const int col = YW * grp + c;
         if (col < p.m) p.part[((int64_t)blockIdx.y * p.m + col) * p.Nt_pad + i] = (double)Ssum[c] - (double)Scomp[c];
       }
     }
@@ -1338,7 +1354,7 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
   if (abort_flag) {
     // drain (bounded): copies in flight before the shared memory is released
     if (tid == 0)
-      for (int rr = 0; rr < issued; ++rr) mbar_wait_bounded(&bars[rr % RS], (rr / RS) & 1);
+      for (int rr = 0; rr < issued; ++rr) mbar_wait_bounded(&bars[rr % URS], (rr / URS) & 1);
     __syncthreads();
   }
   fence_before();

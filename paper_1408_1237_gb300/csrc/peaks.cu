@@ -121,14 +121,21 @@ __global__ void __launch_bounds__(256) ex2_bf16x2_rate_kernel(float* out, float 
   out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
 }
 
-// Four independent accumulators per warp, each m16n8k16 (f16 in, f32 out).
+// Four independent accumulator chains per warp, each m16n8k16 (f16 in, f32
+// out).  Every chain starts from its own accumulator and multiplies its own
+// B operand, so no two MMAs are the same computation (identical chains could
+// be merged by the compiler and would overstate the rate).
 constexpr int MMA_CHAINS = 4;
 __global__ void __launch_bounds__(256) mma_sync_rate_kernel(float* out, float seed) {
   float d[MMA_CHAINS][4];
+  uint32_t b[MMA_CHAINS];
 #pragma unroll
-  for (int a = 0; a < MMA_CHAINS; ++a)
+  for (int a = 0; a < MMA_CHAINS; ++a) {
 #pragma unroll
-    for (int b = 0; b < 4; ++b) d[a][b] = 0.f;
+    for (int e = 0; e < 4; ++e) d[a][e] = seed * (float)(a + 1) + 1e-3f * (float)(e + threadIdx.x);
+    __half2 hb = __floats2half2_rn(0.25f * (a + 1), -0.125f * (a + 1));
+    b[a] = *reinterpret_cast<uint32_t*>(&hb);
+  }
   __half2 h = __floats2half2_rn(seed, 0.5f * seed);
   const uint32_t v = *reinterpret_cast<uint32_t*>(&h);
   for (int it = 0; it < ITERS; ++it) {
@@ -138,13 +145,13 @@ __global__ void __launch_bounds__(256) mma_sync_rate_kernel(float* out, float se
           "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
           "{%8,%9}, {%0,%1,%2,%3};"
           : "+f"(d[a][0]), "+f"(d[a][1]), "+f"(d[a][2]), "+f"(d[a][3])
-          : "r"(v), "r"(v), "r"(v), "r"(v), "r"(v), "r"(v));
+          : "r"(v), "r"(v), "r"(v), "r"(v), "r"(b[a]), "r"(b[a]));
   }
   float s = 0.f;
 #pragma unroll
   for (int a = 0; a < MMA_CHAINS; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) s += d[a][b];
+    for (int e = 0; e < 4; ++e) s += d[a][e];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
