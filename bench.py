@@ -43,9 +43,9 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "af3421004812d11340dfbd8dc8ff17ecb360f609",
-                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "cc922b230208a1c66336969f0d0101d458166d4c"},
-               "bytes": 22775808 + 92288000 + 17172736 + 0}
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "8db8257c9045d9e69c589b4c8d7ba129e5a73af9",
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "da937f5a3005504548b95ee054bdc697fdaf5412"},
+               "bytes": 22762752 + 92209152 + 17047040 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 
@@ -430,6 +430,7 @@ def run_libkrr(args):
     solve, grad, matern, tuned, highd = {}, None, None, None, None
     skipped = []
     extras = world == 1
+    sharded = sharded_product(K, torch, inputs, rank, world, dev, stream) if world > 1 else None
 
     def budget_left(name):
         el = time.perf_counter() - T_START
@@ -492,6 +493,7 @@ def run_libkrr(args):
             "matern": matern,
             "autotune": tuned,
             "highd": highd,
+            "sharded_product": sharded,
             "cpu_baseline": cpu,
             "precision_errors": errors,
         }
@@ -582,6 +584,30 @@ def fcg_once(K, torch, p, dev, stream):
             "inner": i["inner_iters"], "status": K.status_string(i["status"])}
 
 
+def sharded_product(K, torch, inputs, rank, world, dev, stream, reps=3):
+    """On N > 1 GPUs: ONE 2^20-point product (the headline problem, seed 0 on
+    every rank) with its target rows split over the ranks, each rank summing
+    N^2 / world pairs and a sum all-reduce (NCCL) assembling y on every rank
+    (paper_1408_1237_gb300/distributed.py).  Strong scaling: the reported
+    rate is N^2 pairs over the slowest rank's time per product, collective
+    included."""
+    from paper_1408_1237_gb300 import distributed
+    p = inputs.mvp_problem(seed=0, N=MVP_N, d=MVP_D)
+    X = torch.from_numpy(p["X"]).to(dev)
+    q = torch.from_numpy(p["Q"]).to(dev)
+    distributed.sharded_kernel_mvp(X, q, p["sigma"], p["gamma"])
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        distributed.sharded_kernel_mvp(X, q, p["sigma"], p["gamma"])
+    torch.cuda.synchronize(dev)
+    t = max_over_ranks((time.perf_counter() - t0) / reps, world, dev)
+    return {"ranks": world, "ms_per_product": t * 1e3,
+            "Gpairs_per_s": float(MVP_N) * MVP_N / t / 1e9, "scaling": "strong",
+            "collective_bytes_per_rank": distributed.collective_bytes_per_rank(MVP_N, 1, world)}
+
+
 def mixture_opts(K, prec, cap, cycles=4, delta=1e-2):
     """Solver settings of the precision form: delta = 10 gamma (Sec. 6), inner
     tolerance 1e-2, restart 30, outer tolerance 1e-6, at most `cycles`
@@ -641,7 +667,7 @@ def mixture_forms(K, torch, inputs, args, rank, dev, stream):
     out["plain_fp32"] = dict(per_rhs_ms=sum(ms_all) / len(ms_all), rhs_timed=len(ms_all), **_report(K, infos))
     for form, prec in (("block16_fp32", "fp32"), ("block16_fp16_inner", "fp16")):
         (x, infos), ms = _timed(torch, stream, lambda: K.krr_fgmres_solve(
-            X, Bd, mp["sigma"], mp["gamma"], opts=mixture_opts(K, prec, cap, cycles=3)))
+            X, Bd, mp["sigma"], mp["gamma"], opts=mixture_opts(K, prec, cap, cycles=3 if prec == "fp32" else 2)))
         out[form] = dict(total_ms=ms, per_rhs_ms=ms / 16, **_report(K, infos))
     plain = out["plain_fp32"]["per_rhs_ms"]
     for form in ("block16_fp32", "block16_fp16_inner"):
@@ -718,9 +744,8 @@ def gradient_form(K, torch, inputs, args, rank, dev, stream):
     gp = inputs.gradient_problem(seed=rank, N=args.grad_n, d=4, probes=32)
     X = torch.from_numpy(gp["X"]).to(dev)
     y = torch.from_numpy(gp["y"]).to(dev)
-    opts = K.default_opts(inner_tol=1e-2, inner_maxit=400, restart=30, max_cycles=8)
     (gs, gg, gX, infos), ms = _timed(torch, stream, lambda: K.krr_mll_grad(
-        X, y, gp["sigma"], gp["gamma"], n_probes=32, seed=gp["seed"], opts=opts))
+        X, y, gp["sigma"], gp["gamma"], n_probes=32, seed=gp["seed"]))
     return dict(N=args.grad_n, d=4, probes=32, time_ms=ms, dlogsigma=gs, dloggamma=gg, **_report(K, infos))
 
 

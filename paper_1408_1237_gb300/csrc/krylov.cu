@@ -451,8 +451,10 @@ __global__ void restart_check_kernel(KState* S0, int ncols, Group* G, Cond rc, d
     S->relres_true = S->bnorm > 0.0 ? beta / S->bnorm : 0.0;
     bool more = S->bnorm > 0.0 && S->relres_true > tol_stop && isfinite(beta);
     if (more && S->cycles >= S->max_cycles) {
+      // out of cycles: converged if the true residual meets the tolerance
+      // itself (tol_stop only leaves a margin while there are cycles left)
       more = false;
-      S->status = KRR_NOT_CONVERGED;
+      if (S->relres_true > S->tol) S->status = KRR_NOT_CONVERGED;
     }
     if (!isfinite(beta)) S->status = KRR_ERR_NONFINITE;
     S->restart_cont = more ? 1 : 0;
