@@ -149,14 +149,24 @@ typedef enum {
      * length scale h.  krr_mll_grad supports the Gaussian only and returns
      * KRR_ERR_UNIMPLEMENTED otherwise. */
     KRR_OPT_KERNEL = 2,
-    /* value != 0: autotune the source split of every product (the range of
-     * source tiles one CTA sums, i.e. how finely a product is spread over
-     * the SMs).  The first product of each shape (sizes, columns, precision,
-     * kernel family) on this handle, outside a CUDA-graph capture, times
-     * the real launch at 1/4 to 4 times the modelled split count on scratch
-     * weights (a few launches; waits for them) and keeps the fastest for
-     * later products of that shape.  Results stay within the same error
-     * bars; the summation grouping, hence the last bits, may differ. */
+    /* value != 0: autotune the kernel variant and the source split of
+     * every product.  The first product of each shape (sizes, columns,
+     * precision, kernel family) on this handle, outside a CUDA-graph
+     * capture, times the real launch on scratch weights (a few launches per
+     * candidate; waits for them):
+     *  - first the kernel variants of the shape at the modelled split:
+     *    multi-column Gaussian products up to 8 dimensions try the mma.sync
+     *    and tcgen05 kernels for compact target blocks and the tensor-core
+     *    and CUDA-core weighted sums for direct-form blocks (the settings of
+     *    KRR_OPT_TCGEN05 and KRR_OPT_DIRECT_TENSOR); single-column float32
+     *    products that would take the tensor-core exponent path also try
+     *    the packed CUDA-core kernel;
+     *  - then the source split of the fastest variant (the range of source
+     *    tiles one CTA sums) at 1/4 to 4 times the modelled split count.
+     * The handle's own settings win unless a candidate is 2% faster; the
+     * pick is kept for later products of that shape.  Results stay within
+     * the same error bars; the summation grouping, hence the last bits, may
+     * differ. */
     KRR_OPT_AUTOTUNE = 3,
     /* Target-row shard emulation (the row partition a multi-GPU product
      * would use, run on one GPU): with SHARD_COUNT = P > 1, krr_kernel_mvp
@@ -179,10 +189,18 @@ typedef enum {
     /* value != 0 (default): multi-column products (m >= 2, block solves,
      * the gradient's solves) up to 8 dimensions evaluate the kernel values of
      * their direct-form (non-compact) target blocks on the CUDA cores and run
-     * the weighted sum P Q on the tensor cores (split f16 for KRR_FP32,
+     * the weighted sum P Q on the tensor cores (tf32 hi/lo split for KRR_FP32,
      * single f16 / bf16 for reduced precision); 0: the all-CUDA-core kernel
      * (one FMA per pair and column).  Same results to the float32 bar. */
-    KRR_OPT_DIRECT_TENSOR = 7
+    KRR_OPT_DIRECT_TENSOR = 7,
+    /* value 0 to 3: in single-column float32 products up to 8 dimensions
+     * that take the tensor-core exponent kernel, `value` of every 8 pair
+     * exponentials 2^E (Eq. 2) are evaluated on the FP32 pipe (range
+     * reduction to [-1/2, 1/2] and a degree-5 polynomial, relative error
+     * below 1.7e-7) instead of the special-function unit, which otherwise
+     * bounds the kernel.  Same results to the float32 bar.  Other values:
+     * KRR_ERR_INVALID_ARG. */
+    KRR_OPT_EXP_POLY = 8
 } krr_option;
 
 /* Kernel functions (KRR_OPT_KERNEL). */

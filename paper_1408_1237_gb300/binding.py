@@ -387,6 +387,7 @@ KRR_OPT_AUTOTUNE = 3
 KRR_OPT_SHARD_COUNT, KRR_OPT_SHARD_INDEX = 4, 5
 KRR_OPT_HIGHD_TCGEN05 = 6
 KRR_OPT_DIRECT_TENSOR = 7
+KRR_OPT_EXP_POLY = 8
 KRR_KERNEL_GAUSSIAN, KRR_KERNEL_MATERN32 = 0, 1
 
 
@@ -395,7 +396,8 @@ def krr_set_option(option, value, handle=None):
     products on the tcgen05 / tensor-memory kernel; KRR_OPT_KERNEL: the
     kernel function, KRR_KERNEL_GAUSSIAN or KRR_KERNEL_MATERN32, whose length
     scale h is then passed as sigma; KRR_OPT_AUTOTUNE: time the products'
-    source splits on first use of each shape and keep the fastest)."""
+    kernel variants and source splits on first use of each shape and keep
+    the fastest; the others as documented in include/libkrr.h)."""
     h = handle or default_handle()
     h.check(lib().krr_set_option(h.h, int(option), int(value)))
 

@@ -112,6 +112,9 @@ struct Ctx {
   // kernel values on the CUDA cores, the weighted sum on the tensor cores
   // (mvp_dirtc_kernel); false: the all-CUDA-core kernel mvp_dirm_kernel
   bool direct_tensor = true;
+  // exponentials of the single-column tensor-exponent kernel (mvp_tcx_kernel)
+  // taken on the FP32 pipe by polynomial: exp_poly of every 8 (0 to 3)
+  int exp_poly = 0;
   // kernel function of every product and solve (KRR_KERNEL_*, krr_set_option)
   int kernel_family = 0;
   // autotuning of the products' source splits (KRR_OPT_AUTOTUNE): the first
@@ -128,6 +131,9 @@ struct Ctx {
   int prod_depth = 0;
   double split_scale = 1.0;
   std::unordered_map<std::string, double> tune_cache;
+  // the kernel variant the autotuner picked per product shape (TuneVariant
+  // bits; absent: the handle's own settings)
+  std::unordered_map<std::string, int> tune_variant;
   // profiling of the fast product kernel (krr_profile_enable / _read)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, stop
@@ -160,6 +166,40 @@ struct TuneScope {
   ~TuneScope() {
     c.split_scale = old;
     --c.prod_depth;
+  }
+};
+// Kernel variants of a product shape (KRR_OPT_AUTOTUNE picks one per shape):
+// which kernel, hence which CTA shape and targets per thread, carries each
+// kind of target block.
+enum TuneVariant : int {
+  TV_TCGEN05 = 1,        // compact blocks of multi-column products: tcgen05 kernel (128-target CTAs)
+                         // instead of mma.sync (256-target CTAs)
+  TV_DIRECT_TENSOR = 2,  // direct-form blocks of multi-column products: tensor-core P Q (512-thread
+                         // CTAs) instead of one target per thread on the CUDA cores
+  TV_TENSOR_EXP = 4,     // single-column float32 products may take the tensor-core exponent path
+                         // (128-thread CTAs per super-block) instead of the packed CUDA-core kernel
+};
+inline int current_variant(const Ctx& c) {
+  return (c.use_tcgen05 ? TV_TCGEN05 : 0) | (c.direct_tensor ? TV_DIRECT_TENSOR : 0) |
+         (c.allow_tcx ? TV_TENSOR_EXP : 0);
+}
+// Applies the tuned variant of a shape for one product entry point (and puts
+// the handle's settings back after it).
+struct VariantScope {
+  Ctx& c;
+  bool tc5, dt, tcx;
+  VariantScope(Ctx& cc, const std::string& key)
+      : c(cc), tc5(cc.use_tcgen05), dt(cc.direct_tensor), tcx(cc.allow_tcx) {
+    const auto it = c.tune_variant.find(key);
+    if (it == c.tune_variant.end()) return;
+    c.use_tcgen05 = (it->second & TV_TCGEN05) != 0;
+    c.direct_tensor = (it->second & TV_DIRECT_TENSOR) != 0;
+    c.allow_tcx = tcx && (it->second & TV_TENSOR_EXP) != 0;  // never where the handle forbids it
+  }
+  ~VariantScope() {
+    c.use_tcgen05 = tc5;
+    c.direct_tensor = dt;
+    c.allow_tcx = tcx;
   }
 };
 // Split scales the tuner tries, the modelled one first.

@@ -845,11 +845,12 @@ int route_splits(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, 
 }
 
 // The autotuner of the fast products: times the real launch of this route
-// (scratch zero weights; the instruction stream does not depend on them) at
-// each split scale of TUNE_SCALES, best of two after a warm-up, and keeps
-// the fastest in c.tune_cache (the modelled split unless another is 2%
-// faster).  Candidates whose partial sums would exceed TUNE_MAX_BYTES are
-// skipped.
+// (scratch zero weights; the instruction stream does not depend on them),
+// best of two after a warm-up, first for each kernel variant of the shape
+// (kept in c.tune_variant), then for that variant at each split scale of
+// TUNE_SCALES (kept in c.tune_cache; the modelled split unless another is 2%
+// faster).  Split candidates whose partial sums would exceed TUNE_MAX_BYTES
+// are skipped.
 cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, krr_precision prec,
                          cudaStream_t st, const std::string& key) {
   struct Restore {
@@ -873,34 +874,71 @@ cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m
     cudaEventDestroy(ev[0]);
     return e;
   }
+  MvpOut o;
+  o.out_f = (float*)yv;
+  const bool single = m == 1 && prec == KRR_FP32;
+  auto run = [&]() {
+    return single ? mvp_launch(c, Tp, Sp, (const float*)qv, nullptr, 0.f, prec, o, st)
+                  : mvp_multi_launch(c, Tp, Sp, (const float*)qv, m, nullptr, 0.f, prec, o, st);
+  };
+  // one candidate: warm-up (workspace and attributes), then the best of two
+  auto time_it = [&](float& ms) -> cudaError_t {
+    cudaError_t ee = run();
+    ms = 1e30f;
+    for (int rep = 0; rep < 2 && !ee; ++rep) {
+      cudaEventRecord(ev[0], st);
+      ee = run();
+      cudaEventRecord(ev[1], st);
+      if (!ee) ee = cudaEventSynchronize(ev[1]);
+      float t = 0.f;
+      if (!ee) cudaEventElapsedTime(&t, ev[0], ev[1]);
+      ms = std::min(ms, t);
+    }
+    return ee;
+  };
+  // 1. the kernel variant at the modelled split: single-column float32
+  // products up to 8 dimensions that would take the tensor-core exponent
+  // path also try the packed CUDA-core kernel; multi-column Gaussian products
+  // up to 8 dimensions try both kernels for compact blocks and both for
+  // direct-form blocks.  The handle's own variant is kept unless another is
+  // 2% faster.
+  const int cur = current_variant(c);
+  std::vector<int> variants{cur};
+  if (single && Tp.d <= 8 && use_tcx(c, Tp)) {
+    variants.push_back(cur & ~TV_TENSOR_EXP);
+  } else if (!single && Tp.d <= 8 && Tp.kfam == KRR_KERNEL_GAUSSIAN) {
+    for (int v : {0, (int)TV_TCGEN05, (int)TV_DIRECT_TENSOR, TV_TCGEN05 | TV_DIRECT_TENSOR}) {
+      const int vv = (cur & TV_TENSOR_EXP) | v;
+      if (vv != cur) variants.push_back(vv);
+    }
+  }
+  c.tune_cache[key] = 1.0;
+  int best_v = cur;
+  float best_v_ms = -1.f;
+  for (int v : variants) {
+    c.tune_variant[key] = v;
+    float ms;
+    if ((e = time_it(ms))) break;
+    if (best_v_ms < 0.f || ms < 0.98f * best_v_ms) {
+      best_v_ms = ms;
+      best_v = v;
+    }
+  }
+  c.tune_variant[key] = best_v;
+  // 2. the source split of that variant
   double best = 1.0;
   float best_ms = -1.f;
   for (double s : TUNE_SCALES) {
+    if (e) break;
     c.tune_cache[key] = s;
     {
       TuneScope ts(c, s);
+      VariantScope vs(c, key);
       if (s > 1.0 && 8.0 * route_splits(c, Tp, Sp, m, prec) * m * (double)Tp.Npad > TUNE_MAX_BYTES)
         continue;
     }
-    MvpOut o;
-    o.out_f = (float*)yv;
-    auto run = [&]() {
-      return (m == 1 && prec == KRR_FP32)
-                 ? mvp_launch(c, Tp, Sp, (const float*)qv, nullptr, 0.f, prec, o, st)
-                 : mvp_multi_launch(c, Tp, Sp, (const float*)qv, m, nullptr, 0.f, prec, o, st);
-    };
-    if ((e = run())) break;  // warm-up: workspace and attributes of this split
-    float ms = 1e30f;
-    for (int rep = 0; rep < 2 && !e; ++rep) {
-      cudaEventRecord(ev[0], st);
-      e = run();
-      cudaEventRecord(ev[1], st);
-      if (!e) e = cudaEventSynchronize(ev[1]);
-      float t = 0.f;
-      if (!e) cudaEventElapsedTime(&t, ev[0], ev[1]);
-      ms = std::min(ms, t);
-    }
-    if (e) break;
+    float ms;
+    if ((e = time_it(ms))) break;
     if (best_ms < 0.f || ms < 0.98f * best_ms) {
       best_ms = ms;
       best = s;
@@ -909,6 +947,7 @@ cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   c.tune_cache[key] = e ? 1.0 : best;
+  if (e) c.tune_variant.erase(key);
   return e;
 }
 
@@ -929,6 +968,7 @@ cudaError_t mvp_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, cudaSt
     if (te) return te;
   }
   TuneScope scope(c, tuned_scale(c, key));
+  VariantScope vscope(c, key);
   // above 8 dimensions: the high-dimensional tensor-core kernel on compact
   // super-blocks with the multi-column direct-form kernel on the rest, or
   // that direct-form kernel alone
@@ -1089,6 +1129,7 @@ cudaError_t mvp_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, const f
     if (te) return te;
   }
   TuneScope scope(c, tuned_scale(c, key));
+  VariantScope vscope(c, key);
   if (use_tcx(c, Tp)) return tcx_path(c, Tp, Sp, q, qdiag, shift, o, st);
   MvpParams p{};
   p.xt = Tp.xs;
@@ -1166,6 +1207,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
     if (te) return te;
   }
   TuneScope scope(c, tuned_scale(c, key));
+  VariantScope vscope(c, key);
   const bool direct_only = multi_direct_only(Tp);
   cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
@@ -1201,6 +1243,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
     if (te) return te;
   }
   TuneScope scope(c, tuned_scale(c, key));
+  VariantScope vscope(c, key);
   MvpParams p{};
   p.xt = Tp.xs;
   p.Nt = Tp.N;

@@ -1,5 +1,8 @@
 """Autotuned products (handle option KRR_OPT_AUTOTUNE): the first product of
-each shape times several source splits and keeps the fastest.  Whatever the
+each shape times the kernel variants of that shape (tcgen05 or mma.sync for
+compact blocks, tensor-core or CUDA-core weighted sums for direct-form
+blocks, the tensor-core exponent path or the packed CUDA-core kernel for one
+column), then several source splits, and keeps the fastest.  Whatever the
 tuner picks, every result must still meet the bars the untuned products meet
 against the FP64 oracle, and a tuned shape must give the same bits on every
 later call.
@@ -46,7 +49,8 @@ def _scaled_error(oracle_mod, X, Q, Y, sigma, gamma, rows=None):
     return float(np.max(np.abs(YY.astype(np.float64) - ref) / scale))
 
 
-@pytest.mark.parametrize("N,d,m", [(300000, 3, 1), (60000, 2, 1), (40000, 2, 8), (5000, 3, 1)])
+@pytest.mark.parametrize("N,d,m", [(300000, 3, 1), (60000, 2, 1), (40000, 2, 8), (5000, 3, 1), (30001, 8, 16),
+                                   (70000, 3, 16)])
 def test_tuned_products_meet_bar_and_repeat(K, H, oracle_mod, N, d, m):
     rng = np.random.default_rng(N + m)
     X = rng.random((N, d)).astype(np.float32)
