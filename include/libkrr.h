@@ -192,15 +192,7 @@ typedef enum {
      * the weighted sum P Q on the tensor cores (tf32 hi/lo split for KRR_FP32,
      * single f16 / bf16 for reduced precision); 0: the all-CUDA-core kernel
      * (one FMA per pair and column).  Same results to the float32 bar. */
-    KRR_OPT_DIRECT_TENSOR = 7,
-    /* value 0 to 3: in single-column float32 products up to 8 dimensions
-     * that take the tensor-core exponent kernel, `value` of every 8 pair
-     * exponentials 2^E (Eq. 2) are evaluated on the FP32 pipe (range
-     * reduction to [-1/2, 1/2] and a degree-5 polynomial, relative error
-     * below 1.7e-7) instead of the special-function unit, which otherwise
-     * bounds the kernel.  Same results to the float32 bar.  Other values:
-     * KRR_ERR_INVALID_ARG. */
-    KRR_OPT_EXP_POLY = 8
+    KRR_OPT_DIRECT_TENSOR = 7
 } krr_option;
 
 /* Kernel functions (KRR_OPT_KERNEL). */

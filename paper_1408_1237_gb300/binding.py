@@ -387,7 +387,6 @@ KRR_OPT_AUTOTUNE = 3
 KRR_OPT_SHARD_COUNT, KRR_OPT_SHARD_INDEX = 4, 5
 KRR_OPT_HIGHD_TCGEN05 = 6
 KRR_OPT_DIRECT_TENSOR = 7
-KRR_OPT_EXP_POLY = 8
 KRR_KERNEL_GAUSSIAN, KRR_KERNEL_MATERN32 = 0, 1
 
 

@@ -99,46 +99,6 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-// Coefficients c1..c5 of p(f) = 1 + c1 f + ... + c5 f^5 ~ 2^f on [-1/2, 1/2]:
-// a near-minimax fit in relative error (Lawson's iteratively reweighted least
-// squares on 4001 Chebyshev nodes, c0 fixed at 1 so that integer arguments
-// give exact powers of two).  Evaluated by Horner in float32 the relative
-// error stays below 1.7e-7 on [-1/2, 1/2], about MUFU.EX2's own.
-constexpr float EXP2_POLY_C1 = 6.931470037e-01f;
-constexpr float EXP2_POLY_C2 = 2.402224243e-01f;
-constexpr float EXP2_POLY_C3 = 5.550733581e-02f;
-constexpr float EXP2_POLY_C4 = 9.671512991e-03f;
-constexpr float EXP2_POLY_C5 = 1.326472731e-03f;
-// 1.5 * 2^23: adding it to |x| < 2^22 leaves round-to-nearest(x) in the low
-// mantissa bits.
-constexpr float EXP2_POLY_ROUND = 12582912.f;
-
-// Two values of 2^x on the FP32 pipe instead of the special-function unit
-// (Cody-Waite style range reduction, then the polynomial above):
-//   x <- max(x, -125)          (anything smaller stands for 2^-125, which is
-//                               below every float32 sum it can enter)
-//   t = x + 1.5 * 2^23,  j = t - 1.5 * 2^23 = round(x)   (exact, Sterbenz)
-//   f = x - j in [-1/2, 1/2]                              (exact)
-//   2^x = p(f) * 2^j, the scaling done by adding j << 23 to p's exponent
-//   field; the low 32 bits of bits(t) << 23 are j << 23 (the constant's own
-//   low 9 bits are zero).
-// x must be at most 127 (no overflow check).  Packed FP32 instructions carry
-// both values: 2 FADD2 + 6 FFMA2 + 2 FMNMX + 2 integer shifts-adds.
-__device__ __forceinline__ float2 exp2_poly2(float2 x) {
-  x.x = fmaxf(x.x, -125.f);
-  x.y = fmaxf(x.y, -125.f);
-  const float2 t = __fadd2_rn(x, make_float2(EXP2_POLY_ROUND, EXP2_POLY_ROUND));
-  const float2 j = __fadd2_rn(t, make_float2(-EXP2_POLY_ROUND, -EXP2_POLY_ROUND));
-  const float2 f = __ffma2_rn(j, make_float2(-1.f, -1.f), x);
-  float2 p = __ffma2_rn(make_float2(EXP2_POLY_C5, EXP2_POLY_C5), f, make_float2(EXP2_POLY_C4, EXP2_POLY_C4));
-  p = __ffma2_rn(p, f, make_float2(EXP2_POLY_C3, EXP2_POLY_C3));
-  p = __ffma2_rn(p, f, make_float2(EXP2_POLY_C2, EXP2_POLY_C2));
-  p = __ffma2_rn(p, f, make_float2(EXP2_POLY_C1, EXP2_POLY_C1));
-  p = __ffma2_rn(p, f, make_float2(1.f, 1.f));
-  return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(t.x) << 23)),
-                     __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(t.y) << 23)));
-}
-
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }

@@ -112,9 +112,6 @@ struct Ctx {
   // kernel values on the CUDA cores, the weighted sum on the tensor cores
   // (mvp_dirtc_kernel); false: the all-CUDA-core kernel mvp_dirm_kernel
   bool direct_tensor = true;
-  // exponentials of the single-column tensor-exponent kernel (mvp_tcx_kernel)
-  // taken on the FP32 pipe by polynomial: exp_poly of every 8 (0 to 3)
-  int exp_poly = 0;
   // kernel function of every product and solve (KRR_KERNEL_*, krr_set_option)
   int kernel_family = 0;
   // autotuning of the products' source splits (KRR_OPT_AUTOTUNE): the first

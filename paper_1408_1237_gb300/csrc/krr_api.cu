@@ -280,11 +280,6 @@ krr_status krr_set_option(krr_handle h, int option, int value) {
     case KRR_OPT_DIRECT_TENSOR:
       h->ctx.direct_tensor = value != 0;
       return KRR_OK;
-    case KRR_OPT_EXP_POLY:
-      if (value < 0 || value > 3)
-        return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: exp_poly %d out of [0, 3]", value);
-      h->ctx.exp_poly = value;
-      return KRR_OK;
     case KRR_OPT_SHARD_COUNT:
       if (value < 1 || value > 4096)
         return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: shard count %d out of [1, 4096]", value);

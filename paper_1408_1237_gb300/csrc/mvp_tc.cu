@@ -444,15 +444,8 @@ __global__ void __launch_bounds__(256) mvp_tc_kernel(const TcParams p) {
 // super-block, MT m-tiles of 16 targets per warp; a thread accumulates the
 // rows g and g+8 of each m-tile over its columns 2t, 2t+1 and the four
 // threads of a row are summed at the end.
-//
-// PX of every 8 exponentials (0 to 3) are evaluated by exp2_poly2 on the
-// FP32 pipe instead of MUFU.EX2: the FP32 pipe is a quarter busy, so moving
-// a share of the exponentials there lifts the special-function-unit bound.
-// With PX > 0 the kernel is held to 96 registers (5 CTAs per SM, as without
-// the polynomial), where the polynomial's packed constants would otherwise
-// take it to 126 (4 CTAs).
-template <int D, int MT, int PX>
-__global__ void __launch_bounds__(32 * (SB / (16 * MT)), PX > 0 ? 5 : 1) mvp_tcx_kernel(const TcParams p) {
+template <int D, int MT>
+__global__ void __launch_bounds__(32 * (SB / (16 * MT))) mvp_tcx_kernel(const TcParams p) {
   using L = ExpLayout<D>;
   using H = Half<false>;
   constexpr int W = D + 1;
@@ -629,15 +622,11 @@ __global__ void __launch_bounds__(32 * (SB / (16 * MT)), PX > 0 ? 5 : 1) mvp_tcx
           mma16816<false>(e1, afr[mt][ks], bfr[1][ks][0], bfr[1][ks][1]);
         }
         // rows g (elements 0, 1) and g+8 (elements 2, 3): the two columns of
-        // a row and 8-source half share one packed FMA; exponential pair k
-        // of this step goes to the FP32 pipe when k mod 8 < PX
-        auto pexp = [&](int k, float a, float b) {
-          return ((k & 7) < PX) ? exp2_poly2(make_float2(a, b)) : make_float2(ex2(a), ex2(b));
-        };
-        acc[mt][0] = ffma2(q0, pexp(4 * mt + 0, e0[0], e0[1]), acc[mt][0]);
-        acc2[mt][0] = ffma2(q1, pexp(4 * mt + 1, e1[0], e1[1]), acc2[mt][0]);
-        acc[mt][1] = ffma2(q0, pexp(4 * mt + 2, e0[2], e0[3]), acc[mt][1]);
-        acc2[mt][1] = ffma2(q1, pexp(4 * mt + 3, e1[2], e1[3]), acc2[mt][1]);
+        // a row and 8-source half share one packed FMA
+        acc[mt][0] = ffma2(q0, make_float2(ex2(e0[0]), ex2(e0[1])), acc[mt][0]);
+        acc2[mt][0] = ffma2(q1, make_float2(ex2(e1[0]), ex2(e1[1])), acc2[mt][0]);
+        acc[mt][1] = ffma2(q0, make_float2(ex2(e0[2]), ex2(e0[3])), acc[mt][1]);
+        acc2[mt][1] = ffma2(q1, make_float2(ex2(e1[2]), ex2(e1[3])), acc2[mt][1]);
       }
     }
 #pragma unroll
@@ -1730,13 +1719,13 @@ constexpr size_t tcx_smem_bytes() {
          sizeof(float) * 2 * TS;
 }
 
-template <int D, int PX>
-cudaError_t tcx_launch_px(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+template <int D>
+cudaError_t tcx_launch_typed(const TcParams& p, int splits, cudaStream_t st, bool dry) {
   static bool done[128] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 128 && !done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(mvp_tcx_kernel<D, TCX_MT, PX>,
+    cudaError_t e = cudaFuncSetAttribute(mvp_tcx_kernel<D, TCX_MT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tcx_smem_bytes<D>());
     if (e) return e;
@@ -1744,19 +1733,9 @@ cudaError_t tcx_launch_px(const TcParams& p, int splits, cudaStream_t st, bool d
   }
   if (dry) return cudaSuccess;
   dim3 grid((unsigned)p.nblk, (unsigned)splits);
-  mvp_tcx_kernel<D, TCX_MT, PX><<<grid, 32 * (SB / (16 * TCX_MT)), tcx_smem_bytes<D>(), st>>>(p);
+  mvp_tcx_kernel<D, TCX_MT><<<grid, 32 * (SB / (16 * TCX_MT)), tcx_smem_bytes<D>(), st>>>(p);
   count_launch();
   return cudaGetLastError();
-}
-template <int D>
-cudaError_t tcx_launch_typed(const TcParams& p, int poly, int splits, cudaStream_t st, bool dry) {
-  switch (poly) {
-    case 0: return tcx_launch_px<D, 0>(p, splits, st, dry);
-    case 1: return tcx_launch_px<D, 1>(p, splits, st, dry);
-    case 2: return tcx_launch_px<D, 2>(p, splits, st, dry);
-    case 3: return tcx_launch_px<D, 3>(p, splits, st, dry);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 template <int D>
@@ -1910,14 +1889,14 @@ cudaError_t mvp_tcx_partials(Ctx& c, const PointsDev& T, const PointsDev& S, con
   p.s = S.scale;
   p.active = active;
   switch (T.d) {
-    case 1: return tcx_launch_typed<1>(p, c.exp_poly, splits, st, dry);
-    case 2: return tcx_launch_typed<2>(p, c.exp_poly, splits, st, dry);
-    case 3: return tcx_launch_typed<3>(p, c.exp_poly, splits, st, dry);
-    case 4: return tcx_launch_typed<4>(p, c.exp_poly, splits, st, dry);
-    case 5: return tcx_launch_typed<5>(p, c.exp_poly, splits, st, dry);
-    case 6: return tcx_launch_typed<6>(p, c.exp_poly, splits, st, dry);
-    case 7: return tcx_launch_typed<7>(p, c.exp_poly, splits, st, dry);
-    case 8: return tcx_launch_typed<8>(p, c.exp_poly, splits, st, dry);
+    case 1: return tcx_launch_typed<1>(p, splits, st, dry);
+    case 2: return tcx_launch_typed<2>(p, splits, st, dry);
+    case 3: return tcx_launch_typed<3>(p, splits, st, dry);
+    case 4: return tcx_launch_typed<4>(p, splits, st, dry);
+    case 5: return tcx_launch_typed<5>(p, splits, st, dry);
+    case 6: return tcx_launch_typed<6>(p, splits, st, dry);
+    case 7: return tcx_launch_typed<7>(p, splits, st, dry);
+    case 8: return tcx_launch_typed<8>(p, splits, st, dry);
     case 16: return c.highd_tcgen05 ? uhd_launch_typed<16>(p, splits, st, dry) : tch_launch_typed<16>(p, splits, st, dry);
     case 32: return c.highd_tcgen05 ? uhd_launch_typed<32>(p, splits, st, dry) : tch_launch_typed<32>(p, splits, st, dry);
     case 48: return c.highd_tcgen05 ? uhd_launch_typed<48>(p, splits, st, dry) : tch_launch_typed<48>(p, splits, st, dry);

@@ -302,44 +302,3 @@ def test_mvp_multi_direct_tensor_batch_shape_full_size(K, oracle_mod):
     rows = inputs.sample_rows(N, 256, seed=5)
     for c in (0, 5, 15):
         assert scaled_error(oracle_mod, X, Q[c], Y[c], 1.0, 1e-3, rows) <= TOL_FP32, c
-
-
-@pytest.mark.parametrize("poly", [1, 2, 3])
-@pytest.mark.parametrize("N,d,sigma", [(300000, 3, 0.0866), (160000, 2, 0.07), (200001, 4, 0.1),
-                                         (100000, 1, 0.05), (160000, 8, 0.4)])
-def test_mvp_tensor_exponent_poly_offload(K, oracle_mod, poly, N, d, sigma):
-    # KRR_OPT_EXP_POLY: `poly` of every 8 pair exponentials of the tensor-
-    # exponent kernel on the FP32 pipe (degree-5 polynomial).  Clouds large
-    # enough (and sigma wide enough) for that kernel; its launch is checked
-    # in the handle's profile.  Same bar as the MUFU exponentials, and the
-    # results differ from them only in the last bits.
-    rng = np.random.default_rng(N + d + 10 * poly)
-    X = rng.random((N, d)).astype(np.float32)
-    q = rng.standard_normal(N).astype(np.float32)
-    gamma = 1e-3
-    rows = inputs.sample_rows(N, 128, seed=poly)
-    ys = []
-    for opt in (0, poly):
-        h = K.Handle()
-        try:
-            K.krr_set_option(K.KRR_OPT_EXP_POLY, opt, handle=h)
-            K.krr_profile_enable(True, handle=h)
-            ys.append(K.krr_kernel_mvp(_dev(X), _dev(q), sigma, gamma, handle=h).cpu().numpy())
-            prof = K.krr_profile_read(handle=h)
-        finally:
-            h.close()
-        assert prof["tensor_exponent_launches"] == prof["product_launches"] == 1, prof
-    assert scaled_error(oracle_mod, X, q, ys[1], sigma, gamma, rows) <= TOL_FP32
-    scale = oracle_mod.mvp(X.astype(np.float64), np.abs(q.astype(np.float64)), f32(sigma), f32(gamma), rows=rows)
-    assert np.max(np.abs(ys[1][rows].astype(np.float64) - ys[0][rows]) / scale) <= 2e-6
-
-
-def test_exp_poly_option_range(K):
-    h = K.Handle()
-    try:
-        for bad in (-1, 4):
-            with pytest.raises(K.KrrError) as ei:
-                K.krr_set_option(K.KRR_OPT_EXP_POLY, bad, handle=h)
-            assert ei.value.status == K.KRR_ERR_INVALID_ARG
-    finally:
-        h.close()
