@@ -43,9 +43,9 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "8db8257c9045d9e69c589b4c8d7ba129e5a73af9",
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "a191d1b20caefd72496d762b4c4673355068dc96",
                            "paper_1408_1237_gb300/csrc/mvp_tc.cu": "da937f5a3005504548b95ee054bdc697fdaf5412"},
-               "bytes": 22762752 + 92209152 + 17047040 + 0}
+               "bytes": 22911744 + 92082944 + 17238784 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 
