@@ -382,19 +382,23 @@ def run_libkrr(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     m16_ms = e0.elapsed_time(e1)
-    # the same on the tcgen05 / tensor-memory kernel (handle option)
-    h5 = K.Handle()
-    K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h5)
-    K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h5)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h5)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    m16_tc5_ms = e0.elapsed_time(e1)
-    h5.close()
+    # the same on the other kernels (handle option KRR_OPT_TCGEN05): the
+    # mma.sync kernel, and the kernel with the exponent in tensor memory
+    m16_alt = {}
+    for name, opt in (("mma_sync_ms", 0), ("tmem_exponent_ms", 2)):
+        h5 = K.Handle()
+        K.krr_set_option(K.KRR_OPT_TCGEN05, opt, handle=h5)
+        K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h5)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        K.krr_kernel_mvp(X, Q16, sigma, gamma, out=Y16, handle=h5)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        m16_alt[name] = e0.elapsed_time(e1)
+        h5.close()
 
-    progress(f"16-column product: {m16_ms:.1f} ms (tcgen05 kernel {m16_tc5_ms:.1f} ms)")
+    progress(f"16-column product: {m16_ms:.1f} ms (mma.sync kernel {m16_alt['mma_sync_ms']:.1f} ms, "
+             f"tensor-memory exponent kernel {m16_alt['tmem_exponent_ms']:.1f} ms)")
     # ---- end to end through the C ABI with pinned host buffers
     Xh = torch.from_numpy(p["X"]).pin_memory()
     qh = torch.from_numpy(p["Q"]).pin_memory()
@@ -484,8 +488,9 @@ def run_libkrr(args):
             "gpu_launches": launches,
             "clocks": clk,
             "mvp_m16": {"ms": m16_ms, "Gpair_rhs_per_s": pairs * 16 / (m16_ms / 1e3) / 1e9,
-                        "kernel": "mma.sync (default)",
-                        "tcgen05_ms": m16_tc5_ms},
+                        "kernel": "mvp_umx_kernel (exponent by mma.sync, P Q by tcgen05; default "
+                                  "for float32 products of more than 8 columns)",
+                        **m16_alt},
             "fgmres": solve,
             "skipped_for_wall_budget": skipped,
             "rates": rates,

@@ -135,13 +135,19 @@ void krr_fgmres_default_opts(krr_fgmres_opts* opts);
 
 /* Handle options. */
 typedef enum {
-    /* value != 0: the multi-column tensor-core products (krr_kernel_mvp with
-     * m >= 2, block solves) use the 5th-generation tensor-core kernel
-     * (tcgen05.mma with accumulators in tensor memory: S = A B^T into tensor
-     * memory, 2^S written back over it as f16, Y += P Q with P read from
-     * tensor memory) instead of the default mma.sync kernel.  Same results to
-     * the float32 bar; on GB300 the default is faster (measured: 16 columns
-     * at 2^20 points, 450 ms vs 584 ms). */
+    /* The kernel of the compact target blocks of multi-column products
+     * (krr_kernel_mvp with m >= 2, block, batched and gradient solves):
+     *  0: mma.sync for the exponent and for Y += P Q;
+     *  1: mma.sync for the exponent into registers, P = 2^E stored to tensor
+     *     memory (tcgen05.st), Y += P Q by tcgen05.mma with P read from
+     *     tensor memory and accumulators in tensor memory;
+     *  2: tcgen05.mma for the exponent into tensor memory, loaded,
+     *     exponentiated and stored back as P, then Y += P Q as in 1;
+     *  3 (default): 1 for float32 products of more than 8 columns, 0 for
+     *     the others.
+     * Same results to the float32 bar (and the reduced-precision bars).  On
+     * GB300, 16 columns at 2^20 points: float32 406 / 431 / 549 ms, f16
+     * 269 / 261 / 378 ms for 1 / 0 / 2.  Other values: KRR_ERR_INVALID_ARG. */
     KRR_OPT_TCGEN05 = 1,
     /* value: a krr_kernel_family.  The kernel function every product and
      * solver of this handle uses (default KRR_KERNEL_GAUSSIAN).  Under

@@ -391,8 +391,9 @@ KRR_KERNEL_GAUSSIAN, KRR_KERNEL_MATERN32 = 0, 1
 
 
 def krr_set_option(option, value, handle=None):
-    """Set a handle option (KRR_OPT_TCGEN05: multi-column tensor-core
-    products on the tcgen05 / tensor-memory kernel; KRR_OPT_KERNEL: the
+    """Set a handle option (KRR_OPT_TCGEN05: the kernel of multi-column
+    products' compact blocks, 0 mma.sync, 1 and 2 tcgen05, 3 automatic by
+    precision and columns; KRR_OPT_KERNEL: the
     kernel function, KRR_KERNEL_GAUSSIAN or KRR_KERNEL_MATERN32, whose length
     scale h is then passed as sigma; KRR_OPT_AUTOTUNE: time the products'
     kernel variants and source splits on first use of each shape and keep

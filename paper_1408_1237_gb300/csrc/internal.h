@@ -105,6 +105,15 @@ struct Ctx {
   // multi-column tensor-core products on the tcgen05 / tensor-memory kernel
   // instead of the mma.sync kernel (krr_set_option)
   bool use_tcgen05 = false;
+  // which tcgen05 multi-column kernel: 1 = exponent by mma.sync into
+  // registers, P stored to tensor memory (mvp_umx_kernel); 2 = exponent by
+  // tcgen05 into tensor memory, loaded, exponentiated and stored back
+  // (mvp_umma_kernel)
+  int tcgen05_kind = 1;
+  // the default: float32 multi-column products on mvp_umx_kernel, reduced-
+  // precision ones on the mma.sync kernel (the faster of each on GB300);
+  // cleared when KRR_OPT_TCGEN05 picks one kernel for all
+  bool tcgen05_auto = true;
   // single-column products above 8 dimensions on the tcgen05 kernel
   // (mvp_uhd_kernel; false: the mma.sync kernel mvp_tch_kernel)
   bool highd_tcgen05 = true;
@@ -176,25 +185,40 @@ enum TuneVariant : int {
   TV_TENSOR_EXP = 4,     // single-column float32 products may take the tensor-core exponent path
                          // (128-thread CTAs per super-block) instead of the packed CUDA-core kernel
 };
-inline int current_variant(const Ctx& c) {
-  return (c.use_tcgen05 ? TV_TCGEN05 : 0) | (c.direct_tensor ? TV_DIRECT_TENSOR : 0) |
+// Whether the compact blocks of an m-column product of precision prec take
+// a tcgen05 kernel (c.tcgen05_kind) rather than the mma.sync kernel.  The
+// automatic choice takes mvp_umx_kernel for float32 products of more than
+// TC5_AUTO_MIN_COLS columns, where the mma.sync kernel's three split P Q
+// MMAs per column tile bound it.
+constexpr int TC5_AUTO_MIN_COLS = 8;
+inline bool tc5_on(const Ctx& c, int prec, int m) {
+  return c.tcgen05_auto ? (prec == KRR_FP32 && m > TC5_AUTO_MIN_COLS) : c.use_tcgen05;
+}
+inline int current_variant(const Ctx& c, int prec, int m) {
+  return (tc5_on(c, prec, m) ? TV_TCGEN05 : 0) | (c.direct_tensor ? TV_DIRECT_TENSOR : 0) |
          (c.allow_tcx ? TV_TENSOR_EXP : 0);
 }
 // Applies the tuned variant of a shape for one product entry point (and puts
 // the handle's settings back after it).
 struct VariantScope {
   Ctx& c;
-  bool tc5, dt, tcx;
+  bool tc5, tc5_auto, dt, tcx;
+  int tc5_kind;
   VariantScope(Ctx& cc, const std::string& key)
-      : c(cc), tc5(cc.use_tcgen05), dt(cc.direct_tensor), tcx(cc.allow_tcx) {
+      : c(cc), tc5(cc.use_tcgen05), tc5_auto(cc.tcgen05_auto), dt(cc.direct_tensor), tcx(cc.allow_tcx),
+        tc5_kind(cc.tcgen05_kind) {
     const auto it = c.tune_variant.find(key);
     if (it == c.tune_variant.end()) return;
+    c.tcgen05_auto = false;
     c.use_tcgen05 = (it->second & TV_TCGEN05) != 0;
+    if (tc5_auto) c.tcgen05_kind = 1;  // the automatic choice's tcgen05 kernel
     c.direct_tensor = (it->second & TV_DIRECT_TENSOR) != 0;
     c.allow_tcx = tcx && (it->second & TV_TENSOR_EXP) != 0;  // never where the handle forbids it
   }
   ~VariantScope() {
     c.use_tcgen05 = tc5;
+    c.tcgen05_auto = tc5_auto;
+    c.tcgen05_kind = tc5_kind;
     c.direct_tensor = dt;
     c.allow_tcx = tcx;
   }

@@ -48,7 +48,7 @@ std::string tune_key(const Ctx& c, const char* kind, const PointsDev& Tp, const 
                      int prec) {
   char buf[256];
   snprintf(buf, sizeof(buf), "%s|%lld|%lld|%d|%d|%d|%d|%d|%d|%lld|%lld", kind, (long long)Tp.N,
-           (long long)Sp.N, Tp.d, Tp.kfam, m, prec, c.plan_slots, c.use_tcgen05 ? 1 : 0,
+           (long long)Sp.N, Tp.d, Tp.kfam, m, prec, c.plan_slots, c.tcgen05_auto ? 3 : c.use_tcgen05 ? c.tcgen05_kind : 0,
            (long long)Tp.h_nexp, (long long)Tp.h_sb_nexp);
   return buf;
 }
@@ -269,7 +269,11 @@ krr_status krr_set_option(krr_handle h, int option, int value) {
   if (!h) return KRR_ERR_INVALID_ARG;
   switch (option) {
     case KRR_OPT_TCGEN05:
-      h->ctx.use_tcgen05 = value != 0;
+      if (value < 0 || value > 3)
+        return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: tcgen05 kernel %d out of [0, 3]", value);
+      h->ctx.tcgen05_auto = value == 3;
+      h->ctx.use_tcgen05 = value == 1 || value == 2;
+      h->ctx.tcgen05_kind = value == 2 ? 2 : 1;
       return KRR_OK;
     case KRR_OPT_AUTOTUNE:
       h->ctx.autotune = value != 0;

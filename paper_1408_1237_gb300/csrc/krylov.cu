@@ -1624,6 +1624,8 @@ krr_status krr_fgmres_solve_batched(krr_handle h, const krr_problem* probs, int 
       if ((e = sub_context(c, br.size(), &bc))) return cuda_error(c, e, fn);
       bc->plan_slots = slots;
       bc->use_tcgen05 = c.use_tcgen05;
+      bc->tcgen05_kind = c.tcgen05_kind;
+      bc->tcgen05_auto = c.tcgen05_auto;
       bc->kernel_family = c.kernel_family;
       bc->autotune = c.autotune;
       bc->highd_tcgen05 = c.highd_tcgen05;

@@ -744,11 +744,11 @@ cudaError_t dirm_dispatch(const MvpParams& p, int d, int kf, const float* Q, int
 // Source splits of the multi-column kernels (one CTA per super-block): the
 // tensor-core kernel over the expanded-form super-blocks, the CUDA-core
 // kernel over the direct-form ones, each planned for its own grid.
-Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp) {
+Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp, krr_precision prec, int m) {
   // two CTAs (of 128 targets) per super-block, at most two per SM (tensor memory)
   // one CTA per super-block (mma.sync kernel), or two of 128 targets with at
   // most two per SM (tcgen05 kernel: tensor memory)
-  return make_plan((c.use_tcgen05 ? 2 : 1) * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
+  return make_plan((tc5_on(c, prec, m) ? 2 : 1) * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
                    c.plan_slots, c.split_scale);
 }
 // Multi-column products keep the tensor cores to d <= 8 (Gaussian); elsewhere
@@ -840,7 +840,7 @@ int route_splits(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, 
     if (Tp.d <= 8) return make_plan(Tp.nblk, (int)(Sp.Npad / TS), c.num_sms, c.plan_slots, c.split_scale).splits;
   }
   int s = multi_plan_dir(c, Tp, Sp).splits;
-  if (!multi_direct_only(Tp)) s = std::max(s, multi_plan_tc(c, Tp, Sp).splits);
+  if (!multi_direct_only(Tp)) s = std::max(s, multi_plan_tc(c, Tp, Sp, prec, m).splits);
   return s;
 }
 
@@ -902,7 +902,7 @@ cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m
   // up to 8 dimensions try both kernels for compact blocks and both for
   // direct-form blocks.  The handle's own variant is kept unless another is
   // 2% faster.
-  const int cur = current_variant(c);
+  const int cur = current_variant(c, prec, m);
   std::vector<int> variants{cur};
   if (single && Tp.d <= 8 && use_tcx(c, Tp)) {
     variants.push_back(cur & ~TV_TENSOR_EXP);
@@ -1211,7 +1211,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   const bool direct_only = multi_direct_only(Tp);
   cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
   if (e) return e;
-  const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
+  const Plan pt = multi_plan_tc(c, Tp, Sp, prec, m), pd = multi_plan_dir(c, Tp, Sp);
   void* v;
   if ((e = c.ws.get("mvp.partm", sizeof(double) * pt.splits * (size_t)m * Tp.Npad, &v))) return e;
   if ((e = c.ws.get("mvp.partd", sizeof(double) * pd.splits * (size_t)m * Tp.Npad, &v))) return e;
@@ -1225,7 +1225,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
     return e;
   }
   if (direct_only) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
-  if (c.use_tcgen05)
+  if (tc5_on(c, prec, m))
     return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                              pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
   return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
@@ -1261,7 +1261,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   p.s = Sp.scale;
   p.active = o.active;
   p.part_stride = (int64_t)m * Tp.Npad;
-  const Plan pt = multi_plan_tc(c, Tp, Sp), pd = multi_plan_dir(c, Tp, Sp);
+  const Plan pt = multi_plan_tc(c, Tp, Sp, prec, m), pd = multi_plan_dir(c, Tp, Sp);
   const bool direct_only = multi_direct_only(Tp);
   const int64_t nexp = multi_nexp(Tp);
   cudaError_t e = direct_only ? common_reserve(c, Tp, st) : mvp_reserve(c, Tp, Sp, st);
@@ -1275,10 +1275,11 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   if ((e = c.ws.get("mvp.dotcnt", sizeof(unsigned) * MAX_COLS, &dcnt))) return e;
   p.fac = (float*)fac;
   cudaEvent_t pev1 = prof_begin(c, Tp, Sp, st);
-  // expanded-form super-blocks: all columns on the tensor cores (mma.sync
-  // kernel; the tcgen05 / tensor-memory kernel when the handle asks for it)
+  // expanded-form super-blocks: all columns on the tensor cores (float32
+  // products of more than 8 columns: P Q by tcgen05 in mvp_umx_kernel; the
+  // others: mma.sync; KRR_OPT_TCGEN05 overrides)
   if (nexp > 0) {
-    e = c.use_tcgen05
+    e = tc5_on(c, prec, m)
             ? mvp_umma_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                                 pt.tiles_per_split, (double*)part, p.fac, o.active, st)
             : mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,

@@ -1365,6 +1365,386 @@ __global__ void __launch_bounds__(umma::THREADS + 32) mvp_umma_kernel(const TcPa
 }
 
 // ------------------------------------------------------------------------
+// Multi-column product with the exponent on mma.sync and the weighted sum on
+// tcgen05 (KRR_OPT_TCGEN05 = 1, mvp_umx_kernel).  The exponent E = A'B'^T
+// is computed as in mvp_tcx_kernel, into registers; P = 2^E is split into
+// f16 hi / lo there and written to tensor memory with tcgen05.st.16x256b,
+// whose fragment (thread (g, t): lanes g and g + 8, columns 2t and 2t + 1)
+// is the mma.sync accumulator fragment.  The source order of the exponent
+// MMA's B fragment is permuted so that the four values of a row a thread
+// holds per 16 sources, from two 8-source n-tiles, are sources 4t .. 4t + 3:
+// the packed pairs (4t, 4t+1) and (4t+2, 4t+3) are then exactly the K-pairs
+// of tensor-memory columns 2t and 2t + 1 that the P Q MMA reads.  So
+// tensor memory is written once per P value and never read by the CUDA
+// cores (the tensor-memory exponent kernel below loads S and stores P).
+// Roles (per CTA of 128 targets, two per compact super-block):
+//  * 8 compute warps in two chunk groups (warps 0-3 and 4-7, each covering
+//    the 128 tensor-memory lanes: warp w takes lanes 32 (w mod 4) on as two
+//    m-tiles of 16) take alternate 64-source chunks: wait until the P Q MMAs
+//    that last read the chunk's P buffer are complete, exponentiate, store
+//    P hi / lo, signal pfull.  After their first chunk of a tile they fold
+//    the previous tile's Y into Kahan sums and build the next tile's source
+//    K-vectors (one source per thread);
+//  * 1 MMA warp (one elected thread): per chunk, once its P is stored,
+//    Y += Ph Qh (+ Pl Qh + Ph Ql) with A from tensor memory and the weight
+//    tiles (pre-split, as for the kernel below) from shared memory.
+// Every wait is bounded; on abort the issued MMAs and copies are drained
+// before tensor memory is freed.
+namespace umx {
+constexpr int NCW = umma::THREADS / 32;  // compute warps
+constexpr int CPT = TS / umma::NC;       // chunks per tile
+template <int D>
+constexpr size_t smem_bytes(bool split) {
+  const size_t need = umma::URS * (size_t)umma::stage_bytes<D>(split) +
+                      sizeof(uint32_t) * 2 * TS * ExpLayout<D>::KV_STRIDE_W;
+  return need > umma::SMEM_FLOOR ? need : umma::SMEM_FLOOR;
+}
+// Source of column n of n-tile nt in a 16-source block (see above), and the
+// inverse: the shared-memory row of source j in its block, so that the
+// B-fragment loads of an n-tile read 8 consecutive rows (bank-conflict free
+// with the K-vector stride of ExpLayout).
+__device__ __forceinline__ int src_perm(int nt, int n) { return 2 * n - (n & 1) + 2 * nt; }
+__device__ __forceinline__ int src_slot(int j) { return 8 * ((j >> 1) & 1) + 2 * (j >> 2) + (j & 1); }
+__device__ __forceinline__ void st_16x256b_x2(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                  "r"(v[7])
+               : "memory");
+}
+}  // namespace umx
+
+template <int D, bool SPLIT, bool BF>
+__global__ void __launch_bounds__(umma::THREADS + 32, 2) mvp_umx_kernel(const TcParams p) {
+  using namespace umma;
+  using L = ExpLayout<D>;
+  using H = Half<BF>;      // P and weight operands
+  using HE = Half<false>;  // split-f16 exponent operands
+  constexpr int W = D + 1;
+  constexpr int NCW = umx::NCW;
+  constexpr int CPT = umx::CPT;
+  constexpr uint32_t SBYTES = stage_bytes<D>(SPLIT);
+  constexpr int QTILE = 2 * YN * TS;  // bytes of one weight tile
+  constexpr int KVW = L::KV_STRIDE_W;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[URS];   // TMA stages
+  __shared__ __align__(8) uint64_t pfull[NBUF];  // P of buffer b stored (one chunk group)
+  __shared__ __align__(8) uint64_t pdone[NBUF];  // P Q reading buffer b complete (commit)
+  __shared__ __align__(8) uint64_t kready[2];    // a tile's source K-vectors written (compute warps)
+  __shared__ __align__(8) uint64_t yfull[2];     // Y buffer complete for its tile (commit)
+  __shared__ __align__(8) uint64_t yfree[2];     // Y buffer read (compute warps)
+  __shared__ __align__(8) uint64_t dbar;         // after an abort: the MMAs issued are complete
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const bool mma_warp = warp == NCW;
+  const int grp = (warp >> 2) & 1;  // chunk group: chunks c with c % 2 == grp
+  const int qw = warp & 3;          // tensor-memory lane quarter of a compute warp
+  if (p.active && *p.active == 0) return;
+  const int64_t nexp = *p.tn_exp;
+  const int64_t sb_slot = blockIdx.x >> 1;
+  if (sb_slot >= nexp) return;
+  unsigned char* stages = smem_raw;  // URS stages: coordinates, Qh, Ql
+  uint32_t* kvb = reinterpret_cast<uint32_t*>(smem_raw + URS * SBYTES);  // 2 x TS x KVW
+
+  const int64_t blk = p.torder[sb_slot];
+  if (blk * SB < p.row_lo || blk * SB >= p.row_hi) return;  // outside the shard
+  float ctr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) ctr[k] = p.tctr[blk * D + k];
+  const int64_t row_base = blk * SB + (int64_t)(blockIdx.x & 1) * ROWS;
+
+  // ---- operand A' of the exponent MMA: rows 32 qw + 16 mt + g (+ 8)
+  uint32_t afr[2][L::KSTEPS][4];
+  if (!mma_warp) {
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int64_t i = row_base + 32 * qw + 16 * mt + g + 8 * half;
+        const int64_t ii = i < p.Nt ? i : p.Nt - 1;
+        float ah[W], al[W];
+        float r2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float x = p.xt[(ii / TS) * (int64_t)D * TS + (int64_t)k * TS + ii % TS];
+          const float xh = p.s * (x - ctr[k]);
+          r2 = fmaf(xh, xh, r2);
+          ah[k] = HE::to(HE::from(xh));
+          al[k] = xh - ah[k];
+        }
+        ah[D] = 1.f;
+        al[D] = 0.f;
+        if (grp == 0 && blockIdx.y == 0 && t == 0 && i < p.Nt_pad) p.fac[i] = exp2f(-r2);
+#pragma unroll
+        for (int ks = 0; ks < L::KSTEPS; ++ks) {
+          const int k0 = 16 * ks + 2 * t;
+          afr[mt][ks][half] = HE::pack(kv_value<D>(ah, al, k0, true), kv_value<D>(ah, al, k0 + 1, true));
+          afr[mt][ks][half + 2] =
+              HE::pack(kv_value<D>(ah, al, k0 + 8, true), kv_value<D>(ah, al, k0 + 9, true));
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < URS; ++st) mbar_init(&bars[st], 1);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&pfull[b], GROUP_WARPS);
+      mbar_init(&pdone[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&kready[b], NCW);
+      mbar_init(&yfull[b], 1);
+      mbar_init(&yfree[b], NCW);
+    }
+    mbar_init(&dbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t y_col = NBUF * NC;  // Y buffers at y_col and y_col + YN
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
+
+  auto issue = [&](int r) {
+    const int stage = r % URS;
+    const int64_t tile = t_begin + r;
+    unsigned char* dst = stages + stage * SBYTES;
+    mbar_arrive_expect_tx(&bars[stage], SBYTES);
+    bulk_g2s(dst, p.xs + tile * (int64_t)D * TS, D * TS * 4, &bars[stage]);
+    bulk_g2s(dst + D * TS * 4, p.qh_tiles + tile * (int64_t)(YN * TS), QTILE, &bars[stage]);
+    if (SPLIT) bulk_g2s(dst + D * TS * 4 + QTILE, p.ql_tiles + tile * (int64_t)(YN * TS), QTILE, &bars[stage]);
+  };
+  // a bounded wait that also gives up once another role has aborted
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+      if (abort_flag || clock64() - t0 > WAIT_LIMIT_CLOCKS) return false;
+    }
+    return true;
+  };
+
+  int issued = 0;
+  if (mma_warp) {
+    // ================= MMA warp: chunk c's P Q once its P is stored
+    if (lane == 0) {
+      const uint32_t id_y = idesc(BF ? 1 : 0, YN, ROWS);
+      uint32_t n_yf[2] = {0, 0};
+      const int total = nt * CPT;
+      bool ok = true;
+      for (int c = 0; c < total && ok; ++c) {
+        const int r = c / CPT, q = c % CPT, b = c % NBUF, yb = r & 1;
+        ok = wait(&pfull[b], (uint32_t)(c / NBUF) & 1);
+        if (ok && q == 0 && r >= 2) {  // Y buffer yb was read for tile r - 2
+          ok = wait(&yfree[yb], n_yf[yb] & 1);
+          ++n_yf[yb];
+        }
+        if (!ok) break;
+        fence_after();
+        const uint32_t qh_addr = smem_addr(stages + (r % URS) * SBYTES + D * TS * 4);
+        const uint32_t ql_addr = qh_addr + QTILE;
+        const uint32_t pbuf = tmem + (uint32_t)(b * NC);
+        const uint32_t yd = tmem + y_col + (uint32_t)(YN * yb);
+#pragma unroll
+        for (int ks = 0; ks < NC / 16; ++ks) {
+          const uint32_t qoff = (uint32_t)((NC / 8) * q + 2 * ks) * 128u;
+          const uint32_t pa = pbuf + (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
+          const int acc = (q > 0 || ks > 0) ? 1 : 0;
+          mma_ts(yd, pa, sdesc(qh_addr + qoff, (TS / 8) * 128), id_y, acc);
+          if (SPLIT) {
+            mma_ts(yd, pa + 16u, sdesc(qh_addr + qoff, (TS / 8) * 128), id_y, 1);
+            mma_ts(yd, pa, sdesc(ql_addr + qoff, (TS / 8) * 128), id_y, 1);
+          }
+        }
+        commit(&pdone[b]);
+        if (q == CPT - 1) commit(&yfull[yb]);
+      }
+      if (!ok) {
+        // stop the compute warps, and let every MMA issued complete before
+        // the tensor memory is released
+        abort_flag = 1;
+        commit(&dbar);
+        mbar_wait_bounded(&dbar, 0);
+      }
+    }
+    __syncwarp();  // the idle lanes wait for the issuing lane before the block barrier
+  } else {
+    // ================= compute warps
+    if (tid == 0)
+      for (; issued < min(URS, nt); ++issued) issue(issued);
+    constexpr int YW = YN / 2;  // Y columns folded per group
+    float Ssum[YW], Scomp[YW];
+#pragma unroll
+    for (int c = 0; c < YW; ++c) Ssum[c] = Scomp[c] = 0.f;
+    const uint32_t lanes = (uint32_t)(32 * qw) << 16;  // this warp's tensor-memory lanes
+    // tile r's source K-vectors into buffer r & 1 (its stage awaited first;
+    // one source per thread)
+    auto make_k = [&](int r) -> bool {
+      if (!__all_sync(0xffffffffu, wait(&bars[r % URS], (r / URS) & 1))) return false;
+      const float* rs = reinterpret_cast<const float*>(stages + (r % URS) * SBYTES);
+      uint32_t* kv = kvb + (r & 1) * TS * KVW;
+      const int j = tid;
+      float bh[W], bl[W];
+      float bb = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float xh = p.s * (rs[k * TS + j] - ctr[k]);
+        bb = fmaf(-xh, xh, bb);
+        const float v = 2.f * xh;
+        bh[k] = HE::to(HE::from(v));
+        bl[k] = v - bh[k];
+      }
+      if (bb < -30000.f) {  // farther than any target can see: contributes 0
+#pragma unroll
+        for (int k = 0; k < D; ++k) bh[k] = bl[k] = 0.f;
+        bb = -30000.f;
+      }
+      bh[D] = HE::to(HE::from(bb));
+      bl[D] = bb - bh[D];
+      uint32_t kw[L::KV / 2];
+#pragma unroll
+      for (int w = 0; w < L::KV / 2; ++w)
+        kw[w] = HE::pack(kv_value<D>(bh, bl, 2 * w, false), kv_value<D>(bh, bl, 2 * w + 1, false));
+      // row of source j: its permuted slot within its 16-source block
+      uint4* dst = reinterpret_cast<uint4*>(kv + ((j & ~15) + umx::src_slot(j & 15)) * KVW);
+#pragma unroll
+      for (int w = 0; w < L::KV / 8; ++w) dst[w] = make_uint4(kw[4 * w], kw[4 * w + 1], kw[4 * w + 2], kw[4 * w + 3]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&kready[r & 1]);
+      return true;
+    };
+    // tile r's Y (this group's YW columns) into the Kahan sums; Y buffer r & 1
+    // is handed back and, every MMA of tile r being complete, its stage refilled
+    auto fold_y = [&](int r) -> bool {
+      const int yb = r & 1;
+      if (!__all_sync(0xffffffffu, wait(&yfull[yb], (r >> 1) & 1))) return false;
+      fence_after();
+      uint32_t yv[8];
+      ld8(tmem + y_col + (uint32_t)(YN * yb) + lanes + (uint32_t)(YW * grp), yv);
+      wait_ld();
+#pragma unroll
+      for (int c = 0; c < YW; ++c) kahan_add(Ssum[c], Scomp[c], __uint_as_float(yv[c]));
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&yfree[yb]);
+      if (tid == 0 && r + URS < nt) {
+        fence_proxy_async_smem();
+        issue(r + URS);
+        ++issued;
+      }
+      return true;
+    };
+    // rows of this lane's B-fragment columns (sources src_perm(nt, g), stored
+    // at slot 8 nt + g of their block)
+    const int js0 = g, js1 = 8 + g;
+    bool ok = nt > 0 ? make_k(0) : true;
+    for (int r = 0; r < nt && ok; ++r) {
+      ok = __all_sync(0xffffffffu, wait(&kready[r & 1], (uint32_t)(r >> 1) & 1));
+      if (!ok) break;
+      const uint32_t* kv = kvb + (r & 1) * TS * KVW;
+      for (int h2 = 0; h2 < CPT / 2 && ok; ++h2) {
+        const int c = r * CPT + grp + 2 * h2, b = c % NBUF, q = c % CPT;
+        if (c >= NBUF) {  // the P Q MMAs that last read buffer b are complete
+          ok = __all_sync(0xffffffffu, wait(&pdone[b], (uint32_t)(c / NBUF - 1) & 1));
+          if (!ok) break;
+        }
+        fence_after();
+#pragma unroll 1
+        for (int hf = 0; hf < 2; ++hf) {  // 32 sources: tensor-memory columns 32 hf on
+          // B fragments of the two 16-source blocks, shared by both m-tiles
+          uint32_t bfr[2][2][L::KSTEPS][2];
+#pragma unroll
+          for (int k2 = 0; k2 < 2; ++k2) {
+            const int j0 = NC * q + 32 * hf + 16 * k2;
+#pragma unroll
+            for (int ks = 0; ks < L::KSTEPS; ++ks) {
+              bfr[k2][0][ks][0] = kv[(j0 + js0) * KVW + 8 * ks + t];
+              bfr[k2][0][ks][1] = kv[(j0 + js0) * KVW + 8 * ks + t + 4];
+              bfr[k2][1][ks][0] = kv[(j0 + js1) * KVW + 8 * ks + t];
+              bfr[k2][1][ks][1] = kv[(j0 + js1) * KVW + 8 * ks + t + 4];
+            }
+          }
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            uint32_t ph[8], pl[8];
+#pragma unroll
+            for (int k2 = 0; k2 < 2; ++k2) {
+              float e0[4], e1[4];
+              mma16816_z(e0, afr[mt][0], bfr[k2][0][0][0], bfr[k2][0][0][1]);
+              mma16816_z(e1, afr[mt][0], bfr[k2][1][0][0], bfr[k2][1][0][1]);
+#pragma unroll
+              for (int ks = 1; ks < L::KSTEPS; ++ks) {
+                mma16816<false>(e0, afr[mt][ks], bfr[k2][0][ks][0], bfr[k2][0][ks][1]);
+                mma16816<false>(e1, afr[mt][ks], bfr[k2][1][ks][0], bfr[k2][1][ks][1]);
+              }
+              // registers of tcgen05.st.16x256b: (lane g, column 2t), (g, 2t+1),
+              // (g+8, 2t), (g+8, 2t+1); the second 16 sources in the repeat
+              const float v[4][2] = {{ex2(e0[0]), ex2(e0[1])}, {ex2(e1[0]), ex2(e1[1])},
+                                     {ex2(e0[2]), ex2(e0[3])}, {ex2(e1[2]), ex2(e1[3])}};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                ph[4 * k2 + e] = H::pack(v[e][0], v[e][1]);
+                if (SPLIT) {
+                  const float2 lo = ffma2(H::unpack(ph[4 * k2 + e]), make_float2(-1.f, -1.f),
+                                          make_float2(v[e][0], v[e][1]));
+                  pl[4 * k2 + e] = H::pack(lo.x, lo.y);
+                }
+              }
+            }
+            const uint32_t cols = tmem + lanes + ((uint32_t)(16 * mt) << 16) + (uint32_t)(b * NC + 32 * hf);
+            umx::st_16x256b_x2(cols, ph);
+            if (SPLIT) umx::st_16x256b_x2(cols + 16u, pl);
+          }
+        }
+        wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&pfull[b]);
+        if (h2 == 0) {
+          if (r >= 1 && !(ok = fold_y(r - 1))) break;
+          if (r + 1 < nt && !(ok = make_k(r + 1))) break;
+        }
+      }
+    }
+    if (ok && nt > 0) ok = fold_y(nt - 1);
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) atomicExch(p.err, DEV_TIMEOUT);
+    } else {
+      const int64_t i = row_base + 32 * qw + lane;
+      if (i < p.Nt_pad) {
+#pragma unroll
+        for (int c = 0; c < YW; ++c) {
+          const int col = YW * grp + c;
+          if (col < p.m) p.part[((int64_t)blockIdx.y * p.m + col) * p.Nt_pad + i] = (double)Ssum[c] - (double)Scomp[c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (abort_flag) {
+    // drain (bounded): copies in flight before the shared memory is released
+    if (tid == 0)
+      for (int rr = 0; rr < issued; ++rr) mbar_wait_bounded(&bars[rr % URS], (rr / URS) & 1);
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------------
 // High-dimensional single-column product on the 5th-generation tensor cores
 // (tcgen05; the default above 8 dimensions, KRR_OPT_HIGHD_TCGEN05): the
 // contraction of mvp_tch_kernel, the
@@ -1704,11 +2084,35 @@ cudaError_t umma_launch_typed(const TcParams& p, int splits, cudaStream_t st, bo
   return cudaGetLastError();
 }
 
+template <int D, bool SPLIT, bool BF>
+cudaError_t umx_launch_typed(const TcParams& p, int splits, cudaStream_t st, bool dry) {
+  const size_t shm = umx::smem_bytes<D>(SPLIT);
+  static bool done[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 128 && !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(mvp_umx_kernel<D, SPLIT, BF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e) return e;
+    done[dev] = true;
+  }
+  if (dry) return cudaSuccess;
+  dim3 grid((unsigned)(2 * p.nblk), (unsigned)splits);
+  mvp_umx_kernel<D, SPLIT, BF><<<grid, umma::THREADS + 32, shm, st>>>(p); count_launch();
+  return cudaGetLastError();
+}
+
 template <int D>
-cudaError_t umma_dispatch(const TcParams& p, int splits, bool split, bool bf, cudaStream_t st, bool dry) {
-  if (split) return umma_launch_typed<D, true, false>(p, splits, st, dry);
-  return bf ? umma_launch_typed<D, false, true>(p, splits, st, dry)
-            : umma_launch_typed<D, false, false>(p, splits, st, dry);
+cudaError_t umma_dispatch(const TcParams& p, int splits, bool split, bool bf, int kind, cudaStream_t st,
+                          bool dry) {
+  if (kind == 2) {
+    if (split) return umma_launch_typed<D, true, false>(p, splits, st, dry);
+    return bf ? umma_launch_typed<D, false, true>(p, splits, st, dry)
+              : umma_launch_typed<D, false, false>(p, splits, st, dry);
+  }
+  if (split) return umx_launch_typed<D, true, false>(p, splits, st, dry);
+  return bf ? umx_launch_typed<D, false, true>(p, splits, st, dry)
+            : umx_launch_typed<D, false, false>(p, splits, st, dry);
 }
 
 constexpr int TCX_MT = 4;
@@ -1949,14 +2353,14 @@ cudaError_t mvp_umma_partials(Ctx& c, const PointsDev& T, const PointsDev& S, co
   p.s = S.scale;
   p.active = active;
   switch (T.d) {
-    case 1: return umma_dispatch<1>(p, splits, split, bf, st, dry);
-    case 2: return umma_dispatch<2>(p, splits, split, bf, st, dry);
-    case 3: return umma_dispatch<3>(p, splits, split, bf, st, dry);
-    case 4: return umma_dispatch<4>(p, splits, split, bf, st, dry);
-    case 5: return umma_dispatch<5>(p, splits, split, bf, st, dry);
-    case 6: return umma_dispatch<6>(p, splits, split, bf, st, dry);
-    case 7: return umma_dispatch<7>(p, splits, split, bf, st, dry);
-    case 8: return umma_dispatch<8>(p, splits, split, bf, st, dry);
+    case 1: return umma_dispatch<1>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 2: return umma_dispatch<2>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 3: return umma_dispatch<3>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 4: return umma_dispatch<4>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 5: return umma_dispatch<5>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 6: return umma_dispatch<6>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 7: return umma_dispatch<7>(p, splits, split, bf, c.tcgen05_kind, st, dry);
+    case 8: return umma_dispatch<8>(p, splits, split, bf, c.tcgen05_kind, st, dry);
     default: return cudaErrorNotSupported;
   }
 }

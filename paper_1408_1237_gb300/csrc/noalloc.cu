@@ -140,6 +140,8 @@ krr_status setup_device(int dev, DeviceScratch*& out) {
     d.ctx.device = dev;
     d.ctx.num_sms = sms;
     d.ctx.allow_tcx = false;
+    d.ctx.tcgen05_auto = false;  // the regions are laid out for the mma.sync kernels
+    d.ctx.use_tcgen05 = false;
     size_t off = 0;
     for (const Region& r : kRegions) {
       // each region with its real (256-byte rounded) size; the workspace is

@@ -133,13 +133,14 @@ def test_block_batch_shaped_problem(K, oracle_mod):
         assert ib[c]["status"] == K.KRR_OK and rel <= 1e-6, (c, rel, ib[c])
 
 
-def test_block_solve_on_tcgen05_kernel(K, oracle_mod):
-    # the inner multi-column products on the tcgen05 / tensor-memory kernel
+@pytest.mark.parametrize("kind", [1, 2])
+def test_block_solve_on_tcgen05_kernel(K, oracle_mod, kind):
+    # the inner multi-column products on each tcgen05 kernel
     p = inputs.small_problem(seed=21, N=1200)
     B = np.random.default_rng(22).standard_normal((6, 1200)).astype(np.float32)
     h = K.Handle()
     try:
-        K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h)
+        K.krr_set_option(K.KRR_OPT_TCGEN05, kind, handle=h)
         opts = K.default_opts(delta=p["delta"], inner_tol=p["inner_tol"])
         Xb, ib = K.krr_fgmres_solve(_dev(p["X"]), _dev(B), p["sigma"], p["gamma"], opts=opts, handle=h)
     finally:

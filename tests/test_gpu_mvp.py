@@ -208,20 +208,23 @@ def test_mvp_multi_rhs_direct_form_blocks(K, oracle_mod, m, d, sigma, normal):
         assert scaled_error(oracle_mod, X, Q[c], Y[c], sigma, 1e-2) <= TOL_FP32, c
 
 
-@pytest.mark.parametrize("m,d,prec,bound", [(16, 3, "fp32", TOL_FP32), (5, 2, "fp32", TOL_FP32),
-                                            (16, 8, "fp32", TOL_FP32), (16, 3, "fp16", 2e-3),
-                                            (7, 2, "bf16", 2e-2)])
-def test_mvp_multi_rhs_tcgen05_kernel(K, oracle_mod, m, d, prec, bound):
-    # the multi-column tensor-core product on the tcgen05 / tensor-memory
-    # kernel (handle option): same bar as the default mma.sync kernel
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("m,d,prec,bound,N", [(16, 3, "fp32", TOL_FP32, 6000), (5, 2, "fp32", TOL_FP32, 6000),
+                                              (16, 8, "fp32", TOL_FP32, 6000), (16, 3, "fp16", 2e-3, 6000),
+                                              (7, 2, "bf16", 2e-2, 6000), (16, 5, "fp32", TOL_FP32, 9001),
+                                              (12, 1, "fp32", TOL_FP32, 4097), (16, 4, "bf16", 2e-2, 5000)])
+def test_mvp_multi_rhs_tcgen05_kernel(K, oracle_mod, kind, m, d, prec, bound, N):
+    # the multi-column tensor-core product on each kernel (handle option
+    # KRR_OPT_TCGEN05: 0 = mma.sync; 1 = exponent by mma.sync, P stored to
+    # tensor memory; 2 = exponent in tensor memory; 3 = the automatic
+    # choice): the same bar for all
     rng = np.random.default_rng(300 + m + d)
-    N = 6000
     X = rng.random((N, d)).astype(np.float32)
     Q = rng.standard_normal((m, N)).astype(np.float32)
     sigma = 0.08 if d <= 3 else 0.5
     h = K.Handle()
     try:
-        K.krr_set_option(K.KRR_OPT_TCGEN05, 1, handle=h)
+        K.krr_set_option(K.KRR_OPT_TCGEN05, kind, handle=h)
         Y = K.krr_kernel_mvp(_dev(X), _dev(Q), sigma, 1e-3, prec=prec, handle=h).cpu().numpy()
     finally:
         h.close()
@@ -302,3 +305,30 @@ def test_mvp_multi_direct_tensor_batch_shape_full_size(K, oracle_mod):
     rows = inputs.sample_rows(N, 256, seed=5)
     for c in (0, 5, 15):
         assert scaled_error(oracle_mod, X, Q[c], Y[c], 1.0, 1e-3, rows) <= TOL_FP32, c
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_mvp_multi_rhs_tcgen05_full_size_sampled(K, oracle_mod, kind):
+    # the 2^20-point cube with 16 columns (the multi-column benchmark shape)
+    # on each tcgen05 kernel, sampled rows against the oracle
+    p = inputs.mvp_problem(seed=0, m=16)
+    h = K.Handle()
+    try:
+        K.krr_set_option(K.KRR_OPT_TCGEN05, kind, handle=h)
+        Y = K.krr_kernel_mvp(_dev(p["X"]), _dev(p["Q"].T.copy()), p["sigma"], p["gamma"], handle=h).cpu().numpy()
+    finally:
+        h.close()
+    rows = inputs.sample_rows(p["X"].shape[0], 64, seed=11)
+    for c in (0, 7, 15):
+        assert scaled_error(oracle_mod, p["X"], p["Q"][:, c], Y[c], p["sigma"], p["gamma"], rows) <= TOL_FP32, c
+
+
+def test_tcgen05_option_range(K):
+    h = K.Handle()
+    try:
+        for bad in (-1, 4):
+            with pytest.raises(K.KrrError) as ei:
+                K.krr_set_option(K.KRR_OPT_TCGEN05, bad, handle=h)
+            assert ei.value.status == K.KRR_ERR_INVALID_ARG
+    finally:
+        h.close()
