@@ -1658,7 +1658,7 @@ __global__ void __launch_bounds__(umma::THREADS + 32, 2) mvp_umx_kernel(const Tc
           if (!ok) break;
         }
         fence_after();
-#pragma unroll 1
+#pragma unroll
         for (int hf = 0; hf < 2; ++hf) {  // 32 sources: tensor-memory columns 32 hf on
           // B fragments of the two 16-source blocks, shared by both m-tiles
           uint32_t bfr[2][2][L::KSTEPS][2];
