@@ -431,7 +431,7 @@ def run_libkrr(args):
     # gradient, and the Matern / high-d / autotune extras.  They run on one
     # GPU only (a multi-GPU run measures the product) and in this order while
     # the wall-clock budget lasts; a skipped form is recorded as such.
-    solve, grad, matern, tuned, highd = {}, None, None, None, None
+    solve, grad, matern, tuned, highd, latency = {}, None, None, None, None, None
     skipped = []
     extras = world == 1
     sharded = sharded_product(K, torch, inputs, rank, world, dev, stream) if world > 1 else None
@@ -466,6 +466,8 @@ def run_libkrr(args):
         if args.autotune and budget_left("autotune"):
             tuned = autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, stream,
                                   kern_ms, m16_ms)
+        if budget_left("small_product_latency"):
+            latency = small_product_latency(K, torch, rank, dev)
 
     if rank == 0:
         line = {
@@ -497,6 +499,7 @@ def run_libkrr(args):
             "mll_grad": grad,
             "matern": matern,
             "autotune": tuned,
+            "small_product_latency": latency,
             "highd": highd,
             "sharded_product": sharded,
             "cpu_baseline": cpu,
@@ -831,6 +834,44 @@ def autotune_form(K, torch, inputs, args, X, q, Q16, sigma, gamma, rank, dev, st
         out["batching_subset_4x8192"] = batching_form(K, torch, inputs, sub, rank, dev, stream, handle=h,
                                                       plain=False)
     h.close()
+    return out
+
+
+def small_product_latency(K, torch, rank, dev, N=4096, reps=200):
+    """Latency of one small single-column product (N = 4096 uniform points in
+    the unit cube, d = 3), device arrays, mean over `reps` back-to-back calls
+    between two synchronisations: krr_kernel_mvp (prepares the points and
+    waits for their block counts every call), krr_kernel_mvp_points on a
+    prepared point set (no host synchronisation), and the same product
+    captured once in a CUDA graph and replayed."""
+    import numpy as np
+    rng = np.random.default_rng(4242 + rank)
+    X = torch.from_numpy(rng.random((N, 3)).astype(np.float32)).to(dev)
+    q = torch.from_numpy(rng.standard_normal(N).astype(np.float32)).to(dev)
+    y = torch.empty_like(q)
+    h = K.Handle()
+    out = {"N": N, "d": 3, "reps": reps}
+    try:
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize(dev)
+            return (time.perf_counter() - t0) / reps * 1e6
+        out["kernel_mvp_us"] = timed(lambda: K.krr_kernel_mvp(X, q, 0.05, 1e-3, out=y, handle=h))
+        P = K.Points(X, 0.05, handle=h)
+        try:
+            out["points_us"] = timed(lambda: K.krr_kernel_mvp_points(P, q, 1e-3, out=y))
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                K.krr_kernel_mvp_points(P, q, 1e-3, out=y)
+            out["graph_replay_us"] = timed(g.replay)
+        finally:
+            P.close()
+    finally:
+        h.close()
     return out
 
 

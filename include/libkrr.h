@@ -235,6 +235,45 @@ krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d,
                           float sigma, float gamma, const float* Q, int m,
                           float* Y, krr_precision prec, void* stream);
 
+/* ----------------------------------------------------------- prepared point sets
+ * Repeated products over one point set (a serving loop, a caller's own
+ * iterative method, many weight vectors): the Morton sort, packing and block
+ * metadata of krr_kernel_mvp are done once, and each product then runs with
+ * no host synchronisation, so it can be captured in a CUDA graph.
+ *
+ * krr_points_create prepares X (N x d, host or device, row-major float32)
+ * for the kernel width sigma and the handle's kernel family (KRR_OPT_KERNEL
+ * at creation; later changes of the option do not affect the object).  Its
+ * device buffers belong to the object, inside h's workspace; X may be
+ * overwritten or freed once the call returns.  The call waits for the
+ * preparation once, to read the block counts that size the product grids.
+ * On success *out is the object; destroy it with krr_points_destroy before
+ * krr_destroy(h), and use it only with h.  Errors as for krr_kernel_mvp. */
+typedef struct krr_points_s* krr_points;
+krr_status krr_points_create(krr_handle h, const float* X, int64_t N, int d,
+                             float sigma, krr_points* out, void* stream);
+
+/* Y = (K_hat + gamma I) Q over a prepared point set (Eqs. 1-3), as
+ * krr_kernel_mvp computes it (the same kernels, hence the same results):
+ * Q, Y: DEVICE arrays, N x m column-major, 1 <= m <= 64; Y must not alias
+ * Q.  Host arrays: KRR_ERR_INVALID_ARG.  The handle's product options
+ * (KRR_OPT_TCGEN05, _DIRECT_TENSOR, _HIGHD_TCGEN05, _AUTOTUNE, the row
+ * shards) apply as at the call.  No host synchronisation.  The products'
+ * scratch belongs to the point set: once a product of this (m, prec) has
+ * run on it, a call allocates nothing and can be captured in a CUDA graph,
+ * which stays valid until krr_points_destroy (the first call of a shape may
+ * allocate and must not be captured; neither may a larger m or another
+ * precision after the capture).  Device-side errors (a timed-out bounded
+ * wait) are reported by krr_points_destroy. */
+krr_status krr_kernel_mvp_points(krr_handle h, krr_points P, const float* Q,
+                                 int m, float gamma, float* Y,
+                                 krr_precision prec, void* stream);
+
+/* Waits for the device, frees the object's device buffers and reports a
+ * device-side error of its products (KRR_ERR_TIMEOUT; the object is freed
+ * anyway).  NULL P: KRR_OK.  P from another handle: KRR_ERR_INVALID_ARG. */
+krr_status krr_points_destroy(krr_handle h, krr_points P);
+
 /* Prediction product of Eq. GPR_mean / Eq. Kriging:
  *     Y[t,c] = sum_j exp(-|xt_t - xs_j|^2 / (2 sigma^2)) Q[j,c]
  * Xt: Nt x d targets, Xs: Ns x d sources, Q: Ns x m, Y: Nt x m (no diagonal

@@ -93,6 +93,9 @@ _SIGNATURES = {
     "krr_kernel_mvp_noalloc": ([_vp, _i64, _int, _f, _f, _vp, _int, _vp, _vp], _int),
     "krr_profile_read": ([_vp, ctypes.POINTER(krr_profile)], _int),
     "krr_selftest_wait_timeout": ([_vp, ctypes.c_longlong, _vp], _int),
+    "krr_points_create": ([_vp, _vp, _i64, _int, _f, ctypes.POINTER(_vp), _vp], _int),
+    "krr_kernel_mvp_points": ([_vp, _vp, _vp, _int, _f, _vp, _int, _vp], _int),
+    "krr_points_destroy": ([_vp, _vp], _int),
 }
 
 
@@ -235,6 +238,47 @@ def krr_kernel_mvp(X, Q, sigma, gamma, prec="fp32", out=None, handle=None, strea
     Y = out if out is not None else _empty_like_cols(Q, m, N)
     h.check(lib().krr_kernel_mvp(h.h, _ptr(X), N, d, sigma, gamma, _ptr(Q), m, _ptr(Y),
                                  PRECISION[prec], _stream(stream, X, Q, Y)))
+    return Y
+
+
+class Points:
+    """A prepared point set (krr_points_create): products over it with
+    krr_kernel_mvp_points run with no host synchronisation.  Close it (or use
+    it as a context manager) before its handle."""
+
+    def __init__(self, X, sigma, handle=None, stream=None):
+        self.handle = handle or default_handle()
+        _check_f32(X, "X")
+        self.N, self.d = X.shape
+        p = _vp()
+        self.handle.check(lib().krr_points_create(self.handle.h, _ptr(X), self.N, self.d, sigma,
+                                                  ctypes.byref(p), _stream(stream, X)))
+        self.p = p
+
+    def close(self):
+        if self.p and self.handle.h:
+            p, self.p = self.p, None
+            self.handle.check(lib().krr_points_destroy(self.handle.h, p))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def krr_points_create(X, sigma, handle=None, stream=None):
+    return Points(X, sigma, handle=handle, stream=stream)
+
+
+def krr_kernel_mvp_points(points, Q, gamma, prec="fp32", out=None, stream=None):
+    """Y = (K_hat + gamma I) Q over a prepared point set; Q and Y device
+    tensors, (N,) or (m, N)."""
+    _check_f32(Q, "Q")
+    m = _cols(Q, points.N)
+    Y = out if out is not None else _empty_like_cols(Q, m, points.N)
+    points.handle.check(lib().krr_kernel_mvp_points(points.handle.h, points.p, _ptr(Q), m, gamma, _ptr(Y),
+                                                    PRECISION[prec], _stream(stream, Q, Y)))
     return Y
 
 

@@ -32,3 +32,14 @@ krr_status device_view_d(Ctx& c, const char* slot, const double* p, size_t count
 struct krr_handle_s {
   krr::Ctx ctx;
 };
+
+// A prepared point set (krr_points_create).  It owns a context of its own:
+// the sorted layout, block metadata and every scratch buffer of its products
+// live in that context's workspace, so work on the handle never reallocates
+// what a captured graph of its products refers to.  The handle's product
+// options are copied into it at each call.
+struct krr_points_s {
+  krr_handle_s* h = nullptr;
+  krr::Ctx ctx;
+  krr::PointsDev P;
+};

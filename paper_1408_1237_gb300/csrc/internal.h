@@ -31,6 +31,8 @@ struct Workspace {
   bool fixed = false;
   cudaError_t get(const std::string& name, size_t bytes, void** out);
   void release_all();
+  // frees the buffers whose names start with prefix
+  void release_prefix(const std::string& prefix);
 };
 
 // Targets are handled in warp blocks of WB = 32*T consecutive sorted points

@@ -44,6 +44,17 @@ void Workspace::release_all() {
   slots.clear();
 }
 
+void Workspace::release_prefix(const std::string& prefix) {
+  for (auto it = slots.begin(); it != slots.end();) {
+    if (it->first.compare(0, prefix.size(), prefix) == 0) {
+      cudaFree(it->second.p);
+      it = slots.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 std::string tune_key(const Ctx& c, const char* kind, const PointsDev& Tp, const PointsDev& Sp, int m,
                      int prec) {
   char buf[256];
@@ -51,6 +62,50 @@ std::string tune_key(const Ctx& c, const char* kind, const PointsDev& Tp, const 
            (long long)Sp.N, Tp.d, Tp.kfam, m, prec, c.plan_slots, c.tcgen05_auto ? 3 : c.use_tcgen05 ? c.tcgen05_kind : 0,
            (long long)Tp.h_nexp, (long long)Tp.h_sb_nexp);
   return buf;
+}
+
+// The product over prepared points (both krr_kernel_mvp and
+// krr_kernel_mvp_points): gather Q into sorted order, then one single-column
+// launch or multi-column passes of at most MAX_COLS, each writing its
+// columns of Y in original order.  Row shards as set on the handle.  No host
+// synchronisation.
+cudaError_t product_prepared(Ctx& c, const PointsDev& P, const float* dQ, int m, float gamma,
+                             krr_precision prec, float* dY, cudaStream_t st) {
+  struct RowRange {
+    Ctx& c;
+    ~RowRange() {
+      c.row_lo = 0;
+      c.row_hi = INT64_MAX;
+    }
+  } row_range{c};
+  if (c.shard_count > 1) {
+    c.row_lo = (int64_t)SB * (P.nsb * c.shard_index / c.shard_count);
+    c.row_hi = (int64_t)SB * (P.nsb * (c.shard_index + 1) / c.shard_count);
+  }
+  const int64_t N = P.N;
+  void* qs;
+  cudaError_t e;
+  if ((e = c.ws.get("mvp.qs", sizeof(float) * P.Npad * m, &qs))) return e;
+  if ((e = gather_sorted(dQ, N, m, P.perm, P.Npad, (float*)qs, st))) return e;
+  if (m == 1) {
+    MvpOut o;
+    o.perm = P.perm;
+    o.out_orig = dY;
+    return mvp_launch(c, P, P, (const float*)qs, (const float*)qs, gamma, prec, o, st);
+  }
+  // columns in as few passes of at most MAX_COLS as possible: each kernel
+  // value serves every column of a pass
+  const int passes = (m + MAX_COLS - 1) / MAX_COLS;
+  const int width = (m + passes - 1) / passes;
+  for (int col0 = 0; col0 < m; col0 += width) {
+    const int mc = std::min(width, m - col0);
+    const float* qc = (const float*)qs + (size_t)col0 * P.Npad;
+    MvpOut o;
+    o.perm = P.perm;
+    o.out_orig = dY + (size_t)col0 * N;
+    if ((e = mvp_multi_launch(c, P, P, qc, mc, qc, gamma, prec, o, st))) return e;
+  }
+  return cudaSuccess;
 }
 
 bool can_tune(const Ctx& c, cudaStream_t st) {
@@ -365,45 +420,115 @@ krr_status krr_kernel_mvp(krr_handle h, const float* X, int64_t N, int d, float 
   PointsDev P;
   cudaError_t e = prepare_points(c, dX, N, d, sigma, "pts", P, st);
   if (e) return cuda_error(c, e, fn);
-  struct RowRange {
-    Ctx& c;
-    ~RowRange() {
-      c.row_lo = 0;
-      c.row_hi = INT64_MAX;
-    }
-  } row_range{c};
-  if (sharded) {
-    c.row_lo = (int64_t)SB * (P.nsb * c.shard_index / c.shard_count);
-    c.row_hi = (int64_t)SB * (P.nsb * (c.shard_index + 1) / c.shard_count);
-  }
-  void* qs;
-  if ((e = c.ws.get("mvp.qs", sizeof(float) * P.Npad * m, &qs))) return cuda_error(c, e, fn);
-  if ((e = gather_sorted(dQ, N, m, P.perm, P.Npad, (float*)qs, st))) return cuda_error(c, e, fn);
-  if (m == 1) {
-    MvpOut o;
-    o.perm = P.perm;
-    o.out_orig = dY;
-    if ((e = mvp_launch(c, P, P, (const float*)qs, (const float*)qs, gamma, prec, o, st)))
-      return cuda_error(c, e, fn);
-  } else {
-    // columns in as few passes of at most MAX_COLS as possible: each kernel
-    // value serves every column of a pass
-    const int passes = (m + MAX_COLS - 1) / MAX_COLS;
-    const int width = (m + passes - 1) / passes;
-    for (int col0 = 0; col0 < m; col0 += width) {
-      const int mc = std::min(width, m - col0);
-      const float* qc = (const float*)qs + (size_t)col0 * P.Npad;
-      MvpOut o;
-      o.perm = P.perm;
-      o.out_orig = dY + (size_t)col0 * N;
-      if ((e = mvp_multi_launch(c, P, P, qc, mc, qc, gamma, prec, o, st))) return cuda_error(c, e, fn);
-    }
-  }
+  if ((e = product_prepared(c, P, dQ, m, gamma, prec, dY, st))) return cuda_error(c, e, fn);
   if (sY) {
     if ((e = cudaMemcpyAsync(Y, dY, sizeof(float) * N * m, cudaMemcpyDeviceToHost, st)))
       return cuda_error(c, e, fn);
   }
   if (sX || sQ || sY) return read_device_error(c, st, fn);
+  return KRR_OK;
+}
+
+// The handle's product options, copied into a point set's own context.
+static void copy_product_options(Ctx& dst, const Ctx& src) {
+  dst.allow_tcx = src.allow_tcx;
+  dst.use_tcgen05 = src.use_tcgen05;
+  dst.tcgen05_kind = src.tcgen05_kind;
+  dst.tcgen05_auto = src.tcgen05_auto;
+  dst.highd_tcgen05 = src.highd_tcgen05;
+  dst.direct_tensor = src.direct_tensor;
+  dst.kernel_family = src.kernel_family;
+  dst.autotune = src.autotune;
+  dst.shard_count = src.shard_count;
+  dst.shard_index = src.shard_index;
+}
+
+static void free_points(krr_points_s* pts) {
+  release_context(pts->ctx);
+  pts->ctx.ws.release_all();
+  cudaFree(pts->ctx.d_err);
+  delete pts;
+}
+
+krr_status krr_points_create(krr_handle h, const float* X, int64_t N, int d, float sigma, krr_points* out,
+                             void* stream) {
+  NvtxRange nvtx_range("krr_points_create");
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  const char* fn = "krr_points_create";
+  if (!out) return set_error(c, KRR_ERR_INVALID_ARG, "%s: out is NULL", fn);
+  *out = nullptr;
+  krr_status s = check_points(c, fn, X, N, d, sigma);
+  if (s) return s;
+  if (N == 0) return set_error(c, KRR_ERR_INVALID_ARG, "%s: empty point set", fn);
+  cudaStream_t st = (cudaStream_t)stream;
+  float* dX;
+  bool sX;
+  if ((s = device_view(c, "stage.X", X, (size_t)N * d, true, st, &dX, &sX))) return s;
+  krr_points_s* pts = new (std::nothrow) krr_points_s;
+  if (!pts) return set_error(c, KRR_ERR_OOM, "%s: out of host memory", fn);
+  pts->h = h;
+  Ctx& pc = pts->ctx;
+  pc.device = c.device;
+  pc.num_sms = c.num_sms;
+  copy_product_options(pc, c);
+  cudaError_t e = cudaMalloc(&pc.d_err, sizeof(int));
+  if (!e) e = cudaMemsetAsync(pc.d_err, 0, sizeof(int), st);
+  if (!e) e = prepare_points(pc, dX, N, d, sigma, "points", pts->P, st);  // waits once
+  if (e) {
+    free_points(pts);
+    return cuda_error(c, e, fn);
+  }
+  pc.ws.release_prefix("sort.");  // the sort's scratch is not needed again
+  pc.h_status = c.h_status;       // the handle's pinned status word, for this one read
+  s = read_device_error(pc, st, fn);
+  pc.h_status = nullptr;
+  if (s) {
+    c.last_error = pc.last_error;
+    free_points(pts);
+    return s;
+  }
+  *out = pts;
+  return KRR_OK;
+}
+
+krr_status krr_kernel_mvp_points(krr_handle h, krr_points P, const float* Q, int m, float gamma, float* Y,
+                                 krr_precision prec, void* stream) {
+  NvtxRange nvtx_range("krr_kernel_mvp_points");
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  const char* fn = "krr_kernel_mvp_points";
+  if (!P || P->h != h) return set_error(c, KRR_ERR_INVALID_ARG, "%s: point set of another handle", fn);
+  if (!(gamma >= 0.f) || !std::isfinite(gamma))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: gamma must be finite and >= 0", fn);
+  if (m < 1 || m > 64) return set_error(c, KRR_ERR_INVALID_ARG, "%s: m = %d out of range [1, 64]", fn, m);
+  if (prec != KRR_FP32 && prec != KRR_BF16 && prec != KRR_FP16)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: unknown precision %d", fn, (int)prec);
+  if (!Q || !Y) return set_error(c, KRR_ERR_INVALID_ARG, "%s: Q or Y is NULL", fn);
+  if ((const void*)Y == (const void*)Q) return set_error(c, KRR_ERR_INVALID_ARG, "%s: Y aliases Q", fn);
+  if (!is_device_ptr(c, Q) || !is_device_ptr(c, Y))
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: Q and Y must be device arrays", fn);
+  if (c.shard_index >= c.shard_count)
+    return set_error(c, KRR_ERR_INVALID_ARG, "%s: shard index %d >= shard count %d", fn, c.shard_index,
+                     c.shard_count);
+  Ctx& pc = P->ctx;
+  copy_product_options(pc, c);
+  cudaError_t e = product_prepared(pc, P->P, Q, m, gamma, prec, Y, (cudaStream_t)stream);
+  if (e) return cuda_error(c, e, fn);
+  return KRR_OK;
+}
+
+krr_status krr_points_destroy(krr_handle h, krr_points P) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  if (!P) return KRR_OK;
+  if (P->h != h) return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_points_destroy: point set of another handle");
+  cudaDeviceSynchronize();  // products in flight finish before their buffers go
+  int err = DEV_OK;
+  cudaMemcpy(&err, P->ctx.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  free_points(P);
+  if (err == DEV_TIMEOUT)
+    return set_error(h->ctx, KRR_ERR_TIMEOUT, "krr_points_destroy: a product's bounded device wait ran out");
+  if (err != DEV_OK) return set_error(h->ctx, KRR_ERR_CUDA, "krr_points_destroy: device error %d", err);
   return KRR_OK;
 }
 

@@ -97,6 +97,12 @@ int main(void) {
     }
     if (krr_kernel_mvp(NULL, NULL, 1, 3, 1.f, 0.f, NULL, 1, NULL, KRR_FP32, NULL)
         != KRR_ERR_INVALID_ARG) return 9;
+    krr_points pts = NULL;
+    if (krr_points_create(NULL, NULL, 1, 3, 1.f, &pts, NULL) != KRR_ERR_INVALID_ARG || pts != NULL)
+        return 11;
+    if (krr_kernel_mvp_points(NULL, NULL, NULL, 1, 0.f, NULL, KRR_FP32, NULL) != KRR_ERR_INVALID_ARG)
+        return 12;
+    if (krr_points_destroy(NULL, NULL) != KRR_ERR_INVALID_ARG) return 13;
     printf("ok %d\n", (int)s);
     return 0;
 }
