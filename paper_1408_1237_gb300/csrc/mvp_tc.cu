@@ -1399,11 +1399,10 @@ constexpr size_t smem_bytes(bool split) {
                       sizeof(uint32_t) * 2 * TS * ExpLayout<D>::KV_STRIDE_W;
   return need > umma::SMEM_FLOOR ? need : umma::SMEM_FLOOR;
 }
-// Source of column n of n-tile nt in a 16-source block (see above), and the
-// inverse: the shared-memory row of source j in its block, so that the
-// B-fragment loads of an n-tile read 8 consecutive rows (bank-conflict free
-// with the K-vector stride of ExpLayout).
-__device__ __forceinline__ int src_perm(int nt, int n) { return 2 * n - (n & 1) + 2 * nt; }
+// Column n of n-tile nt in a 16-source block takes source 2n - (n mod 2) +
+// 2 nt (see above).  Its inverse gives the shared-memory row of source j in
+// its block, so that the B-fragment loads of an n-tile read 8 consecutive
+// rows (bank-conflict free with the K-vector stride of ExpLayout).
 __device__ __forceinline__ int src_slot(int j) { return 8 * ((j >> 1) & 1) + 2 * (j >> 2) + (j & 1); }
 __device__ __forceinline__ void st_16x256b_x2(uint32_t taddr, const uint32_t (&v)[8]) {
   asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
@@ -1510,7 +1509,12 @@ __global__ void __launch_bounds__(umma::THREADS + 32, 2) mvp_umx_kernel(const Tc
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t y_col = NBUF * NC;  // Y buffers at y_col and y_col + YN
+  // Y buffers at y_col and y_col + YW2: with the split, each holds Ph Qh +
+  // Pl Qh in its first YN columns and Ph Ql in the next YN (one N = 32 MMA
+  // computes Ph [Qh | Ql]); the halves are added when Y is folded
+  constexpr uint32_t YW2 = SPLIT ? 2 * YN : YN;
+  static_assert(NBUF * NC + 2 * YW2 <= TMEM_COLS, "tensor-memory columns");
+  const uint32_t y_col = NBUF * NC;
   const int t_begin = blockIdx.y * p.tiles_per_split;
   const int nt = min(p.ntiles, t_begin + p.tiles_per_split) - t_begin;
 
@@ -1538,6 +1542,7 @@ __global__ void __launch_bounds__(umma::THREADS + 32, 2) mvp_umx_kernel(const Tc
     // ================= MMA warp: chunk c's P Q once its P is stored
     if (lane == 0) {
       const uint32_t id_y = idesc(BF ? 1 : 0, YN, ROWS);
+      const uint32_t id_y2 = idesc(BF ? 1 : 0, 2 * YN, ROWS);
       uint32_t n_yf[2] = {0, 0};
       const int total = nt * CPT;
       bool ok = true;
@@ -1551,18 +1556,20 @@ __global__ void __launch_bounds__(umma::THREADS + 32, 2) mvp_umx_kernel(const Tc
         if (!ok) break;
         fence_after();
         const uint32_t qh_addr = smem_addr(stages + (r % URS) * SBYTES + D * TS * 4);
-        const uint32_t ql_addr = qh_addr + QTILE;
         const uint32_t pbuf = tmem + (uint32_t)(b * NC);
-        const uint32_t yd = tmem + y_col + (uint32_t)(YN * yb);
+        const uint32_t yd = tmem + y_col + YW2 * (uint32_t)yb;
 #pragma unroll
         for (int ks = 0; ks < NC / 16; ++ks) {
           const uint32_t qoff = (uint32_t)((NC / 8) * q + 2 * ks) * 128u;
           const uint32_t pa = pbuf + (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
           const int acc = (q > 0 || ks > 0) ? 1 : 0;
-          mma_ts(yd, pa, sdesc(qh_addr + qoff, (TS / 8) * 128), id_y, acc);
           if (SPLIT) {
+            // B rows 0-15 are Qh, rows 16-31 the Ql tile that follows it (the
+            // 8-row-group stride is a quarter of a tile): Ph [Qh | Ql]
+            mma_ts(yd, pa, sdesc(qh_addr + qoff, (TS / 8) * 128), id_y2, acc);
             mma_ts(yd, pa + 16u, sdesc(qh_addr + qoff, (TS / 8) * 128), id_y, 1);
-            mma_ts(yd, pa, sdesc(ql_addr + qoff, (TS / 8) * 128), id_y, 1);
+          } else {
+            mma_ts(yd, pa, sdesc(qh_addr + qoff, (TS / 8) * 128), id_y, acc);
           }
         }
         commit(&pdone[b]);
@@ -1628,11 +1635,14 @@ __global__ void __launch_bounds__(umma::THREADS + 32, 2) mvp_umx_kernel(const Tc
       const int yb = r & 1;
       if (!__all_sync(0xffffffffu, wait(&yfull[yb], (r >> 1) & 1))) return false;
       fence_after();
-      uint32_t yv[8];
-      ld8(tmem + y_col + (uint32_t)(YN * yb) + lanes + (uint32_t)(YW * grp), yv);
+      uint32_t yv[8], yl[8];
+      const uint32_t ya = tmem + y_col + YW2 * (uint32_t)yb + lanes + (uint32_t)(YW * grp);
+      ld8(ya, yv);
+      if (SPLIT) ld8(ya + YN, yl);
       wait_ld();
 #pragma unroll
-      for (int c = 0; c < YW; ++c) kahan_add(Ssum[c], Scomp[c], __uint_as_float(yv[c]));
+      for (int c = 0; c < YW; ++c)
+        kahan_add(Ssum[c], Scomp[c], SPLIT ? __uint_as_float(yv[c]) + __uint_as_float(yl[c]) : __uint_as_float(yv[c]));
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive1(&yfree[yb]);
