@@ -43,9 +43,9 @@ METRIC = "Gaussian kernel MVP Gpairs/s; FGMRES time-to-1e-6 residual vs plain FP
 TRAFFIC = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "9775246cbc799cc4467e0840befecdb000cb45d1"},
            "bytes": 22374656 + 83717888}
 # the same for the tensor-core exponent path (mvp_tcx_kernel + direct-form tail)
-TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "a191d1b20caefd72496d762b4c4673355068dc96",
-                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "da937f5a3005504548b95ee054bdc697fdaf5412"},
-               "bytes": 22911744 + 92082944 + 17238784 + 0}
+TRAFFIC_TCX = {"sources": {"paper_1408_1237_gb300/csrc/mvp.cu": "c97b0b9bbaaeb44ef0f54387704d2631a12ca666",
+                           "paper_1408_1237_gb300/csrc/mvp_tc.cu": "56d5c2079577a7fb0c3bb0e0a57e1d21f79255e6"},
+               "bytes": 22713600 + 92372480 + 17144576 + 0}
 MVP_N, MVP_D = 1 << 20, 3
 
 

@@ -143,11 +143,14 @@ typedef enum {
      *     tensor memory and accumulators in tensor memory;
      *  2: tcgen05.mma for the exponent into tensor memory, loaded,
      *     exponentiated and stored back as P, then Y += P Q as in 1;
-     *  3 (default): 1 for float32 products of more than 8 columns, 0 for
-     *     the others.
+     *  3 (default): 1 for float32 products of more than 8 columns with at
+     *     least 65536 targets at d >= 5 or 131072 at d <= 4, else 0; the
+     *     solvers (block, batched and gradient solves) instead time 0 and 1
+     *     once per product shape when they reserve it (a few products,
+     *     before any graph capture) and keep the faster.
      * Same results to the float32 bar (and the reduced-precision bars).  On
-     * GB300, 16 columns at 2^20 points: float32 406 / 431 / 549 ms, f16
-     * 269 / 261 / 378 ms for 1 / 0 / 2.  Other values: KRR_ERR_INVALID_ARG. */
+     * GB300, 16 columns at 2^20 points: float32 370 / 434 / 552 ms, f16
+     * 260 / 261 / 378 ms for 1 / 0 / 2.  Other values: KRR_ERR_INVALID_ARG. */
     KRR_OPT_TCGEN05 = 1,
     /* value: a krr_kernel_family.  The kernel function every product and
      * solver of this handle uses (default KRR_KERNEL_GAUSSIAN).  Under

@@ -187,17 +187,27 @@ enum TuneVariant : int {
   TV_TENSOR_EXP = 4,     // single-column float32 products may take the tensor-core exponent path
                          // (128-thread CTAs per super-block) instead of the packed CUDA-core kernel
 };
-// Whether the compact blocks of an m-column product of precision prec take
-// a tcgen05 kernel (c.tcgen05_kind) rather than the mma.sync kernel.  The
-// automatic choice takes mvp_umx_kernel for float32 products of more than
+// Whether the compact blocks of an m-column product of precision prec over
+// the targets Tp take a tcgen05 kernel (c.tcgen05_kind) rather than the
+// mma.sync kernel.  The automatic choice (measured on GB300, 16 columns,
+// compact blocks) takes mvp_umx_kernel for float32 products of more than
 // TC5_AUTO_MIN_COLS columns, where the mma.sync kernel's three split P Q
-// MMAs per column tile bound it.
+// MMAs per column tile bound it, once there are enough targets: from 65536
+// at d >= 5 (two exponent contraction steps; 1.25-1.46x at 65536 and
+// 262144, 0.84-0.91x at 16384) and from 131072 at d <= 4 (1.08-1.14x at
+// 262144, 0.90-1.02x at 65536, 0.57-1.0x at 16384).  The solvers refine it
+// per shape by timing both kernels (mvp_multi_reserve).
 constexpr int TC5_AUTO_MIN_COLS = 8;
-inline bool tc5_on(const Ctx& c, int prec, int m) {
-  return c.tcgen05_auto ? (prec == KRR_FP32 && m > TC5_AUTO_MIN_COLS) : c.use_tcgen05;
+constexpr int64_t TC5_AUTO_MIN_N_HIGH_D = 65536, TC5_AUTO_MIN_N_LOW_D = 131072;
+inline bool tc5_auto_choice(int prec, int m, const PointsDev& Tp) {
+  return prec == KRR_FP32 && m > TC5_AUTO_MIN_COLS &&
+         Tp.N >= (Tp.d >= 5 ? TC5_AUTO_MIN_N_HIGH_D : TC5_AUTO_MIN_N_LOW_D);
 }
-inline int current_variant(const Ctx& c, int prec, int m) {
-  return (tc5_on(c, prec, m) ? TV_TCGEN05 : 0) | (c.direct_tensor ? TV_DIRECT_TENSOR : 0) |
+inline bool tc5_on(const Ctx& c, int prec, int m, const PointsDev& Tp) {
+  return c.tcgen05_auto ? tc5_auto_choice(prec, m, Tp) : c.use_tcgen05;
+}
+inline int current_variant(const Ctx& c, int prec, int m, const PointsDev& Tp) {
+  return (tc5_on(c, prec, m, Tp) ? TV_TCGEN05 : 0) | (c.direct_tensor ? TV_DIRECT_TENSOR : 0) |
          (c.allow_tcx ? TV_TENSOR_EXP : 0);
 }
 // Applies the tuned variant of a shape for one product entry point (and puts

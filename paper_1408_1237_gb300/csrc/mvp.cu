@@ -748,7 +748,7 @@ Plan multi_plan_tc(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp, krr_p
   // two CTAs (of 128 targets) per super-block, at most two per SM (tensor memory)
   // one CTA per super-block (mma.sync kernel), or two of 128 targets with at
   // most two per SM (tcgen05 kernel: tensor memory)
-  return make_plan((tc5_on(c, prec, m) ? 2 : 1) * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
+  return make_plan((tc5_on(c, prec, m, Tp) ? 2 : 1) * Tp.h_sb_nexp * NW, (int)(Sp.Npad / TS), c.num_sms,
                    c.plan_slots, c.split_scale);
 }
 // Multi-column products keep the tensor cores to d <= 8 (Gaussian); elsewhere
@@ -852,7 +852,7 @@ int route_splits(const Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, 
 // faster).  Split candidates whose partial sums would exceed TUNE_MAX_BYTES
 // are skipped.
 cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m, krr_precision prec,
-                         cudaStream_t st, const std::string& key) {
+                         cudaStream_t st, const std::string& key, bool tcgen05_only = false) {
   struct Restore {
     Ctx& c;
     bool prof;
@@ -902,9 +902,11 @@ cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m
   // up to 8 dimensions try both kernels for compact blocks and both for
   // direct-form blocks.  The handle's own variant is kept unless another is
   // 2% faster.
-  const int cur = current_variant(c, prec, m);
+  const int cur = current_variant(c, prec, m, Tp);
   std::vector<int> variants{cur};
-  if (single && Tp.d <= 8 && use_tcx(c, Tp)) {
+  if (tcgen05_only) {
+    variants.push_back(cur ^ TV_TCGEN05);
+  } else if (single && Tp.d <= 8 && use_tcx(c, Tp)) {
     variants.push_back(cur & ~TV_TENSOR_EXP);
   } else if (!single && Tp.d <= 8 && Tp.kfam == KRR_KERNEL_GAUSSIAN) {
     for (int v : {0, (int)TV_TCGEN05, (int)TV_DIRECT_TENSOR, TV_TCGEN05 | TV_DIRECT_TENSOR}) {
@@ -925,11 +927,12 @@ cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m
     }
   }
   c.tune_variant[key] = best_v;
-  // 2. the source split of that variant
+  // 2. the source split of that variant (not for the solvers' kernel-only
+  // choice, which keeps the modelled split)
   double best = 1.0;
   float best_ms = -1.f;
   for (double s : TUNE_SCALES) {
-    if (e) break;
+    if (e || tcgen05_only) break;
     c.tune_cache[key] = s;
     {
       TuneScope ts(c, s);
@@ -949,6 +952,18 @@ cudaError_t autotune_mvp(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, int m
   c.tune_cache[key] = e ? 1.0 : best;
   if (e) c.tune_variant.erase(key);
   return e;
+}
+
+// Whether a solver's reserve of this multi-column shape times the two
+// kernels of its compact blocks (automatic kernel choice, float32, more than
+// TC5_AUTO_MIN_COLS columns, compact blocks present, not nested in another
+// product or tuning, stream not capturing).
+bool solver_kernel_choice(const Ctx& c, const PointsDev& Tp, int m, krr_precision prec, cudaStream_t st) {
+  if (!c.tcgen05_auto || c.tuning || c.prod_depth > 0) return false;
+  if (prec != KRR_FP32 || m <= TC5_AUTO_MIN_COLS || multi_direct_only(Tp) || Tp.h_sb_nexp == 0) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs == cudaStreamCaptureStatusNone;
 }
 
 }  // namespace
@@ -1205,6 +1220,12 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
   if (can_tune(c, st) && !c.tune_cache.count(key)) {
     cudaError_t te = autotune_mvp(c, Tp, Sp, m, prec, st, key);
     if (te) return te;
+  } else if (solver_kernel_choice(c, Tp, m, prec, st) && !c.tune_variant.count(key)) {
+    // a solver reserving a float32 multi-column shape under the automatic
+    // kernel choice: time mvp_umx_kernel against the mma.sync kernel once
+    // (a few products, before any graph capture) and keep the faster
+    cudaError_t te = autotune_mvp(c, Tp, Sp, m, prec, st, key, true);
+    if (te) return te;
   }
   TuneScope scope(c, tuned_scale(c, key));
   VariantScope vscope(c, key);
@@ -1225,7 +1246,7 @@ cudaError_t mvp_multi_reserve(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, 
     return e;
   }
   if (direct_only) return cudaSuccess;  // no expanded-form blocks: no tensor-core kernel
-  if (tc5_on(c, prec, m))
+  if (tc5_on(c, prec, m, Tp))
     return mvp_umma_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                              pt.tiles_per_split, nullptr, nullptr, nullptr, st, true);
   return mvp_tc_partials(c, Tp, Sp, nullptr, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
@@ -1279,7 +1300,7 @@ cudaError_t mvp_multi_launch(Ctx& c, const PointsDev& Tp, const PointsDev& Sp, c
   // products of more than 8 columns: P Q by tcgen05 in mvp_umx_kernel; the
   // others: mma.sync; KRR_OPT_TCGEN05 overrides)
   if (nexp > 0) {
-    e = tc5_on(c, prec, m)
+    e = tc5_on(c, prec, m, Tp)
             ? mvp_umma_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
                                 pt.tiles_per_split, (double*)part, p.fac, o.active, st)
             : mvp_tc_partials(c, Tp, Sp, Q, m, prec == KRR_FP32, prec == KRR_BF16, pt.splits,
