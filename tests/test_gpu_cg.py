@@ -1,6 +1,6 @@
 """GPU conjugate gradient (Sec. 3), the unpreconditioned baseline of Tables I-II.
 
-Judged like the FGMRES solver: the relative residual of the returned FP64
+Checked like the FGMRES solver: the relative residual of the returned FP64
 solution, recomputed by the FP64 oracle, must meet the tolerance, and the
 library's reported true residual must agree with the oracle's.
 """
