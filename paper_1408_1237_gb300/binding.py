@@ -260,6 +260,12 @@ class Points:
             p, self.p = self.p, None
             self.handle.check(lib().krr_points_destroy(self.handle.h, p))
 
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
     def __enter__(self):
         return self
 
