@@ -430,6 +430,21 @@ krr_status krr_profile_enable(krr_handle h, int enable);
 /* Fill *out, waiting for the recorded events, and reset the timed list. */
 krr_status krr_profile_read(krr_handle h, krr_profile* out);
 
+/* ------------------------------------------------ tuning cache file
+ * The autotuner's results on h (KRR_OPT_AUTOTUNE, and the solvers' timed
+ * kernel choice): per product shape, the kernel variant and the source-split
+ * scale.  A shape's key holds its sizes, columns, precision, kernel family,
+ * planning slots, compact-block counts and the kernel-option mode, so an
+ * entry is used only for the same shape under the same options.
+ * krr_tune_save writes them to the text file `path` (a header with the
+ * device's SM count, then one line per shape); KRR_ERR_INVALID_ARG when the
+ * file cannot be written.  krr_tune_load reads such a file into h (its
+ * entries replace h's for the same shapes), so that a later process skips
+ * the timing; KRR_ERR_INVALID_ARG for a missing or malformed file or one
+ * written on a device with another SM count.  Host-only: no device work. */
+krr_status krr_tune_save(krr_handle h, const char* path);
+krr_status krr_tune_load(krr_handle h, const char* path);
+
 /* ------------------------------------------------ no-allocation product
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory: processes whose device memory pool belongs

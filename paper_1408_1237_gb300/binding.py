@@ -96,6 +96,8 @@ _SIGNATURES = {
     "krr_points_create": ([_vp, _vp, _i64, _int, _f, ctypes.POINTER(_vp), _vp], _int),
     "krr_kernel_mvp_points": ([_vp, _vp, _vp, _int, _f, _vp, _int, _vp], _int),
     "krr_points_destroy": ([_vp, _vp], _int),
+    "krr_tune_save": ([_vp, ctypes.c_char_p], _int),
+    "krr_tune_load": ([_vp, ctypes.c_char_p], _int),
 }
 
 
@@ -450,6 +452,20 @@ def krr_set_option(option, value, handle=None):
     the fastest; the others as documented in include/libkrr.h)."""
     h = handle or default_handle()
     h.check(lib().krr_set_option(h.h, int(option), int(value)))
+
+
+def krr_tune_save(path, handle=None):
+    """Write the handle's tuning results (kernel variant and split scale per
+    product shape) to a text file."""
+    h = handle or default_handle()
+    h.check(lib().krr_tune_save(h.h, str(path).encode()))
+
+
+def krr_tune_load(path, handle=None):
+    """Read tuning results written by krr_tune_save (same SM count) into the
+    handle, so that its products skip the timing."""
+    h = handle or default_handle()
+    h.check(lib().krr_tune_load(h.h, str(path).encode()))
 
 
 def krr_profile_enable(enable=True, handle=None):

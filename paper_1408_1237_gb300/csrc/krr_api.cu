@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "api_util.h"
 #include "common.cuh"
@@ -357,6 +358,78 @@ krr_status krr_set_option(krr_handle h, int option, int value) {
     default:
       return set_error(h->ctx, KRR_ERR_INVALID_ARG, "krr_set_option: unknown option %d", option);
   }
+}
+
+// Tuning cache file: "krr-tune 1 sms <n>", then per shape
+// "<key>\t<split scale>\t<variant or -1>" (keys hold no tabs or newlines).
+krr_status krr_tune_save(krr_handle h, const char* path) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  if (!path) return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_save: path is NULL");
+  FILE* f = std::fopen(path, "w");
+  if (!f) return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_save: cannot write %s", path);
+  bool ok = std::fprintf(f, "krr-tune 1 sms %d\n", c.num_sms) > 0;
+  for (const auto& kv : c.tune_cache) {
+    const auto it = c.tune_variant.find(kv.first);
+    ok = ok && std::fprintf(f, "%s\t%.17g\t%d\n", kv.first.c_str(), kv.second,
+                            it == c.tune_variant.end() ? -1 : it->second) > 0;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_save: write to %s failed", path);
+  return KRR_OK;
+}
+
+krr_status krr_tune_load(krr_handle h, const char* path) {
+  if (!h) return KRR_ERR_INVALID_ARG;
+  Ctx& c = h->ctx;
+  if (!path) return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_load: path is NULL");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_load: cannot read %s", path);
+  char line[1024];
+  int sms = -1;
+  if (!std::fgets(line, sizeof line, f) || std::sscanf(line, "krr-tune 1 sms %d", &sms) != 1) {
+    std::fclose(f);
+    return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_load: %s is not a tuning cache file", path);
+  }
+  if (sms != c.num_sms) {
+    std::fclose(f);
+    return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_load: %s was tuned on %d SMs, this device has %d",
+                     path, sms, c.num_sms);
+  }
+  std::vector<std::pair<std::string, std::pair<double, int>>> entries;
+  bool ok = true;
+  while (std::fgets(line, sizeof line, f)) {
+    const size_t n = std::strlen(line);
+    if (n == 0 || line[n - 1] != '\n') {
+      ok = false;  // over-long or truncated line
+      break;
+    }
+    line[n - 1] = 0;
+    char* t1 = std::strchr(line, '\t');
+    char* t2 = t1 ? std::strchr(t1 + 1, '\t') : nullptr;
+    if (!t1 || !t2 || t1 == line) {
+      ok = false;
+      break;
+    }
+    *t1 = *t2 = 0;
+    char* end1 = nullptr;
+    char* end2 = nullptr;
+    const double scale = std::strtod(t1 + 1, &end1);
+    const long variant = std::strtol(t2 + 1, &end2, 10);
+    if (*end1 || *end2 || !(scale > 0.0 && scale <= 256.0) || variant < -1 || variant > 7) {
+      ok = false;
+      break;
+    }
+    entries.push_back({std::string(line), {scale, (int)variant}});
+  }
+  std::fclose(f);
+  if (!ok) return set_error(c, KRR_ERR_INVALID_ARG, "krr_tune_load: malformed line in %s", path);
+  for (const auto& e : entries) {
+    c.tune_cache[e.first] = e.second.first;
+    if (e.second.second >= 0) c.tune_variant[e.first] = e.second.second;
+    else c.tune_variant.erase(e.first);
+  }
+  return KRR_OK;
 }
 
 krr_status krr_profile_enable(krr_handle h, int enable) {

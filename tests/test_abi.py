@@ -103,6 +103,8 @@ int main(void) {
     if (krr_kernel_mvp_points(NULL, NULL, NULL, 1, 0.f, NULL, KRR_FP32, NULL) != KRR_ERR_INVALID_ARG)
         return 12;
     if (krr_points_destroy(NULL, NULL) != KRR_ERR_INVALID_ARG) return 13;
+    if (krr_tune_save(NULL, "x") != KRR_ERR_INVALID_ARG || krr_tune_load(NULL, "x") != KRR_ERR_INVALID_ARG)
+        return 14;
     printf("ok %d\n", (int)s);
     return 0;
 }
