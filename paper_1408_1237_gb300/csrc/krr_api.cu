@@ -239,7 +239,7 @@ using namespace krr;
 
 extern "C" {
 
-int krr_version(void) { return 200; }
+int krr_version(void) { return 300; }
 
 const char* krr_status_string(krr_status s) {
   switch (s) {
